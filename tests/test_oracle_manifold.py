@@ -1,0 +1,243 @@
+"""Pins of the oracle's geometry (Sec. 3.1-3.2), block FOM (App. A), step size
+(Algorithm 2) and CG parameter (Sec. 3.4) against closed forms, library routines,
+finite differences and crafted scalar functions."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import earcg, fom
+from oracle.manifold import (lyapunov, outer, polar, sf_from, tangent_defect, transport_general,
+                             transport_self)
+from oracle.model import Model
+from tests.small_models import small, start
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rand(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _stiefel(rng, n, p):
+    return np.linalg.qr(_rand(rng, n, p))[0]
+
+
+def _tangent(Phi, Z):
+    M = Phi.conj().T @ Z
+    return Z - Phi @ (0.5 * (M + M.conj().T))
+
+
+def test_polar_factor_properties():
+    rng = np.random.default_rng(0)
+    Psi = _rand(rng, 40, 5)
+    pf, d, V = polar(Psi)
+    np.testing.assert_allclose(pf.conj().T @ pf, np.eye(5), atol=1e-13)
+    S = sf_from(d, V)
+    np.testing.assert_allclose(pf @ S, Psi, atol=1e-12)
+    np.testing.assert_allclose(S, S.conj().T, atol=1e-13)
+    assert np.linalg.eigvalsh(S).min() > 0
+    # library polar decomposition as an independent route
+    U, P = sla.polar(Psi, side="right")
+    np.testing.assert_allclose(pf, U, atol=1e-12)
+    Phi = _stiefel(rng, 40, 5)
+    np.testing.assert_allclose(polar(Phi)[0], Phi, atol=1e-13)
+
+
+def test_lyapunov_matches_library_solver():
+    rng = np.random.default_rng(1)
+    A = _rand(rng, 6, 6)
+    S = A.conj().T @ A + np.eye(6)
+    d, V = np.linalg.eigh(S)
+    M = _rand(rng, 6, 6)
+    X = lyapunov(d, V, M)
+    np.testing.assert_allclose(X, sla.solve_continuous_lyapunov(S, M), atol=1e-12)
+
+
+def test_transport_closed_form_equals_general_form_and_is_tangent():
+    rng = np.random.default_rng(2)
+    Phi = _stiefel(rng, 30, 4)
+    eta = _tangent(Phi, _rand(rng, 30, 4))
+    tau = 0.37
+    T1 = transport_self(Phi, tau, eta)
+    T2 = transport_general(Phi, tau * eta, eta)
+    np.testing.assert_allclose(T1, T2, atol=1e-12)
+    Phip = polar(Phi + tau * eta)[0]
+    assert tangent_defect(Phip, T1) < 1e-12
+    g = _tangent(Phi, _rand(rng, 30, 4))
+    assert tangent_defect(Phip, transport_general(Phi, tau * eta, g)) < 1e-12
+
+
+def test_transport_is_the_derivative_of_the_retraction():
+    """T_{xi}(eta) = d/dt pf(Phi + xi + t eta) at t = 0 (central differences)."""
+    rng = np.random.default_rng(3)
+    Phi = _stiefel(rng, 25, 3)
+    xi = 0.4 * _tangent(Phi, _rand(rng, 25, 3))
+    eta = _tangent(Phi, _rand(rng, 25, 3))
+    h = 1e-5
+    fd = (polar(Phi + xi + h * eta)[0] - polar(Phi + xi - h * eta)[0]) / (2 * h)
+    np.testing.assert_allclose(transport_general(Phi, xi, eta), fd, atol=1e-8)
+
+
+def test_projected_sylvester_matches_library_solver():
+    rng = np.random.default_rng(4)
+    A = _rand(rng, 9, 9)
+    A = A + A.conj().T
+    Sig = _rand(rng, 3, 3)
+    Sig = Sig + Sig.conj().T - 10 * np.eye(3)
+    C = _rand(rng, 9, 3)
+    Y = fom.sylvester_projected(A, Sig, C)
+    np.testing.assert_allclose(Y, sla.solve_sylvester(A, -Sig, C), atol=1e-11)
+
+
+def test_orthonormalise_is_rank_revealing():
+    rng = np.random.default_rng(5)
+    V = _stiefel(rng, 50, 4)
+    R = _rand(rng, 50, 3)
+    R = np.hstack([R, R[:, :1] * 2.0 + R[:, 1:2], V[:, :1]])   # rank 3 after projecting out V
+    Q = fom.orthonormalise(R, V)
+    assert Q.shape[1] == 3
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(3), atol=1e-13)
+    assert np.abs(V.conj().T @ Q).max() < 1e-13
+
+
+def test_fom_with_tight_tolerance_solves_the_sylvester_equation_exactly():
+    """Algorithm 4 with rtol -> 0 reproduces the dense Sylvester solution."""
+    m = Model(small(nproj=4, nb=3, ecut=2.0))
+    Phi = earcg.lowdin(start(m))
+    pt = earcg.evaluate(m, Phi)
+    H = m.dense_H(0, pt.vtot)
+    mu = 0.01
+    Sig = pt.Lam[0] - mu * np.eye(m.p)
+    alpha = earcg.kinetic_alpha(m, Phi)[0]
+    X, it, rel, _ = fom.fom(lambda V: H @ V, Phi[0], pt.HPhi[0], Sig, mu,
+                            fom.tpa_inverse(m.kin[0], alpha), rtol=1e-11, max_iter=200)
+    Xd = sla.solve_sylvester(H, -Sig, Phi[0])
+    np.testing.assert_allclose(X, Xd, atol=1e-9 * np.abs(Xd).max())
+
+
+def test_fom_galerkin_condition_and_stopping_rule():
+    m = Model(small(nproj=4, nb=3, ecut=2.0))
+    Phi = earcg.lowdin(start(m))
+    pt = earcg.evaluate(m, Phi)
+    H = m.dense_H(0, pt.vtot)
+    mu = 0.01
+    Sig = pt.Lam[0] - mu * np.eye(m.p)
+    alpha = earcg.kinetic_alpha(m, Phi)[0]
+    X, it, rel, _ = fom.fom(lambda V: H @ V, Phi[0], pt.HPhi[0], Sig, mu,
+                            fom.tpa_inverse(m.kin[0], alpha), rtol=2.5e-2)
+    X0 = Phi[0] / mu
+    r0 = np.linalg.norm(H @ X0 - X0 @ Sig - Phi[0])
+    rj = np.linalg.norm(H @ X - X @ Sig - Phi[0])
+    assert rj <= 2.5e-2 * r0 + 1e-12
+    assert abs(rj / r0 - rel) < 1e-10
+
+
+def test_ea_gradient_with_uniform_shift_is_the_riesz_representative():
+    """Cor. 1 with a uniform coercive shift Sigma = -s I and an exact solve: G is tangent
+    and g(G, eta) = <(H - Sigma) G, eta> = <R, eta> for tangent eta (Eq. (2.7))."""
+    rng = np.random.default_rng(6)
+    n, p = 40, 3
+    A = _rand(rng, n, n)
+    H = A + A.conj().T
+    s = -np.linalg.eigvalsh(H).min() + 1.0
+    Sig = -s * np.eye(p)
+    Phi = _stiefel(rng, n, p)
+    X = sla.solve_sylvester(H, -Sig, Phi)
+    G = Phi - X @ np.linalg.inv(Phi.conj().T @ X)
+    assert tangent_defect(Phi, G) < 1e-11
+    R = H @ Phi - Phi @ (Phi.conj().T @ H @ Phi)
+    for _ in range(3):
+        eta = _tangent(Phi, _rand(rng, n, p))
+        lhs = np.vdot(H @ G - G @ Sig, eta).real
+        assert abs(lhs - np.vdot(R, eta).real) < 1e-10 * abs(lhs)
+
+
+def test_shifted_sylvester_operator_spectrum():
+    """Proof of Prop. 4: at an eigenbasis, X -> H X - X (Lambda - mu I) has the eigenvalues
+    lambda_m - lambda_l + mu (Kronecker sum, checked on a dense matrix)."""
+    rng = np.random.default_rng(7)
+    n, p, mu = 8, 2, 0.01
+    A = _rand(rng, n, n)
+    H = A + A.conj().T
+    lam, U = np.linalg.eigh(H)
+    Phi = U[:, :p]
+    Sig = Phi.conj().T @ H @ Phi - mu * np.eye(p)
+    L = np.kron(np.eye(p), H) - np.kron(Sig.T, np.eye(n))
+    ev = np.sort(np.linalg.eigvals(L).real)
+    want = np.sort((lam[:, None] - lam[None, :p] + mu).ravel())
+    np.testing.assert_allclose(ev, want, atol=1e-10)
+
+
+def _prm(**kw):
+    return earcg.Params(**kw)
+
+
+def test_secant_solves_a_quadratic_in_one_step():
+    """f(t) = (t - 3)^2: from tau0 = 1 the first secant step lands on the minimiser."""
+    f = lambda t: (None, (t - 3.0) ** 2, 2.0 * (t - 3.0))
+    tau, _, trials = earcg.modified_secant(f, 9.0, -6.0, 1.0, _prm())
+    assert tau == pytest.approx(3.0, abs=1e-14)
+    assert trials == 2
+
+
+def test_secant_accepts_the_initial_step_when_it_is_wolfe():
+    f = lambda t: (None, (t - 1.0) ** 2, 2.0 * (t - 1.0))
+    tau, _, trials = earcg.modified_secant(f, 1.0, -2.0, 1.0, _prm())
+    assert tau == 1.0 and trials == 1
+
+
+def test_secant_too_big_branch_shrinks_the_interval():
+    """A secant point with f > f(0) and f' < 0 (past a hump) resets [a, b] = [0, gamma b]."""
+    calls = []
+
+    def g(t):
+        calls.append(t)
+        if t == 8.0:
+            return None, 5.0, -1.0      # first trial: not Wolfe
+        if len(calls) == 2:
+            return None, 5.0, -0.5      # secant point: f > f0 and f' < 0 -> too big
+        return None, (t - 1.0) ** 2 - 1.0, 2.0 * (t - 1.0)
+
+    tau, _, trials = earcg.modified_secant(g, 0.0, -2.0, 8.0, _prm())
+    assert calls[2] == 4.0               # tau = gamma * b
+    assert tau == pytest.approx(1.0, abs=1e-12)
+
+
+def test_secant_too_small_branch_expands_the_interval():
+    """A secant point left of a (f' decreasing) resets [a, b] = [0, b / gamma]."""
+    calls = []
+
+    def g(t):
+        calls.append(t)
+        if len(calls) == 1:
+            return None, -0.1, -30.0    # f' more negative at b than at a: secant gives tau < 0
+        return None, (t - 5.0) ** 2 - 25.0, 2.0 * (t - 5.0)
+
+    tau, _, _ = earcg.modified_secant(g, 0.0, -10.0, 1.0, _prm())
+    assert calls == [1.0, 2.0, 5.0]      # no evaluation left of a; tau = b / gamma, then secant
+    assert tau == pytest.approx(5.0, abs=1e-12)
+
+
+def test_secant_trial_cap_raises():
+    g = lambda t: (None, 1.0 + t, 1.0)  # never satisfies the energy test
+    with pytest.raises(earcg.LineSearchError):
+        earcg.modified_secant(g, 0.0, -1.0, 1.0, _prm(max_ls=5))
+
+
+def test_beta_hybrid_fr_prp_clamping():
+    assert earcg.beta_fr_prp(2.0, 4.0, 1.0) == pytest.approx(0.25)   # PRP < FR
+    assert earcg.beta_fr_prp(2.0, 4.0, -3.0) == pytest.approx(0.5)   # FR < PRP
+    assert earcg.beta_fr_prp(2.0, 4.0, 5.0) == 0.0                    # PRP < 0 clamps
+
+
+def test_oracle_defaults_are_the_paper_constants():
+    with open(os.path.join(HERE, "golden", "paper_constants.json")) as fh:
+        c = json.load(fh)
+    prm = earcg.Params()
+    for key in ("delta", "sigma", "gamma", "eps", "mu", "fom_rtol"):
+        assert getattr(prm, key) == c[key]["value"], key
+    assert min(prm.sigma, 1 - 2 * prm.delta) == c["wolfe_curvature_factor"]["value"]
