@@ -1,0 +1,179 @@
+/*
+ * libeacg: energy-adaptive Riemannian conjugate gradient (eARCG) minimisation of the
+ * Kohn-Sham energy on the Stiefel manifold in a periodic plane-wave basis, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Peterseim, Pueschel, Stykel, "Energy-Adaptive Riemannian Conjugate Gradient
+ * Method for Density Functional Theory", arXiv 2503.16225.  Problem statement
+ * min_{Phi in St} E(Phi): Sec. 2.1, Eq. (2.2); discrete form on the product of
+ * Stiefel manifolds over k-points: Sec. 5.1, Eq. (5.1).
+ *
+ * Conventions shared by every entry point
+ *   - Coefficient blocks ("psi" buffers) are complex double (interleaved re, im),
+ *     laid out [K][p][n_max]: k-point major, then band, then plane-wave index in the
+ *     canonical basis order of eacg_get_basis; entries n_k .. n_max-1 of every band are
+ *     zero on input and are written as zero on output.  Column i of block k is orbital
+ *     i of Phi_k in C^{n_k x p} (Sec. 5.1).
+ *   - Real-space grids are double [jx][jy][jz] (z fastest), r_j = a j / N.
+ *   - Small matrices (Lambda) are complex double [K][p][p], column-major.
+ *   - Pointers named *_dev are device pointers (caller-owned, valid for the call);
+ *     *_host are host pointers.  Calls are ordered on the system's CUDA stream and
+ *     return after the stream has been synchronised.
+ *   - Every call returns eacg_status; no call aborts or throws.  eacg_last_error gives
+ *     a message for the last failing call of a system.  After a failure other than
+ *     EACG_ENOTCONV or EACG_ELINESEARCH the system keeps its state from before the call.
+ *   - One system is not thread-safe; distinct systems are independent.
+ */
+#ifndef EACG_H
+#define EACG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eacg_system eacg_system;
+
+typedef enum {
+  EACG_OK = 0,
+  EACG_EINVAL = 1,        /* invalid argument or model                          */
+  EACG_ENOMEM = 2,        /* device allocation failed                           */
+  EACG_ECUDA = 3,         /* a CUDA runtime call or launch failed               */
+  EACG_EBREAKDOWN = 4,    /* singular projected system in the block FOM         */
+  EACG_ENONCOERCIVE = 5,  /* reserved: shifted Hamiltonian not coercive         */
+  EACG_ELINESEARCH = 6,   /* step-size search hit its trial cap (Algorithm 2)   */
+  EACG_ENAN = 7,          /* non-finite energy or residual                      */
+  EACG_ENOTCONV = 8,      /* outer iteration cap reached before the tolerance   */
+  EACG_EUNSUPPORTED = 9   /* size outside what this build supports              */
+} eacg_status;
+
+/* Synthetic crystal (cubic cell) and its discretisation (Sec. 1, Eq. (1.1); Sec. 5.1).
+ * Local part: V(G) = sum_a -4 pi Z_a / (Omega |G|^2) exp(-|G|^2 rc_a^2 / 4) e^{-i G.R_a}.
+ * Nonlocal part: nproj_per_atom in {0, 1, 4} L2-normalised Gaussian projectors
+ * (s, px, py, pz) of width proj_width with couplings D[a][0] (s) and D[a][1] (p). */
+typedef struct {
+  double a;                /* cubic cell edge (bohr)                           */
+  int natoms;
+  const double* pos;       /* host, natoms x 3 cartesian (bohr)                */
+  const int* Z;            /* host, natoms                                     */
+  const double* rc;        /* host, natoms (bohr)                              */
+  int nproj_per_atom;      /* 0, 1 or 4                                        */
+  double proj_width;       /* bohr                                             */
+  const double* D;         /* host, natoms x 2 (Ha)                            */
+  double ecut;             /* basis: 1/2 |k+G|^2 <= ecut (Ha)                  */
+  int N;                   /* FFT grid edge, 2^a 3^b or 2^a 5^c, 8 <= N <= 96  */
+  int nbands;              /* p: occupied orbitals per k-point                 */
+  int nk;                  /* K: number of k-points                            */
+  const double* kfrac;     /* host, K x 3 fractional coordinates (units of 2 pi / a) */
+  const double* kweight;   /* host, K weights (sum 1)                          */
+  int hartree;             /* 1: Hartree term on                               */
+  int xc;                  /* 1: Slater exchange on                            */
+  double occ;              /* occupation f of every orbital (2: spin paired)   */
+} eacg_model;
+
+/* Iteration constants (defaults: Sec. 5.2).  precision: 0 = FP64 throughout,
+ * 1 = mixed (FP32 transforms while ||R||_F > switch_res, FP64 afterwards). */
+typedef struct {
+  double mu;          /* shift correction, Sigma = Lambda - mu I (Sec. 4.3): 0.01  */
+  double res_tol;     /* stop when ||R||_F <= res_tol: 1e-8                        */
+  double fom_rtol;    /* relative Sylvester residual of the block FOM: 2.5e-2      */
+  double delta, sigma, gamma, eps;  /* Algorithm 2: 0.05, 0.1, 0.5, 1e-12          */
+  double warm_res;    /* warm-up phase ends at ||R||_F <= warm_res: 1e-2          */
+  double switch_res;  /* mixed precision: FP64 from ||R||_F <= switch_res: 1e-3    */
+  int max_outer;      /* 300 */
+  int max_warm;       /* 100 */
+  int max_fom;        /* 50  */
+  int max_ls;         /* 30  */
+  int precision;      /* 0 FP64, 1 mixed */
+} eacg_params;
+
+typedef struct {
+  double E;            /* energy after the step (Ha, without ion-ion term)        */
+  double rnorm;        /* ||R||_F = (sum_k ||H Phi_k - Phi_k Lambda_k||_F^2)^1/2   */
+  double tau;          /* accepted step size                                       */
+  double beta;         /* CG parameter used for the next direction                 */
+  int fom_iters_max;   /* largest per-k FOM iteration count at the new point       */
+  int ls_trials;       /* trial points of Algorithm 2 in this step                 */
+  int phase;           /* 0 warm-up, 1 energy-adaptive                             */
+  int precision;       /* precision used for this step's transforms                */
+  int converged;       /* 1 when rnorm <= res_tol                                  */
+  long long h_band_apps; /* cumulative band applications of H (one band at one k = 1) */
+} eacg_step_info;
+
+typedef struct {
+  double E;
+  double rnorm;
+  int iterations;
+  int warm_iterations;
+  int status;          /* eacg_status of the solve */
+  int ls_trials;       /* total trial points */
+  long long h_band_apps;
+} eacg_result;
+
+/* Defaults of Sec. 5.2 and the readings documented with the library. */
+void eacg_default_params(eacg_params* prm);
+
+/* Device bytes a system of this model needs (HBM admission), excluding the Krylov
+ * blocks of the FOM, which grow with its iteration count (returned in *fom_bytes_per_iter
+ * when not NULL).  Returns 0 for an invalid model. */
+size_t eacg_bytes_required(const eacg_model* model, const eacg_params* prm, size_t* fom_bytes_per_iter);
+
+/* Builds the basis (Sec. 5.1), local potential and projectors on the device.
+ * stream: a cudaStream_t (NULL = legacy default stream).  *out owns all device state. */
+eacg_status eacg_create_system(const eacg_model* model, const eacg_params* prm, void* stream, eacg_system** out);
+void eacg_destroy(eacg_system* sys);
+const char* eacg_last_error(const eacg_system* sys);
+
+/* n_k per k-point (nk_host: K ints, may be NULL), n_max = max n_k, union column count. */
+eacg_status eacg_get_dims(const eacg_system* sys, int* nk_host, int* n_max, int* ncols);
+/* Integer triples m (G = 2 pi m / a) of the basis: m_dev int32 [K][n_max][3]
+ * (rows >= n_k unspecified).  Canonical order: (mx, my, mz) lexicographic, mz fastest. */
+eacg_status eacg_get_basis(const eacg_system* sys, int* m_dev);
+
+/* Sets the iterate to pf(psi) (polar factor, Eq. (3.1)) of a raw block and resets the
+ * CG state; the next eacg_step starts Algorithm 3 from it. */
+eacg_status eacg_set_psi(eacg_system* sys, const double* psi_dev);
+eacg_status eacg_get_psi(eacg_system* sys, double* psi_dev_out);
+
+/* Density rho(r_j) = sum_k w_k f sum_i |u_ik(r_j)|^2 of an orthonormal block (Sec. 1),
+ * written to rho_dev (N^3, may be NULL); updates the system's potential
+ * V = V_loc + V_H(rho) + V_x(rho) used by eacg_apply_H.  precision as in eacg_params. */
+eacg_status eacg_density(eacg_system* sys, const double* psi_dev, double* rho_dev, int precision);
+/* Current total potential (N^3). */
+eacg_status eacg_get_potential(eacg_system* sys, double* vtot_dev);
+
+/* hpsi = H psi with the current potential: 1/2 |k+G|^2 psi + local part by the FFT pair
+ * + B D B^* psi (Eq. (1.4) in the DFTK form of Sec. 5.2).  psi and hpsi must not overlap. */
+eacg_status eacg_apply_H(eacg_system* sys, const double* psi_dev, double* hpsi_dev, int precision);
+
+/* Full evaluation at an orthonormal block: density, potential, H Phi, Lambda =
+ * herm(Phi^* H Phi) (Eq. (2.6)), residual R = H Phi - Phi Lambda, energy terms.
+ * terms_host[6] = {kinetic, local, Hartree, exchange, nonlocal, total}.  lam_dev and
+ * res_dev may be NULL.  *rnorm = ||R||_F. */
+eacg_status eacg_energy(eacg_system* sys, const double* psi_dev, double* terms_host, double* lam_dev,
+                        double* res_dev, double* rnorm, int precision);
+
+/* Energy-adaptive gradient G = Phi - X (Phi^* X)^{-1}, H X - X (Lambda - mu I) = Phi solved
+ * per k by the preconditioned block FOM (Sec. 5.2, Algorithm 4).  fom_iters_host: K ints
+ * (may be NULL). */
+eacg_status eacg_ea_gradient(eacg_system* sys, const double* psi_dev, double* g_dev, int* fom_iters_host,
+                             int precision);
+
+/* Polar retraction Phi+ = pf(Phi + tau eta) (Eq. (3.2)) and the transport
+ * T_{tau eta}(eta) = eta S^{-1} - tau Phi+ [[eta S^{-1}, eta S^{-1}]] (Sec. 3.2). */
+eacg_status eacg_retract(eacg_system* sys, const double* phi_dev, const double* eta_dev, double tau,
+                         double* phi_out_dev, double* teta_out_dev);
+
+/* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
+eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);
+/* Iterates eacg_step until ||R||_F <= res_tol or max_outer; result in *out. */
+eacg_status eacg_solve(eacg_system* sys, eacg_result* out);
+/* eacg_set_psi + eacg_solve + eacg_get_psi through host buffers (copies on the system's
+ * stream; psi0_host and psi_out_host are [K][p][n_max] complex double, may alias). */
+eacg_status eacg_solve_host(eacg_system* sys, const double* psi0_host, double* psi_out_host, eacg_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

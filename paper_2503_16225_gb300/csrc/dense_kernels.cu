@@ -1,0 +1,875 @@
+// Dense kernels of libeacg (sm_103a, FP64 complex), batched over k-points:
+// Gram-type products A^H B with a long reduction, block updates A B with a small
+// right factor, small Hermitian eigen-decompositions (parallel cyclic Jacobi),
+// inverses, Lyapunov solves, pairings and norms, and the projected shifted
+// solves of the block FOM.  Every matrix is column-major: A_ij = A[j * ld + i].
+// All reductions run over fixed chunks combined in a fixed order, so results do
+// not depend on scheduling.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace eacg {
+
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // c + a * b
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // c + conj(a) * b
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// ----------------------------------------------------------------------------- A^H B
+constexpr int CN_TILE = 16;
+constexpr int CN_CHUNK = 1024;  // rows per partial
+constexpr int CN_SUB = 32;      // rows staged per step
+
+size_t dense_cn_work(int K, int L, int m, int n) {
+  const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
+  return (size_t)K * nch * m * n;
+}
+
+__global__ void k_gemm_cn_partial(int L, int m, int n, const double2* __restrict__ A, size_t sA, int lda,
+                                  const double2* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
+                                  const int* __restrict__ kactive) {
+  const int k = blockIdx.z;
+  if (kactive && !kactive[k]) return;
+  const int tiles_m = (m + CN_TILE - 1) / CN_TILE;
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const int ch = blockIdx.y, nch = gridDim.y;
+  const int ti = threadIdx.x % CN_TILE, tj = threadIdx.x / CN_TILE;
+  const int i0 = tm * CN_TILE, j0 = tn * CN_TILE;
+  __shared__ double2 sa[CN_SUB][CN_TILE + 1];
+  __shared__ double2 sb[CN_SUB][CN_TILE + 1];
+  const double2* Ak = A + k * sA;
+  const double2* Bk = B + k * sB;
+  double2 acc = make_double2(0.0, 0.0);
+  const int l_beg = ch * CN_CHUNK, l_end = min(L, l_beg + CN_CHUNK);
+  for (int l0 = l_beg; l0 < l_end; l0 += CN_SUB) {
+    for (int e = threadIdx.x; e < CN_SUB * CN_TILE; e += blockDim.x) {
+      const int c = e / CN_SUB, r = e - c * CN_SUB;
+      const int l = l0 + r;
+      sa[r][c] = (l < l_end && i0 + c < m) ? Ak[(size_t)(i0 + c) * lda + l] : make_double2(0.0, 0.0);
+      sb[r][c] = (l < l_end && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + l] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < CN_SUB; ++r) acc = cfmac(sa[r][ti], sb[r][tj], acc);
+    __syncthreads();
+  }
+  if (i0 + ti < m && j0 + tj < n) part[(((size_t)k * nch + ch) * n + (j0 + tj)) * m + (i0 + ti)] = acc;
+}
+
+__global__ void k_gemm_cn_reduce(int m, int n, int nch, const double2* __restrict__ part, double2* __restrict__ C,
+                                 size_t sC, int ldc, double2 alpha, double2 beta, const int* __restrict__ kactive) {
+  const int k = blockIdx.y;
+  if (kactive && !kactive[k]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += gridDim.x * blockDim.x) {
+    const int j = e / m, i = e - j * m;
+    double2 s = make_double2(0.0, 0.0);
+    for (int c = 0; c < nch; ++c) s = s + part[(((size_t)k * nch + c) * n + j) * m + i];
+    double2* cp = C + k * sC + (size_t)j * ldc + i;
+    double2 r = cmul(alpha, s);
+    if (beta.x != 0.0 || beta.y != 0.0) r = r + cmul(beta, *cp);
+    *cp = r;
+  }
+}
+
+void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
+                   int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
+                   const int* kactive, cudaStream_t st) {
+  if (K <= 0 || m <= 0 || n <= 0) return;
+  const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
+  const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
+  dim3 g1(tiles, nch > 0 ? nch : 1, K);
+  if (nch > 0) k_gemm_cn_partial<<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+  dim3 g2((m * n + 255) / 256, K);
+  k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
+}
+
+// ----------------------------------------------------------------------------- A B (small B)
+constexpr int NN_COLS = 8;
+constexpr int NN_ROWS = 64;
+__global__ void k_gemm_nn(int L, int m, int n, const double2* __restrict__ A, size_t sA, int lda,
+                          const double2* __restrict__ B, size_t sB, int ldb, double2* __restrict__ C, size_t sC,
+                          int ldc, double2 alpha, double2 beta, const int* __restrict__ kactive) {
+  const int k = blockIdx.y;
+  if (kactive && !kactive[k]) return;
+  __shared__ double2 sb[NN_ROWS][NN_COLS];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const double2* Ak = A + k * sA;
+  const double2* Bk = B + k * sB;
+  double2* Ck = C + k * sC;
+  const bool bz = (beta.x == 0.0 && beta.y == 0.0);
+  for (int j0 = 0; j0 < n; j0 += NN_COLS) {
+    double2 acc[NN_COLS];
+#pragma unroll
+    for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = make_double2(0.0, 0.0);
+    for (int i0 = 0; i0 < m; i0 += NN_ROWS) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < NN_ROWS * NN_COLS; e += blockDim.x) {
+        const int r = e / NN_COLS, c = e - r * NN_COLS;
+        sb[r][c] = (i0 + r < m && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + i0 + r] : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      if (l < L) {
+        const int iend = min(NN_ROWS, m - i0);
+        for (int r = 0; r < iend; ++r) {
+          const double2 a = Ak[(size_t)(i0 + r) * lda + l];
+#pragma unroll
+          for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = cfma(a, sb[r][jj], acc[jj]);
+        }
+      }
+    }
+    if (l < L) {
+#pragma unroll
+      for (int jj = 0; jj < NN_COLS; ++jj) {
+        if (j0 + jj < n) {
+          double2* cp = Ck + (size_t)(j0 + jj) * ldc + l;
+          double2 r = cmul(alpha, acc[jj]);
+          if (!bz) r = r + cmul(beta, *cp);
+          *cp = r;
+        }
+      }
+    }
+  }
+}
+
+void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
+                   int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
+                   cudaStream_t st) {
+  if (K <= 0 || L <= 0 || n <= 0) return;
+  dim3 g((L + 127) / 128, K);
+  k_gemm_nn<<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
+}
+
+// ----------------------------------------------------------------------------- Hermitian eig
+// Parallel cyclic Jacobi (round-robin pairs) on one p x p Hermitian matrix per CTA.
+__global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double* __restrict__ w,
+                       double2* __restrict__ Vg, const int* __restrict__ kactive) {
+  const int k = blockIdx.x;
+  if (kactive && !kactive[k]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int pe = p + (p & 1);  // even number of slots (a dummy index when p is odd)
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* V = A + p * p;
+  int* slot = reinterpret_cast<int*>(V + p * p);   // [pe] current pairing order
+  double* rot = reinterpret_cast<double*>(slot + pe + (pe & 1));  // [pe/2][4]: c, s, cos phi, sin phi
+  double* red = rot + 2 * pe;                      // [2]
+  const double2* Ak = Ag + k * sA;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    A[e] = Ak[e];
+    const int j = e / p, i = e - j * p;
+    V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  for (int i = threadIdx.x; i < pe; i += blockDim.x) slot[i] = i;
+  __syncthreads();
+  // symmetrise exactly
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    if (i < j) {
+      const double2 a = A[j * p + i], b = A[i * p + j];
+      const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+      A[j * p + i] = h;
+      A[i * p + j] = cconj(h);
+    } else if (i == j) {
+      A[e].y = 0.0;
+    }
+  }
+  __syncthreads();
+  const int npair = pe / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0.0, dia = 0.0;
+      for (int j = 0; j < p; ++j)
+        for (int i = 0; i < p; ++i) {
+          const double a2 = cabs2(A[j * p + i]);
+          if (i == j)
+            dia += a2;
+          else
+            off += a2;
+        }
+      red[0] = off;
+      red[1] = dia;
+    }
+    __syncthreads();
+    if (!(red[0] > 1e-32 * (red[0] + red[1]))) break;
+    __syncthreads();
+    for (int round = 0; round < pe - 1; ++round) {
+      // rotation parameters for each pair (top[t] = slot[t], bot[t] = slot[pe-1-t])
+      for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+        int i = slot[t], j = slot[pe - 1 - t];
+        if (i > j) {
+          const int q = i;
+          i = j;
+          j = q;
+        }
+        double c = 1.0, s = 0.0, cf = 1.0, sf = 0.0;
+        if (j < p) {
+          const double2 b = A[j * p + i];
+          const double r = sqrt(cabs2(b));
+          if (r > 1e-300) {
+            const double a = A[i * p + i].x, d = A[j * p + j].x;
+            const double zeta = (d - a) / (2.0 * r);
+            const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            s = tt * c;
+            cf = b.x / r;   // e^{i phi} = b / r
+            sf = b.y / r;
+          }
+        }
+        rot[4 * t + 0] = c;
+        rot[4 * t + 1] = s;
+        rot[4 * t + 2] = cf;
+        rot[4 * t + 3] = sf;
+      }
+      __syncthreads();
+      // columns: (A_ki, A_kj) <- (c A_ki - s e^{-i phi} A_kj, s A_ki + c e^{-i phi} A_kj); same for V
+      for (int e = threadIdx.x; e < npair * p; e += blockDim.x) {
+        const int t = e / p, r = e - t * p;
+        int i = slot[t], j = slot[pe - 1 - t];
+        if (i > j) {
+          const int q = i;
+          i = j;
+          j = q;
+        }
+        if (j >= p) continue;
+        const double c = rot[4 * t], s = rot[4 * t + 1];
+        const double2 em = make_double2(rot[4 * t + 2], -rot[4 * t + 3]);  // e^{-i phi}
+        {
+          const double2 ai = A[i * p + r], aj = cmul(em, A[j * p + r]);
+          A[i * p + r] = make_double2(c * ai.x - s * aj.x, c * ai.y - s * aj.y);
+          A[j * p + r] = make_double2(s * ai.x + c * aj.x, s * ai.y + c * aj.y);
+        }
+        {
+          const double2 vi = V[i * p + r], vj = cmul(em, V[j * p + r]);
+          V[i * p + r] = make_double2(c * vi.x - s * vj.x, c * vi.y - s * vj.y);
+          V[j * p + r] = make_double2(s * vi.x + c * vj.x, s * vi.y + c * vj.y);
+        }
+      }
+      __syncthreads();
+      // rows: (A_ik, A_jk) <- (c A_ik - s e^{i phi} A_jk, s A_ik + c e^{i phi} A_jk)
+      for (int e = threadIdx.x; e < npair * p; e += blockDim.x) {
+        const int t = e / p, col = e - t * p;
+        int i = slot[t], j = slot[pe - 1 - t];
+        if (i > j) {
+          const int q = i;
+          i = j;
+          j = q;
+        }
+        if (j >= p) continue;
+        const double c = rot[4 * t], s = rot[4 * t + 1];
+        const double2 ep = make_double2(rot[4 * t + 2], rot[4 * t + 3]);
+        const double2 ai = A[col * p + i], aj = cmul(ep, A[col * p + j]);
+        A[col * p + i] = make_double2(c * ai.x - s * aj.x, c * ai.y - s * aj.y);
+        A[col * p + j] = make_double2(s * ai.x + c * aj.x, s * ai.y + c * aj.y);
+      }
+      __syncthreads();
+      // exact zero of the annihilated pairs, then rotate the pairing (slot 0 fixed)
+      if (threadIdx.x == 0) {
+        for (int t = 0; t < npair; ++t) {
+          int i = slot[t], j = slot[pe - 1 - t];
+          if (i > j) {
+            const int q = i;
+            i = j;
+            j = q;
+          }
+          if (j < p && rot[4 * t + 1] != 0.0) {
+            A[j * p + i] = make_double2(0.0, 0.0);
+            A[i * p + j] = make_double2(0.0, 0.0);
+          }
+          A[i * p + i].y = 0.0;
+          if (j < p) A[j * p + j].y = 0.0;
+        }
+        const int last = slot[pe - 1];
+        for (int q = pe - 1; q > 1; --q) slot[q] = slot[q - 1];
+        slot[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // sort ascending by rank (ties by index) and write out
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const double wi = A[i * p + i].x;
+    int rank = 0;
+    for (int j = 0; j < p; ++j) {
+      const double wj = A[j * p + j].x;
+      if (wj < wi || (wj == wi && j < i)) ++rank;
+    }
+    w[(size_t)k * p + rank] = wi;
+    for (int r = 0; r < p; ++r) Vg[(size_t)k * p * p + (size_t)rank * p + r] = V[i * p + r];
+  }
+}
+
+void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
+                cudaStream_t st) {
+  const int pe = p + (p & 1);
+  const size_t sm = sizeof(double2) * 2 * p * p + sizeof(int) * (pe + 2) + sizeof(double) * (2 * pe + 2) + 16;
+  cudaFuncSetAttribute(k_heig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int threads = p <= 16 ? 128 : 256;
+  k_heig<<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
+}
+
+// out = V diag(f(w)) V^H, f(x) = x^expo for x > cut_rel * max(w, 0), else 0
+__global__ void k_eig_func(int p, const double2* __restrict__ V, const double* __restrict__ w, double expo,
+                           double cut_rel, double2* __restrict__ out, const int* __restrict__ kactive) {
+  const int k = blockIdx.x;
+  if (kactive && !kactive[k]) return;
+  extern __shared__ double fsm[];
+  const double* wk = w + (size_t)k * p;
+  const double2* Vk = V + (size_t)k * p * p;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < p; ++i) mx = fmax(mx, wk[i]);
+    fsm[p] = mx;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const double x = wk[i];
+    fsm[i] = (x > cut_rel * fsm[p] && x > 0.0) ? pow(x, expo) : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    double2 s = make_double2(0.0, 0.0);
+    for (int l = 0; l < p; ++l) {
+      const double f = fsm[l];
+      if (f != 0.0) s = s + cscale(cmul(Vk[l * p + i], cconj(Vk[l * p + j])), f);
+    }
+    out[(size_t)k * p * p + e] = s;
+  }
+}
+
+void dense_eig_func(int K, int p, const double2* V, const double* w, double expo, double cut_rel, double2* out,
+                    const int* kactive, cudaStream_t st) {
+  k_eig_func<<<K, 128, sizeof(double) * (p + 1), st>>>(p, V, w, expo, cut_rel, out, kactive);
+}
+
+// Gauss-Jordan inverse with partial pivoting, one CTA per matrix (p <= 64).
+__global__ void k_inverse(int p, const double2* __restrict__ A, double2* __restrict__ Ainv, int* __restrict__ info) {
+  const int k = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* M = reinterpret_cast<double2*>(smem_raw);  // [2p][p] column-major augmented
+  __shared__ int piv;
+  const double2* Ak = A + (size_t)k * p * p;
+  for (int e = threadIdx.x; e < 2 * p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    M[e] = j < p ? Ak[e] : make_double2(i == j - p ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < p; ++c) {
+    if (threadIdx.x == 0) {
+      int best = c;
+      double bv = cabs2(M[c * p + c]);
+      for (int i = c + 1; i < p; ++i) {
+        const double v = cabs2(M[c * p + i]);
+        if (v > bv) {
+          bv = v;
+          best = i;
+        }
+      }
+      piv = best;
+      if (bv == 0.0 && info) info[k] = c + 1;
+    }
+    __syncthreads();
+    const int r = piv;
+    if (r != c) {
+      for (int j = threadIdx.x; j < 2 * p; j += blockDim.x) {
+        const double2 t = M[j * p + c];
+        M[j * p + c] = M[j * p + r];
+        M[j * p + r] = t;
+      }
+    }
+    __syncthreads();
+    const double2 d = M[c * p + c];
+    const double dd = cabs2(d);
+    const double2 dinv = dd > 0 ? make_double2(d.x / dd, -d.y / dd) : make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * p; j += blockDim.x) M[j * p + c] = cmul(M[j * p + c], dinv);
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * 2 * p; e += blockDim.x) {
+      const int j = e / p, i = e - j * p;
+      if (i != c && j != c) {
+        const double2 f = M[c * p + i];
+        M[j * p + i] = M[j * p + i] - cmul(f, M[j * p + c]);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+      if (i != c) M[c * p + i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    // column c of the left half now is e_c; its inverse part lives in column p + c
+  }
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ainv[(size_t)k * p * p + e] = M[p * p + e];
+}
+
+void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st) {
+  const size_t sm = sizeof(double2) * 2 * p * p;
+  cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_inverse<<<K, 256, sm, st>>>(p, A, Ainv, info);
+}
+
+// Lyapunov by the eigenbasis of S.
+__global__ void k_lyap(int p, const double2* __restrict__ Vg, const double* __restrict__ s, const double2* __restrict__ Mg,
+                       double2* __restrict__ X) {
+  const int k = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* V = reinterpret_cast<double2*>(smem_raw);
+  double2* T1 = V + p * p;
+  double2* T2 = T1 + p * p;
+  const double2* Vk = Vg + (size_t)k * p * p;
+  const double2* Mk = Mg + (size_t)k * p * p;
+  const double* sk = s + (size_t)k * p;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) V[e] = Vk[e];
+  __syncthreads();
+  // T1 = M V
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    double2 a = make_double2(0.0, 0.0);
+    for (int l = 0; l < p; ++l) a = cfma(Mk[l * p + i], V[j * p + l], a);
+    T1[e] = a;
+  }
+  __syncthreads();
+  // T2 = (V^H T1) ./ (s_i + s_j)
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    double2 a = make_double2(0.0, 0.0);
+    for (int l = 0; l < p; ++l) a = cfmac(V[i * p + l], T1[j * p + l], a);
+    T2[e] = cscale(a, 1.0 / (sk[i] + sk[j]));
+  }
+  __syncthreads();
+  // T1 = T2 V^H ; X = V T1
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    double2 a = make_double2(0.0, 0.0);
+    for (int l = 0; l < p; ++l) a = cfma(T2[l * p + i], cconj(V[l * p + j]), a);
+    T1[e] = a;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    double2 a = make_double2(0.0, 0.0);
+    for (int l = 0; l < p; ++l) a = cfma(V[l * p + i], T1[j * p + l], a);
+    X[(size_t)k * p * p + e] = a;
+  }
+}
+
+void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st) {
+  const size_t sm = sizeof(double2) * 3 * p * p;
+  cudaFuncSetAttribute(k_lyap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_lyap<<<K, 256, sm, st>>>(p, V, s, M, X);
+}
+
+// ----------------------------------------------------------------------------- elementwise
+__global__ void k_axpby(size_t n, double2 a, const double2* __restrict__ x, double2 b, const double2* __restrict__ y,
+                        double2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double2 r = cmul(a, x[i]);
+    if (y) r = r + cmul(b, y[i]);
+    out[i] = r;
+  }
+}
+void dense_axpby(size_t n, double2 a, const double2* x, double2 b, const double2* y, double2* out, cudaStream_t st) {
+  const int blocks = (int)min((size_t)2048, (n + 255) / 256);
+  k_axpby<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(n, a, x, b, y, out);
+}
+
+__global__ void k_herm(int p, double2* A) {
+  const int k = blockIdx.x;
+  double2* Ak = A + (size_t)k * p * p;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    if (i < j) {
+      const double2 a = Ak[j * p + i], b = Ak[i * p + j];
+      const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+      Ak[j * p + i] = h;
+      Ak[i * p + j] = cconj(h);
+    } else if (i == j) {
+      Ak[e].y = 0.0;
+    }
+  }
+}
+void dense_herm(int K, int p, double2* A, cudaStream_t st) { k_herm<<<K, 256, 0, st>>>(p, A); }
+
+__global__ void k_shift_diag(int p, const double2* __restrict__ A, double mu, double2* __restrict__ out) {
+  const int k = blockIdx.x;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    double2 v = A[(size_t)k * p * p + e];
+    if (i == j) v.x -= mu;
+    out[(size_t)k * p * p + e] = v;
+  }
+}
+void dense_shift_diag(int K, int p, const double2* A, double mu, double2* out, cudaStream_t st) {
+  k_shift_diag<<<K, 256, 0, st>>>(p, A, mu, out);
+}
+
+constexpr int DOT_BLOCKS_PER_K = 32;
+__global__ void k_dot(int K, size_t len, const double2* __restrict__ V, const double2* __restrict__ W,
+                      const double* __restrict__ wk, double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int k = blockIdx.y;
+  const size_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const size_t b0 = blockIdx.x * chunk, b1 = min(len, b0 + chunk);
+  double s = 0.0;
+  const double2* v = V + (size_t)k * len;
+  const double2* w = W + (size_t)k * len;
+  for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += v[i].x * w[i].x + v[i].y * w[i].y;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+    if (threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(size_t)k * gridDim.x + blockIdx.x] = sh[0] * (wk ? wk[k] : 1.0);
+}
+int dense_dot(int K, size_t len, const double2* V, const double2* W, const double* wk, double* partials,
+              cudaStream_t st) {
+  dim3 g(DOT_BLOCKS_PER_K, K);
+  k_dot<<<g, 256, 0, st>>>(K, len, V, W, wk, partials);
+  return K * DOT_BLOCKS_PER_K;
+}
+__global__ void k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += p[i];
+    *out = s;
+  }
+}
+void dense_sum_partials(const double* partials, int n, double* out, cudaStream_t st) {
+  k_sum_partials<<<1, 32, 0, st>>>(partials, n, out);
+}
+
+__global__ void k_norms2(size_t len, const double2* __restrict__ V, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int k = blockIdx.x;
+  const double2* v = V + (size_t)k * len;
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < len; i += blockDim.x) s += v[i].x * v[i].x + v[i].y * v[i].y;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+    if (threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = sh[0];
+}
+void dense_norms2(int K, size_t len, const double2* V, double* out, cudaStream_t st) {
+  k_norms2<<<K, 256, 0, st>>>(len, V, out);
+}
+
+void dense_copy(double2* dst, const double2* src, size_t n, cudaStream_t st) {
+  cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+}
+void dense_zero(double2* dst, size_t n, cudaStream_t st) { cudaMemsetAsync(dst, 0, n * sizeof(double2), st); }
+
+__global__ void k_tpa(int p, int n_max, const double* __restrict__ kin, const double* __restrict__ alpha,
+                      const double2* __restrict__ in, double2* __restrict__ out, bool unit_gain) {
+  const int k = blockIdx.y;
+  const size_t tot = (size_t)p * n_max;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n_max), g = (int)(e % n_max);
+    const double a = alpha[(size_t)k * p + i];
+    const double f = (unit_gain ? a : 1.0) / (kin[(size_t)k * n_max + g] + a);
+    out[(size_t)k * tot + e] = cscale(in[(size_t)k * tot + e], f);
+  }
+}
+void dense_tpa(int K, int p, int n_max, const double* kin, const double* alpha, const double2* in, double2* out,
+               bool unit_gain, cudaStream_t st) {
+  dim3 g(64, K);
+  k_tpa<<<g, 256, 0, st>>>(p, n_max, kin, alpha, in, out, unit_gain);
+}
+
+__global__ void k_kinetic_alpha(int p, int n_max, const double* __restrict__ kin, const double2* __restrict__ phi,
+                                double* __restrict__ alpha) {
+  __shared__ double sh[256];
+  const int k = blockIdx.y, i = blockIdx.x;
+  const double2* v = phi + ((size_t)k * p + i) * n_max;
+  const double* kk = kin + (size_t)k * n_max;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < n_max; g += blockDim.x) s += kk[g] * (v[g].x * v[g].x + v[g].y * v[g].y);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+    if (threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) alpha[(size_t)k * p + i] = sh[0];
+}
+void dense_kinetic_alpha(int K, int p, int n_max, const double* kin, const double2* phi, double* alpha,
+                         cudaStream_t st) {
+  dim3 g(p, K);
+  k_kinetic_alpha<<<g, 256, 0, st>>>(p, n_max, kin, phi, alpha);
+}
+
+// E_kin partials: per (k, i) f w_k sum_g kin |c|^2
+__global__ void k_kin_energy(int p, int n_max, const double* __restrict__ kin, const double2* __restrict__ phi,
+                             const double* __restrict__ kw, double occ, double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int k = blockIdx.y, i = blockIdx.x;
+  const double2* v = phi + ((size_t)k * p + i) * n_max;
+  const double* kk = kin + (size_t)k * n_max;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < n_max; g += blockDim.x) s += kk[g] * (v[g].x * v[g].x + v[g].y * v[g].y);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+    if (threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(size_t)k * p + i] = occ * kw[k] * sh[0];
+}
+void dense_kin_energy(int K, int p, int n_max, const double* kin, const double2* phi, const double* kw, double occ,
+                      double* partials, cudaStream_t st) {
+  dim3 g(p, K);
+  k_kin_energy<<<g, 256, 0, st>>>(p, n_max, kin, phi, kw, occ, partials);
+}
+
+__global__ void k_scale_rows(int m, int n, double2* P, const double* __restrict__ d) {
+  const int k = blockIdx.x;
+  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+    const int j = e / m, i = e - j * m;
+    P[(size_t)k * m * n + (size_t)j * m + i] = cscale(P[(size_t)k * m * n + (size_t)j * m + i], d[i]);
+  }
+}
+void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStream_t st) {
+  k_scale_rows<<<K, 256, 0, st>>>(m, n, P, d);
+}
+
+// ----------------------------------------------------------------------------- FOM projected solves
+// One CTA per (m, k): Gaussian elimination with partial pivoting of [A - s_m I | c_m] (q x (q+1),
+// column-major in work), then back substitution; y written to column m of Y (ld q).
+__global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int lda, size_t sA,
+                                const double* __restrict__ s, const double2* __restrict__ C, int ldc, size_t sC,
+                                double2* __restrict__ Y, double2* __restrict__ work, const int* __restrict__ kactive,
+                                int* __restrict__ info) {
+  const int m = blockIdx.x, k = blockIdx.y;
+  if (kactive && !kactive[k]) return;
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  __shared__ int piv;
+  double2* W = work + ((size_t)k * p + m) * (size_t)q * (q + 1);
+  const double2* Ak = A + k * sA;
+  const double sm = s[(size_t)k * p + m];
+  for (size_t e = threadIdx.x; e < (size_t)q * (q + 1); e += blockDim.x) {
+    const int j = (int)(e / q), i = (int)(e - (size_t)j * q);
+    double2 v;
+    if (j < q) {
+      v = Ak[(size_t)j * lda + i];
+      if (i == j) v.x -= sm;
+    } else {
+      v = C[k * sC + (size_t)m * ldc + i];
+    }
+    W[e] = v;
+  }
+  __syncthreads();
+  for (int c = 0; c < q; ++c) {
+    double best = -1.0;
+    int bi = c;
+    for (int i = c + threadIdx.x; i < q; i += blockDim.x) {
+      const double v = cabs2(W[(size_t)c * q + i]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) {
+        const double o = sv[threadIdx.x + h];
+        const int oi = si[threadIdx.x + h];
+        if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+          sv[threadIdx.x] = o;
+          si[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      piv = si[0];
+      if (!(sv[0] > 0.0) && info) info[k * p + m] = c + 1;
+    }
+    __syncthreads();
+    const int r = piv;
+    if (r != c) {
+      for (int j = c + threadIdx.x; j <= q; j += blockDim.x) {
+        const double2 t = W[(size_t)j * q + c];
+        W[(size_t)j * q + c] = W[(size_t)j * q + r];
+        W[(size_t)j * q + r] = t;
+      }
+    }
+    __syncthreads();
+    const double2 d = W[(size_t)c * q + c];
+    const double dd = cabs2(d);
+    const double2 dinv = dd > 0 ? make_double2(d.x / dd, -d.y / dd) : make_double2(0.0, 0.0);
+    const int rows = q - c - 1;
+    for (size_t e = threadIdx.x; e < (size_t)rows * (q - c); e += blockDim.x) {
+      const int jj = (int)(e / rows), ii = (int)(e - (size_t)jj * rows);
+      const int i = c + 1 + ii, j = c + 1 + jj;
+      const double2 f = cmul(W[(size_t)c * q + i], dinv);
+      W[(size_t)j * q + i] = W[(size_t)j * q + i] - cmul(f, W[(size_t)j * q + c]);
+    }
+    __syncthreads();
+  }
+  // back substitution, rhs in column q
+  for (int i = q - 1; i >= 0; --i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = i + 1 + threadIdx.x; j < q; j += blockDim.x) acc = cfma(W[(size_t)j * q + i], W[(size_t)q * q + j], acc);
+    sv[threadIdx.x] = acc.x;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) sv[threadIdx.x] += sv[threadIdx.x + h];
+      __syncthreads();
+    }
+    const double rx = sv[0];
+    __syncthreads();
+    sv[threadIdx.x] = acc.y;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) sv[threadIdx.x] += sv[threadIdx.x + h];
+      __syncthreads();
+    }
+    const double ry = sv[0];
+    if (threadIdx.x == 0) {
+      const double2 d = W[(size_t)i * q + i];
+      const double dd = cabs2(d);
+      const double2 rhs = W[(size_t)q * q + i] - make_double2(rx, ry);
+      W[(size_t)q * q + i] = dd > 0 ? cmul(rhs, make_double2(d.x / dd, -d.y / dd)) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < q; i += blockDim.x) Y[k * sC + (size_t)m * ldc + i] = W[(size_t)q * q + i];
+}
+
+void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s, const double2* C,
+                       int ldc, size_t sC, double2* Y, double2* work, const int* kactive, int* info,
+                       cudaStream_t st) {
+  dim3 g(p, K);
+  k_shifted_solve<<<g, 256, 0, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, work, kactive, info);
+}
+
+__global__ void k_mirror(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ kactive) {
+  const int k = blockIdx.x;
+  if (kactive && !kactive[k]) return;
+  double2* Ak = A + k * sA;
+  for (int e = threadIdx.x; e < q0 * p; e += blockDim.x) {
+    const int jj = e / q0, i = e - jj * q0;  // element (i, q0 + jj) of the upper block
+    Ak[(size_t)i * lda + q0 + jj] = cconj(Ak[(size_t)(q0 + jj) * lda + i]);
+  }
+}
+void fom_mirror(int K, int q0, int p, double2* A, int lda, size_t sA, const int* kactive, cudaStream_t st) {
+  if (q0 > 0) k_mirror<<<K, 256, 0, st>>>(q0, p, A, lda, sA, kactive);
+}
+
+__global__ void k_pad_diag(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ nzero, double big) {
+  const int k = blockIdx.x;
+  double2* Ak = A + k * sA;
+  const int nz = nzero[k];
+  for (int i = threadIdx.x; i < nz && i < p; i += blockDim.x)
+    Ak[(size_t)(q0 + i) * lda + q0 + i] = make_double2(big, 0.0);
+}
+void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, double big, cudaStream_t st) {
+  k_pad_diag<<<K, 64, 0, st>>>(q0, p, A, lda, sA, nzero, big);
+}
+
+// ----------------------------------------------------------------------------- small helpers
+// M[:, i] = U[:, i] w_i^{-1/2} when w_i > tol * lref[k] (and lref[k] > 0), else 0; nzero[k] = dropped count.
+__global__ void k_orth_scale(int p, const double2* __restrict__ U, const double* __restrict__ w,
+                             const double* __restrict__ lref, double tol, double2* __restrict__ M, int* __restrict__ nzero) {
+  const int k = blockIdx.x;
+  const double ref = lref[k];
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p;
+    const double wj = w[(size_t)k * p + j];
+    const bool keep = ref > 0.0 && wj > tol * ref;
+    M[(size_t)k * p * p + e] = keep ? cscale(U[(size_t)k * p * p + e], 1.0 / sqrt(wj)) : make_double2(0.0, 0.0);
+  }
+  if (threadIdx.x == 0 && nzero) {
+    int nz = 0;
+    for (int j = 0; j < p; ++j) {
+      const double wj = w[(size_t)k * p + j];
+      if (!(ref > 0.0 && wj > tol * ref)) ++nz;
+    }
+    nzero[k] = nz;
+  }
+}
+void small_orth_scale(int K, int p, const double2* U, const double* w, const double* lref, double tol, double2* M,
+                      int* nzero, cudaStream_t st) {
+  k_orth_scale<<<K, 256, 0, st>>>(p, U, w, lref, tol, M, nzero);
+}
+
+__global__ void k_put_herm_block(int p, const double2* __restrict__ src, double2* A, int lda, size_t sA, int q0) {
+  const int k = blockIdx.x;
+  const double2* S = src + (size_t)k * p * p;
+  double2* Ak = A + k * sA;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    const double2 a = S[j * p + i], b = S[i * p + j];
+    Ak[(size_t)(q0 + j) * lda + q0 + i] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+}
+void small_put_herm_block(int K, int p, const double2* src, double2* A, int lda, size_t sA, int q0, cudaStream_t st) {
+  k_put_herm_block<<<K, 256, 0, st>>>(p, src, A, lda, sA, q0);
+}
+
+__global__ void k_take_y(int q, int qcap, int p, const double2* __restrict__ Y, double2* __restrict__ Yf,
+                         const int* __restrict__ take) {
+  const int k = blockIdx.x;
+  if (!take[k]) return;
+  for (int e = threadIdx.x; e < qcap * p; e += blockDim.x) {
+    const int j = e / qcap, i = e - j * qcap;
+    const size_t o = (size_t)k * qcap * p + (size_t)j * qcap + i;
+    Yf[o] = i < q ? Y[o] : make_double2(0.0, 0.0);
+  }
+}
+void small_take_y(int K, int q, int qcap, int p, const double2* Y, double2* Yf, const int* take, cudaStream_t st) {
+  k_take_y<<<K, 256, 0, st>>>(q, qcap, p, Y, Yf, take);
+}
+
+__global__ void k_max_eval(int K, int p, const double* __restrict__ w, double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double m = w[(size_t)k * p];
+  for (int i = 1; i < p; ++i) m = fmax(m, w[(size_t)k * p + i]);
+  out[k] = m;
+}
+void small_max_eval(int K, int p, const double* w, double* out, cudaStream_t st) {
+  k_max_eval<<<(K + 127) / 128, 128, 0, st>>>(K, p, w, out);
+}
+
+__global__ void k_conj_transpose(int p, const double2* __restrict__ A, double2* __restrict__ out) {
+  const int k = blockIdx.x;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    out[(size_t)k * p * p + e] = cconj(A[(size_t)k * p * p + (size_t)i * p + j]);
+  }
+}
+void small_conj_transpose(int K, int p, const double2* A, double2* out, cudaStream_t st) {
+  k_conj_transpose<<<K, 256, 0, st>>>(p, A, out);
+}
+
+__global__ void k_add_herm(int p, const double2* __restrict__ A, double sc, double2* __restrict__ out) {
+  const int k = blockIdx.x;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    const double2 a = A[(size_t)k * p * p + e], b = A[(size_t)k * p * p + (size_t)i * p + j];
+    out[(size_t)k * p * p + e] = make_double2(sc * (a.x + b.x), sc * (a.y - b.y));
+  }
+}
+void small_add_herm(int K, int p, const double2* A, double s, double2* out, cudaStream_t st) {
+  k_add_herm<<<K, 256, 0, st>>>(p, A, s, out);
+}
+
+__global__ void k_sqrt_vals(int n, const double* __restrict__ w, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sqrt(w[i]);
+}
+void small_sqrt_vals(int K, int p, const double* w, double* out, cudaStream_t st) {
+  k_sqrt_vals<<<(K * p + 127) / 128, 128, 0, st>>>(K * p, w, out);
+}
+
+}  // namespace eacg

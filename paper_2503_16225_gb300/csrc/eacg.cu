@@ -1,0 +1,1444 @@
+// libeacg C ABI and host-side driver of the eARCG iteration (arXiv 2503.16225).
+//
+// The driver only sequences kernels and takes the scalar decisions of the step-size
+// search (Algorithm 2), the CG parameter (Sec. 3.4) and the per-k stopping of the block
+// FOM (Algorithm 4); every vector and matrix operation runs in the kernels of
+// grid_kernels.cu and dense_kernels.cu on the system's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/eacg.h"
+#include "kernels.h"
+
+using namespace eacg;
+
+namespace {
+
+const double2 ONE = {1.0, 0.0};
+const double2 ZERO = {0.0, 0.0};
+const double2 MONE = {-1.0, 0.0};
+inline double2 cr(double x) { return make_double2(x, 0.0); }
+
+struct Status {
+  eacg_status code = EACG_OK;
+};
+
+}  // namespace
+
+namespace eacg {
+void small_orth_scale(int K, int p, const double2* U, const double* w, const double* lref, double tol, double2* M,
+                      int* nzero, cudaStream_t st);
+void small_put_herm_block(int K, int p, const double2* src, double2* A, int lda, size_t sA, int q0, cudaStream_t st);
+void small_take_y(int K, int q, int qcap, int p, const double2* Y, double2* Yf, const int* take, cudaStream_t st);
+void small_max_eval(int K, int p, const double* w, double* out, cudaStream_t st);
+void small_conj_transpose(int K, int p, const double2* A, double2* out, cudaStream_t st);
+void small_add_herm(int K, int p, const double2* A, double s, double2* out, cudaStream_t st);
+void small_sqrt_vals(int K, int p, const double* w, double* out, cudaStream_t st);
+}  // namespace eacg
+
+struct eacg_system {
+  // ---- model
+  int N = 0, K = 0, p = 0, natoms = 0, npa = 0, nproj = 0, hartree = 1, xc = 1;
+  double a = 0, omega = 0, b = 0, ecut = 0, occ = 2, width = 0.7, thr = 0;
+  std::vector<double> kfrac, kw, pos, Z, rc, D, dvec;
+  eacg_params prm{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  // ---- basis
+  std::vector<int> nk;
+  int n_max = 0, ncols = 0, ny = 0;
+  GridCtx g{};
+  size_t blk = 0;  // elements of one [K][p][n_max] block
+  // ---- device allocations (freed in destroy)
+  std::vector<void*> allocs;
+  int *d_nk = nullptr, *d_m = nullptr, *d_xmap = nullptr, *d_colfy = nullptr, *d_colfz = nullptr, *d_ylist = nullptr;
+  double *d_kfrac = nullptr, *d_kin = nullptr, *d_kw = nullptr, *d_pos = nullptr, *d_Z = nullptr, *d_rc = nullptr;
+  double *d_dvec = nullptr, *d_bw = nullptr;
+  double2* d_tw64 = nullptr;
+  float2* d_tw32 = nullptr;
+  double *d_vloc = nullptr, *d_vtot = nullptr, *d_rho = nullptr, *d_vh = nullptr, *d_partial = nullptr;
+  float* d_vtot32 = nullptr;
+  double2* d_fft3 = nullptr;
+  double2 *d_B = nullptr, *d_P = nullptr, *d_P2 = nullptr;
+  void* d_tbuf = nullptr;
+  int rho_groups = 1;
+  // blocks
+  double2 *phi = nullptr, *hphi = nullptr, *res = nullptr, *eta = nullptr, *gv = nullptr, *teta = nullptr,
+          *tg = nullptr, *psi_t = nullptr, *phi_t = nullptr, *hphi_t = nullptr, *res_t = nullptr, *teta_t = nullptr,
+          *tmp1 = nullptr, *tmp2 = nullptr, *tmp3 = nullptr, *Xb = nullptr, *Cb = nullptr, *fvt = nullptr,
+          *fwt = nullptr;
+  // small [K][p][p]
+  double2 *lam = nullptr, *lam_t = nullptr, *sm1 = nullptr, *sm2 = nullptr, *sm3 = nullptr, *evec = nullptr,
+          *evec_t = nullptr, *sinv_t = nullptr, *sig = nullptr, *sigv = nullptr, *sigvh = nullptr;
+  double *eval = nullptr, *eval_t = nullptr, *sval = nullptr, *alpha = nullptr, *sqd = nullptr, *lref = nullptr;
+  double2* cn_work = nullptr;
+  size_t cn_elems = 0;
+  double* d_red = nullptr;    // reduction scratch
+  double* d_esum = nullptr;   // block sums of the grid energy terms
+  double* d_out = nullptr;    // scalars copied to the host
+  double* h_out = nullptr;    // pinned
+  int *d_kactive = nullptr, *d_nzero = nullptr, *d_info = nullptr, *d_take = nullptr;
+  int* h_int = nullptr;       // pinned
+  // FOM Krylov storage (grown on demand)
+  int qcap = 0;
+  double2 *fV = nullptr, *fW = nullptr, *fA = nullptr, *fC = nullptr, *fY = nullptr, *fYt = nullptr, *fYf = nullptr,
+          *fwork = nullptr;
+  size_t fwork_elems = 0;
+  // ---- iteration state
+  int fresh = 1, have_psi = 0, phase = 0, iter = 0, warm_iter = 0, cur_prec = 0;
+  double E = 0, rnorm = 0, tau = 1, rg = 0;
+  double eterms[5] = {0, 0, 0, 0, 0};
+  long long h_apps = 0;
+  int last_fom_max = 0;
+  int ls_total = 0;
+};
+
+// ============================================================================ helpers
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      s->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return EACG_ECUDA;                                                          \
+    }                                                                             \
+  } while (0)
+#define CKL(s)                                                                    \
+  do {                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                          \
+    if (e_ != cudaSuccess) {                                                      \
+      (s)->err = std::string("kernel launch: ") + cudaGetErrorString(e_);         \
+      return EACG_ECUDA;                                                          \
+    }                                                                             \
+  } while (0)
+#define TRY(x)                        \
+  do {                                            \
+    eacg_status st_ = (x);                        \
+    if (st_ != EACG_OK) return st_;               \
+  } while (0)
+
+template <typename P>
+static eacg_status dalloc(eacg_system* s, P** ptr, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+    return EACG_ENOMEM;
+  }
+  cudaMemsetAsync(p, 0, bytes, s->st);
+  s->allocs.push_back(p);
+  *ptr = reinterpret_cast<P*>(p);
+  return EACG_OK;
+}
+
+static void dfree(eacg_system* s, void* p) {
+  if (!p) return;
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+  if (it != s->allocs.end()) s->allocs.erase(it);
+  cudaFree(p);
+}
+
+static bool make_plan(int N, FftPlan* pl) {
+  std::memset(pl, 0, sizeof(*pl));
+  pl->N = N;
+  int n = N, np = 0;
+  int rad[16];
+  while (n % 4 == 0) {
+    rad[np++] = 4;
+    n /= 4;
+  }
+  while (n % 2 == 0) {
+    rad[np++] = 2;
+    n /= 2;
+  }
+  while (n % 3 == 0) {
+    rad[np++] = 3;
+    n /= 3;
+  }
+  while (n % 5 == 0) {
+    rad[np++] = 5;
+    n /= 5;
+  }
+  if (n != 1 || np > 8 || np == 0) return false;
+  bool h3 = false, h5 = false, h4 = false;
+  for (int i = 0; i < np; ++i) {
+    h3 |= rad[i] == 3;
+    h5 |= rad[i] == 5;
+    h4 |= rad[i] == 4;
+  }
+  if (h3 && h5) return false;
+  int E;
+  if (h5)
+    E = 20;
+  else if (h3)
+    E = 12;
+  else
+    E = (N >= 32) ? 8 : 4;
+  if (!h4 && E == 20) E = 20;
+  if (N % E != 0) {
+    if (!h3 && !h5 && N % 4 == 0)
+      E = 4;
+    else
+      return false;
+  }
+  pl->E = E;
+  pl->TPL = N / E;
+  pl->npass = np;
+  int ns = 1;
+  for (int i = 0; i < np; ++i) {
+    pl->radix[i] = rad[i];
+    pl->ns[i] = ns;
+    ns *= rad[i];
+  }
+  return true;
+}
+
+static eacg_status sync_read(eacg_system* s, int ndouble) {
+
+
+  CK(cudaMemcpyAsync(s->h_out, s->d_out, sizeof(double) * ndouble, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return EACG_OK;
+}
+
+// ============================================================================ model set-up
+static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::string* why) {
+  if (!m) {
+    *why = "model is NULL";
+    return EACG_EINVAL;
+  }
+  if (!(m->a > 0) || m->N < 8 || m->N > 96 || m->nbands < 1 || m->nk < 1 || !(m->ecut > 0) || m->natoms < 0) {
+    *why = "invalid cell, grid, band, k-point or cutoff";
+    return EACG_EINVAL;
+  }
+  if (m->natoms > 0 && (!m->pos || !m->Z || !m->rc)) {
+    *why = "atoms without positions / charges / radii";
+    return EACG_EINVAL;
+  }
+  if (!(m->nproj_per_atom == 0 || m->nproj_per_atom == 1 || m->nproj_per_atom == 4)) {
+    *why = "nproj_per_atom must be 0, 1 or 4";
+    return EACG_EINVAL;
+  }
+  if (m->nproj_per_atom > 0 && m->natoms > 0 && !m->D) {
+    *why = "projectors without couplings";
+    return EACG_EINVAL;
+  }
+  if (!m->kfrac || !m->kweight) {
+    *why = "k-points missing";
+    return EACG_EINVAL;
+  }
+  if (m->nbands > 64) {
+    *why = "nbands > 64 is not supported by this build";
+    return EACG_EUNSUPPORTED;
+  }
+  FftPlan pl;
+  if (!make_plan(m->N, &pl)) {
+    *why = "grid size N must be 2^a 3^b or 2^a 5^c";
+    return EACG_EUNSUPPORTED;
+  }
+  if (prm && (!(prm->mu > 0) || prm->max_ls < 1 || prm->max_fom < 1)) {
+    *why = "invalid parameters";
+    return EACG_EINVAL;
+  }
+  return EACG_OK;
+}
+
+extern "C" void eacg_default_params(eacg_params* prm) {
+  if (!prm) return;
+  prm->mu = 0.01;
+  prm->res_tol = 1e-8;
+  prm->fom_rtol = 2.5e-2;
+  prm->delta = 0.05;
+  prm->sigma = 0.1;
+  prm->gamma = 0.5;
+  prm->eps = 1e-12;
+  prm->warm_res = 1e-2;
+  prm->switch_res = 1e-3;
+  prm->max_outer = 300;
+  prm->max_warm = 100;
+  prm->max_fom = 50;
+  prm->max_ls = 30;
+  prm->precision = 0;
+}
+
+static double sphere_volume_estimate(const eacg_model* m) {
+  const double b = 2.0 * M_PI / m->a;
+  const double r = std::sqrt(2.0 * m->ecut) / b + 1.0;
+  return 4.0 / 3.0 * M_PI * r * r * r;
+}
+
+extern "C" size_t eacg_bytes_required(const eacg_model* m, const eacg_params* prm, size_t* fom_per_iter) {
+  std::string why;
+  if (validate(m, prm, &why) != EACG_OK) return 0;
+  const size_t N3 = (size_t)m->N * m->N * m->N;
+  const size_t nmax = (size_t)sphere_volume_estimate(m) + 64;
+  const size_t K = m->nk, p = m->nbands;
+  const size_t blk = K * p * nmax * 16;
+  const size_t ncols = (size_t)(M_PI * std::pow(std::sqrt(2.0 * m->ecut) / (2.0 * M_PI / m->a) + 1.0, 2)) + 16;
+  const size_t tb = K * p * m->N * ncols * 16;
+  const size_t nproj = (size_t)m->natoms * m->nproj_per_atom;
+  size_t tot = 17 * blk + tb + N3 * (8 * 6 + 16 + 4) + K * nproj * nmax * 16 + 8 * N3 * 8 + (64 << 20);
+  if (fom_per_iter) *fom_per_iter = 2 * blk + K * p * p * 16 * 8;
+  return tot;
+}
+
+static eacg_status build_basis(eacg_system* s) {
+  const int N = s->N, K = s->K;
+  int* d_rowoff = nullptr;
+  int* d_colmark = nullptr;
+  int* d_colidx = nullptr;
+  int* d_scal = nullptr;
+  TRY(dalloc(s, &d_rowoff, sizeof(int) * (size_t)K * (N * N + 1)));
+  TRY(dalloc(s, &d_colmark, sizeof(int) * N * N));
+  TRY(dalloc(s, &d_colidx, sizeof(int) * N * N));
+  TRY(dalloc(s, &d_scal, sizeof(int) * 4));
+  TRY(dalloc(s, &s->d_nk, sizeof(int) * K));
+  grid_build_sphere(N, K, s->d_kfrac, s->thr, s->b, 0, s->d_nk, d_rowoff, nullptr, nullptr, d_colmark, s->st);
+  CKL(s);
+  s->nk.assign(K, 0);
+  CK(cudaMemcpyAsync(s->nk.data(), s->d_nk, sizeof(int) * K, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  s->n_max = *std::max_element(s->nk.begin(), s->nk.end());
+  if (s->n_max <= 0) {
+    s->err = "empty basis (cutoff below the smallest |k+G|^2/2)";
+    return EACG_EINVAL;
+  }
+  for (int k = 0; k < K; ++k) {
+    if (s->nk[k] < s->p) {
+      s->err = "fewer plane waves than bands at some k-point";
+      return EACG_EINVAL;
+    }
+  }
+  // the sphere must sit strictly inside the grid's frequency box
+  {
+    double kmax = 0;
+    for (double v : s->kfrac) kmax = std::max(kmax, std::fabs(v));
+    if (std::sqrt(s->thr) + kmax >= N / 2 - 0.5) {
+      s->err = "grid too small for the cutoff sphere (N must exceed 2 |k+G|_max / b + 1)";
+      return EACG_EINVAL;
+    }
+  }
+  TRY(dalloc(s, &s->d_m, sizeof(int) * 3 * (size_t)K * s->n_max));
+  TRY(dalloc(s, &s->d_kin, sizeof(double) * (size_t)K * s->n_max));
+  grid_build_sphere(N, K, s->d_kfrac, s->thr, s->b, s->n_max, s->d_nk, d_rowoff, s->d_m, s->d_kin, d_colmark, s->st);
+  CKL(s);
+  TRY(dalloc(s, &s->d_colfy, sizeof(int) * N * N));
+  TRY(dalloc(s, &s->d_colfz, sizeof(int) * N * N));
+  TRY(dalloc(s, &s->d_ylist, sizeof(int) * N));
+  grid_columns(N, d_colmark, d_colidx, s->d_colfy, s->d_colfz, d_scal, s->d_ylist, d_scal + 1, s->st);
+  CKL(s);
+  int hs[2];
+  CK(cudaMemcpyAsync(hs, d_scal, sizeof(int) * 2, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  s->ncols = hs[0];
+  s->ny = hs[1];
+  TRY(dalloc(s, &s->d_xmap, sizeof(int) * (size_t)K * s->ncols * N));
+  grid_xmap(N, K, s->n_max, s->d_nk, s->d_m, d_colidx, s->ncols, s->d_xmap, s->st);
+  CKL(s);
+  CK(cudaStreamSynchronize(s->st));
+  dfree(s, d_rowoff);
+  dfree(s, d_colmark);
+  dfree(s, d_colidx);
+  dfree(s, d_scal);
+  return EACG_OK;
+}
+
+static eacg_status build_potential_and_projectors(eacg_system* s) {
+  const int N = s->N;
+  const size_t N3 = (size_t)N * N * N;
+  TRY(dalloc(s, &s->d_fft3, sizeof(double2) * N3));
+  TRY(dalloc(s, &s->d_vloc, sizeof(double) * N3));
+  TRY(dalloc(s, &s->d_vtot, sizeof(double) * N3));
+  TRY(dalloc(s, &s->d_vtot32, sizeof(float) * N3));
+  TRY(dalloc(s, &s->d_vh, sizeof(double) * N3));
+  TRY(dalloc(s, &s->d_rho, sizeof(double) * N3));
+  grid_vloc_g(N, s->b, s->omega, s->natoms, s->d_pos, s->d_Z, s->d_rc, s->d_fft3, s->st);
+  CKL(s);
+  grid_fft3(s->g, s->d_fft3, true, s->st);
+  grid_complex_real_part(s->d_fft3, s->d_vloc, N3, s->st);
+  CKL(s);
+  // initial potential: local part only (rho = 0), FP64 and FP32 copies
+  {
+    double* esum = nullptr;
+    TRY(dalloc(s, &esum, sizeof(double) * 3 * 256));
+    grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, 0, 0, s->d_vtot, s->d_vtot32, esum, s->st);
+    CKL(s);
+    CK(cudaStreamSynchronize(s->st));
+    dfree(s, esum);
+  }
+  if (s->nproj > 0) {
+    TRY(dalloc(s, &s->d_B, sizeof(double2) * (size_t)s->K * s->nproj * s->n_max));
+    TRY(dalloc(s, &s->d_P, sizeof(double2) * (size_t)s->K * s->nproj * 64));
+    TRY(dalloc(s, &s->d_P2, sizeof(double2) * (size_t)s->K * s->nproj * 64));
+    grid_projectors(s->K, s->n_max, s->d_nk, s->d_m, s->d_kfrac, s->b, s->omega, s->natoms, s->d_pos, s->npa,
+                    s->width, s->d_B, s->st);
+    CKL(s);
+  }
+  return EACG_OK;
+}
+
+static eacg_status alloc_work(eacg_system* s) {
+  const int K = s->K, p = s->p, N = s->N;
+  s->blk = (size_t)K * p * s->n_max;
+  const size_t bb = sizeof(double2) * s->blk;
+  double2** blocks[] = {&s->phi, &s->hphi, &s->res, &s->eta, &s->gv, &s->teta, &s->tg, &s->psi_t, &s->phi_t,
+                        &s->hphi_t, &s->res_t, &s->teta_t, &s->tmp1, &s->tmp2, &s->tmp3, &s->Xb, &s->Cb, &s->fvt, &s->fwt};
+  for (auto b : blocks) TRY(dalloc(s, b, bb));
+  const size_t sp = sizeof(double2) * (size_t)K * p * p;
+  double2** smalls[] = {&s->lam, &s->lam_t, &s->sm1, &s->sm2, &s->sm3, &s->evec, &s->evec_t, &s->sinv_t,
+                        &s->sig, &s->sigv, &s->sigvh};
+  for (auto m : smalls) TRY(dalloc(s, m, sp));
+  double** vecs[] = {&s->eval, &s->eval_t, &s->sval, &s->alpha, &s->sqd, &s->lref};
+  for (auto v : vecs) TRY(dalloc(s, v, sizeof(double) * (size_t)K * p));
+  // tbuf: one FP64 complex value per (band, jx, column)
+  TRY(dalloc(s, &s->d_tbuf, sizeof(double2) * (size_t)K * p * N * s->ncols));
+  // rho groups: enough CTAs to fill the GPU
+  s->rho_groups = std::max(1, std::min(K * p, (2 * 152 + N - 1) / N));
+  TRY(dalloc(s, &s->d_partial, sizeof(double) * (size_t)s->rho_groups * N * N * N));
+  TRY(dalloc(s, &s->d_bw, sizeof(double) * (size_t)K * p));
+  {
+    std::vector<double> bw((size_t)K * p);
+    for (int k = 0; k < K; ++k)
+      for (int i = 0; i < p; ++i) bw[(size_t)k * p + i] = s->kw[k] * s->occ / s->omega;
+    CK(cudaMemcpyAsync(s->d_bw, bw.data(), sizeof(double) * bw.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+  }
+  const size_t cnw = std::max(dense_cn_work(K, s->n_max, 64 * 64, 1),
+                              dense_cn_work(K, s->n_max, std::max(p, s->nproj), p));
+  s->cn_elems = std::max(cnw, (size_t)K * 4096);
+  TRY(dalloc(s, &s->cn_work, sizeof(double2) * s->cn_elems));
+  TRY(dalloc(s, &s->d_red, sizeof(double) * (size_t)(K * 64 + 4096)));
+  TRY(dalloc(s, &s->d_out, sizeof(double) * 4096));
+  TRY(dalloc(s, &s->d_esum, sizeof(double) * 3 * 256));
+  TRY(dalloc(s, &s->d_kactive, sizeof(int) * K));
+  TRY(dalloc(s, &s->d_nzero, sizeof(int) * K));
+  TRY(dalloc(s, &s->d_info, sizeof(int) * (size_t)K * 64));
+  TRY(dalloc(s, &s->d_take, sizeof(int) * K));
+  {
+
+
+    CK(cudaMallocHost(&s->h_out, sizeof(double) * 4096));
+    CK(cudaMallocHost(&s->h_int, sizeof(int) * 4 * K + 64));
+  }
+  return EACG_OK;
+}
+
+// Krylov storage for q columns per k; grows by doubling and keeps the contents.
+static eacg_status copy_cols(eacg_system* s, double2* dst, int ldd, size_t sd, const double2* src, int lds, size_t ss,
+                             int rows, int cols) {
+  if (!src || rows <= 0 || cols <= 0) return EACG_OK;
+  for (int k = 0; k < s->K; ++k) {
+    CK(cudaMemcpy2DAsync(dst + k * sd, sizeof(double2) * ldd, src + k * ss, sizeof(double2) * lds,
+                         sizeof(double2) * rows, cols, cudaMemcpyDeviceToDevice, s->st));
+  }
+  return EACG_OK;
+}
+
+static eacg_status fom_reserve(eacg_system* s, int qneed) {
+  if (qneed <= s->qcap) return EACG_OK;
+  const int K = s->K, p = s->p, nm = s->n_max;
+  int qc = std::max(s->qcap, std::min(s->prm.max_fom, 6) * p);
+  while (qc < qneed) qc *= 2;
+  qc = std::min(qc, std::max(qneed, s->prm.max_fom * p));
+  double2 *nV, *nW, *nA, *nC, *nY, *nYt, *nYf;
+  TRY(dalloc(s, &nV, sizeof(double2) * (size_t)K * qc * nm));
+  TRY(dalloc(s, &nW, sizeof(double2) * (size_t)K * qc * nm));
+  TRY(dalloc(s, &nA, sizeof(double2) * (size_t)K * qc * qc));
+  TRY(dalloc(s, &nC, sizeof(double2) * (size_t)K * qc * p));
+  TRY(dalloc(s, &nY, sizeof(double2) * (size_t)K * qc * p));
+  TRY(dalloc(s, &nYt, sizeof(double2) * (size_t)K * qc * p));
+  TRY(dalloc(s, &nYf, sizeof(double2) * (size_t)K * qc * p));
+  const int oc = s->qcap;
+  if (oc > 0) {
+    TRY(copy_cols(s, nV, nm, (size_t)qc * nm, s->fV, nm, (size_t)oc * nm, nm, oc));
+    TRY(copy_cols(s, nW, nm, (size_t)qc * nm, s->fW, nm, (size_t)oc * nm, nm, oc));
+    TRY(copy_cols(s, nA, qc, (size_t)qc * qc, s->fA, oc, (size_t)oc * oc, oc, oc));
+    TRY(copy_cols(s, nC, qc, (size_t)qc * p, s->fC, oc, (size_t)oc * p, oc, p));
+    TRY(copy_cols(s, nY, qc, (size_t)qc * p, s->fY, oc, (size_t)oc * p, oc, p));
+    TRY(copy_cols(s, nYt, qc, (size_t)qc * p, s->fYt, oc, (size_t)oc * p, oc, p));
+    TRY(copy_cols(s, nYf, qc, (size_t)qc * p, s->fYf, oc, (size_t)oc * p, oc, p));
+  }
+  CK(cudaStreamSynchronize(s->st));
+  dfree(s, s->fV);
+  dfree(s, s->fW);
+  dfree(s, s->fA);
+  dfree(s, s->fC);
+  dfree(s, s->fY);
+  dfree(s, s->fYt);
+  dfree(s, s->fYf);
+  s->fV = nV;
+  s->fW = nW;
+  s->fA = nA;
+  s->fC = nC;
+  s->fY = nY;
+  s->fYt = nYt;
+  s->fYf = nYf;
+  s->qcap = qc;
+  const size_t fw = (size_t)K * p * qc * (qc + 1);
+  if (fw > s->fwork_elems) {
+    dfree(s, s->fwork);
+    s->fwork = nullptr;
+    TRY(dalloc(s, &s->fwork, sizeof(double2) * fw));
+    s->fwork_elems = fw;
+  }
+  const size_t cnw = std::max(dense_cn_work(K, nm, qc, p), (size_t)K * 4096);
+  if (cnw > s->cn_elems) {
+    dfree(s, s->cn_work);
+    s->cn_work = nullptr;
+    TRY(dalloc(s, &s->cn_work, sizeof(double2) * cnw));
+    s->cn_elems = cnw;
+  }
+  return EACG_OK;
+}
+
+// ============================================================================ operators
+// out = H in with the current potential (prec 0: FP64 transforms, 1: FP32).
+static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out, int prec, const int* kactive) {
+  const int nb = s->K * s->p;
+  grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st);
+  grid_plane_h(s->g, prec, s->d_tbuf, prec ? (const void*)s->d_vtot32 : (const void*)s->d_vtot, nb, kactive, s->st);
+  const double N3 = (double)s->N * s->N * s->N;
+  grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st);
+  CKL(s);
+  if (s->nproj > 0) {
+    const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
+    dense_gemm_cn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np, ONE,
+                  ZERO, s->cn_work, kactive, s->st);
+    dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
+    dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
+    dense_gemm_nn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm, nm, ONE,
+                  ONE, kactive, s->st);
+    CKL(s);
+  }
+  s->h_apps += (long long)s->K * s->p;
+  return EACG_OK;
+}
+
+// rho of an orthonormal block and the potential built from it; E_loc, E_H, E_x into d_red[0..2].
+static eacg_status density_and_potential(eacg_system* s, const double2* phi, int prec) {
+  const int nb = s->K * s->p;
+  const int N = s->N;
+  const size_t N3 = (size_t)N * N * N;
+  grid_xpass_inv(s->g, prec, phi, s->d_tbuf, nb, nullptr, s->st);
+  grid_plane_rho(s->g, prec, s->d_tbuf, nb, s->rho_groups, s->d_bw, s->d_partial, s->st);
+  grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
+  CKL(s);
+  if (s->hartree) {
+    grid_real_to_complex(s->d_rho, s->d_fft3, N3, s->st);
+    grid_fft3(s->g, s->d_fft3, false, s->st);
+    grid_hartree_scale(s->d_fft3, N, s->b, s->st);
+    grid_fft3(s->g, s->d_fft3, true, s->st);
+    grid_complex_real_part(s->d_fft3, s->d_vh, N3, s->st);
+    CKL(s);
+  }
+  const int nblk = grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, s->hartree, s->xc, s->d_vtot, s->d_vtot32,
+                                    s->d_esum, s->st);
+  CKL(s);
+  return (nblk == 256) ? EACG_OK : EACG_ECUDA;
+}
+
+// ============================================================================ reductions to host
+// Sum of the 3 * nblk strided block sums of k_vtot_energy, done on the host after one copy.
+static eacg_status fetch_grid_energies(eacg_system* s, double* eloc, double* eh, double* ex) {
+  const int nblk = 256;
+
+
+  CK(cudaMemcpyAsync(s->h_out, s->d_esum, sizeof(double) * 3 * nblk, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  double a = 0, b = 0, c = 0;
+  for (int i = 0; i < nblk; ++i) {
+    a += s->h_out[3 * i];
+    b += s->h_out[3 * i + 1];
+    c += s->h_out[3 * i + 2];
+  }
+  const double dv = s->omega / ((double)s->N * s->N * s->N);
+  *eloc = a * dv;
+  *eh = b * dv;
+  *ex = c * dv;
+  return EACG_OK;
+}
+
+// weighted pairing <V, W> = sum_k w_k Re tr(V_k^* W_k) into d_out[slot]
+static void pairing_dev(eacg_system* s, const double2* V, const double2* W, int slot, bool weighted) {
+  const int np = dense_dot(s->K, (size_t)s->p * s->n_max, V, W, weighted ? s->d_kw : nullptr, s->d_red, s->st);
+  dense_sum_partials(s->d_red, np, s->d_out + slot, s->st);
+}
+
+// ============================================================================ evaluation
+struct EvalOut {
+  double E, rnorm, terms[5];
+};
+
+// Density, potential, H phi, Lambda, R and the energy at an orthonormal phi.
+static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, double2* res, double2* lam, int prec,
+                            EvalOut* out) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  TRY(density_and_potential(s, phi, prec));
+  TRY(apply_H_block(s, phi, hphi, prec, nullptr));
+  // Lambda = herm(Phi^* H Phi)
+  dense_gemm_cn(K, nm, p, p, phi, (size_t)p * nm, nm, hphi, (size_t)p * nm, nm, lam, (size_t)p * p, p, ONE, ZERO,
+                s->cn_work, nullptr, s->st);
+  dense_herm(K, p, lam, s->st);
+  // R = H Phi - Phi Lambda
+  dense_copy(res, hphi, s->blk, s->st);
+  dense_gemm_nn(K, nm, p, p, phi, (size_t)p * nm, nm, lam, (size_t)p * p, p, res, (size_t)p * nm, nm, MONE, ONE,
+                nullptr, s->st);
+  CKL(s);
+  // kinetic energy partials -> d_red[0..K*p), summed into d_out[0]
+  dense_kin_energy(K, p, nm, s->d_kin, phi, s->d_kw, s->occ, s->d_red, s->st);
+  dense_sum_partials(s->d_red, K * p, s->d_out + 0, s->st);
+  // nonlocal energy: sum_k w_k f sum D |P|^2 = pairing of unscaled and scaled projections
+  if (s->nproj > 0) {
+    const int npp = dense_dot(K, (size_t)s->nproj * p, s->d_P2, s->d_P, s->d_kw, s->d_red, s->st);
+    dense_sum_partials(s->d_red, npp, s->d_out + 1, s->st);
+  } else {
+    cudaMemsetAsync(s->d_out + 1, 0, sizeof(double), s->st);
+  }
+  // ||R||^2 (unweighted)
+  pairing_dev(s, res, res, 2, false);
+  CKL(s);
+  TRY(sync_read(s, 3));
+  const double ekin = s->h_out[0];
+  const double enl = s->occ * s->h_out[1];
+  const double r2 = s->h_out[2];
+  double eloc, eh, ex;
+  TRY(fetch_grid_energies(s, &eloc, &eh, &ex));
+  out->terms[0] = ekin;
+  out->terms[1] = eloc;
+  out->terms[2] = s->hartree ? eh : 0.0;
+  out->terms[3] = s->xc ? ex : 0.0;
+  out->terms[4] = enl;
+  out->E = ekin + eloc + out->terms[2] + out->terms[3] + enl;
+  out->rnorm = std::sqrt(std::max(r2, 0.0));
+  if (!std::isfinite(out->E) || !std::isfinite(out->rnorm)) {
+    s->err = "non-finite energy or residual";
+    return EACG_ENAN;
+  }
+  return EACG_OK;
+}
+
+// out = pf(psi) = psi V D^{-1/2} V^H; keeps the eigenpairs of psi^* psi and S^{-1}.
+static eacg_status polar(eacg_system* s, const double2* psi, double2* out, double* ev, double2* evv, double2* sinv) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  dense_gemm_cn(K, nm, p, p, psi, (size_t)p * nm, nm, psi, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, ONE, ZERO,
+                s->cn_work, nullptr, s->st);
+  dense_heig(K, p, s->sm1, (size_t)p * p, ev, evv, nullptr, s->st);
+  dense_eig_func(K, p, evv, ev, -0.5, 0.0, sinv, nullptr, s->st);
+  dense_gemm_nn(K, nm, p, p, psi, (size_t)p * nm, nm, sinv, (size_t)p * p, p, out, (size_t)p * nm, nm, ONE, ZERO,
+                nullptr, s->st);
+  CKL(s);
+  return EACG_OK;
+}
+
+// ============================================================================ directions
+// Warm-up direction g = Z - Phi herm(Phi^* Z), Z = TPA (unit gain) applied to R.
+static eacg_status precond_gradient(eacg_system* s, const double2* phi, const double2* res, double2* g) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  dense_kinetic_alpha(K, p, nm, s->d_kin, phi, s->alpha, s->st);
+  dense_tpa(K, p, nm, s->d_kin, s->alpha, res, s->tmp1, true, s->st);
+  dense_gemm_cn(K, nm, p, p, phi, (size_t)p * nm, nm, s->tmp1, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, ONE,
+                ZERO, s->cn_work, nullptr, s->st);
+  dense_herm(K, p, s->sm1, s->st);
+  dense_copy(g, s->tmp1, s->blk, s->st);
+  dense_gemm_nn(K, nm, p, p, phi, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, g, (size_t)p * nm, nm, MONE, ONE,
+                nullptr, s->st);
+  CKL(s);
+  return EACG_OK;
+}
+
+// Rank-revealing orthonormalisation of R (n x p per k) against the first q columns of V
+// (Algorithm 4, reading: two projections, eigen-decomposition of the Gram matrix with
+// relative drop tolerance 1e-12 against the Gram of R before projection, second pass).
+// Result into out (n x p per k, dropped directions as leading zero columns), nzero[k].
+static eacg_status orthonormalise(eacg_system* s, double2* R, const double2* V, int q, size_t sV, double2* out,
+                                  const int* kactive) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  const size_t sb = (size_t)p * nm;
+  // reference: largest Gram eigenvalue before projection
+  dense_gemm_cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
+  dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
+  small_max_eval(K, p, s->sval, s->lref, s->st);
+  if (q > 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      dense_gemm_cn(K, nm, q, p, V, sV, nm, R, sb, nm, s->fYt, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work,
+                    kactive, s->st);
+      dense_gemm_nn(K, nm, q, p, V, sV, nm, s->fYt, (size_t)s->qcap * p, s->qcap, R, sb, nm, MONE, ONE, kactive, s->st);
+    }
+  }
+  // first pass
+  dense_gemm_cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
+  dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
+  small_orth_scale(K, p, s->sm2, s->sval, s->lref, 1e-12, s->sm3, s->d_nzero, s->st);
+  dense_gemm_nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, s->tmp3, sb, nm, ONE, ZERO, kactive, s->st);
+  // second pass on the kept block
+  dense_gemm_cn(K, nm, p, p, s->tmp3, sb, nm, s->tmp3, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work,
+                kactive, s->st);
+  dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
+  small_max_eval(K, p, s->sval, s->lref, s->st);
+  small_orth_scale(K, p, s->sm2, s->sval, s->lref, 1e-12, s->sm3, s->d_info, s->st);
+  dense_gemm_nn(K, nm, p, p, s->tmp3, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st);
+  CKL(s);
+  return EACG_OK;
+}
+
+// Copies contiguous [K][p][n_max] blocks into columns [q0, q0 + p) of the Krylov storage.
+static eacg_status put_cols(eacg_system* s, const double2* v, const double2* w, int q0) {
+  const size_t wb = sizeof(double2) * (size_t)s->p * s->n_max;
+  const size_t dp = sizeof(double2) * (size_t)s->qcap * s->n_max;
+  CK(cudaMemcpy2DAsync(s->fV + (size_t)q0 * s->n_max, dp, v, wb, wb, s->K, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpy2DAsync(s->fW + (size_t)q0 * s->n_max, dp, w, wb, wb, s->K, cudaMemcpyDeviceToDevice, s->st));
+  return EACG_OK;
+}
+
+// Energy-adaptive gradient by the preconditioned block FOM, per k (Algorithm 4, Sec. 5.2).
+// Uses the current potential (the one of phi).  fom_iters: host array of K ints or NULL.
+static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2* hphi, const double2* lam,
+                               double2* g, int prec, int* fom_iters) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  const size_t sb = (size_t)p * nm;
+  const double mu = s->prm.mu;
+  TRY(fom_reserve(s, 2 * p));
+  // Sigma = Lambda - mu I, its eigenpairs and Q^H
+  dense_shift_diag(K, p, lam, mu, s->sig, s->st);
+  dense_heig(K, p, s->sig, (size_t)p * p, s->eval, s->sigv, nullptr, s->st);
+  small_conj_transpose(K, p, s->sigv, s->sigvh, s->st);
+  dense_kinetic_alpha(K, p, nm, s->d_kin, phi, s->alpha, s->st);
+  // C = Phi - (H X0 - X0 Sigma), X0 = Phi / mu, H X0 = H Phi / mu
+  dense_copy(s->Cb, hphi, s->blk, s->st);
+  dense_gemm_nn(K, nm, p, p, phi, sb, nm, s->sig, (size_t)p * p, p, s->Cb, sb, nm, MONE, ONE, nullptr, s->st);
+  dense_axpby(s->blk, ONE, phi, cr(-1.0 / mu), s->Cb, s->Cb, s->st);
+  dense_norms2(K, sb, s->Cb, s->d_out + 64, s->st);
+  CKL(s);
+  TRY(sync_read(s, 64 + K));
+  std::vector<double> cnorm(K);
+  std::vector<int> active(K, 1), iters(K, 0);
+  for (int k = 0; k < K; ++k) {
+    cnorm[k] = std::sqrt(s->h_out[64 + k]);
+    if (!(cnorm[k] > 0)) active[k] = 0;
+  }
+  auto upload_active = [&]() -> eacg_status {
+    for (int k = 0; k < K; ++k) s->h_int[k] = active[k];
+    CK(cudaMemcpyAsync(s->d_kactive, s->h_int, sizeof(int) * K, cudaMemcpyHostToDevice, s->st));
+    return EACG_OK;
+  };
+  TRY(upload_active());
+  cudaMemsetAsync(s->fYf, 0, sizeof(double2) * (size_t)K * s->qcap * p, s->st);
+  cudaMemsetAsync(s->fA, 0, sizeof(double2) * (size_t)K * s->qcap * s->qcap, s->st);
+  // V_1 = orth(P^{-1} C), W_1 = H V_1, A_1 = herm(V_1^* W_1), C_1 = V_1^* C
+  dense_tpa(K, p, nm, s->d_kin, s->alpha, s->Cb, s->tmp2, false, s->st);
+  dense_zero(s->fvt, s->blk, s->st);
+  dense_zero(s->fwt, s->blk, s->st);
+  TRY(orthonormalise(s, s->tmp2, nullptr, 0, 0, s->fvt, s->d_kactive));
+  TRY(apply_H_block(s, s->fvt, s->fwt, prec, s->d_kactive));
+  TRY(put_cols(s, s->fvt, s->fwt, 0));
+  int q = 0;
+  auto add_block = [&](int q0) -> eacg_status {
+    // columns [q0, q0 + p) of V and W are new: fill A and C
+    const size_t sV = (size_t)s->qcap * nm;
+    const size_t sA = (size_t)s->qcap * s->qcap;
+    double2* Vn = s->fV + (size_t)q0 * nm;
+    double2* Wn = s->fW + (size_t)q0 * nm;
+    if (q0 > 0) {
+      dense_gemm_cn(K, nm, q0, p, s->fV, sV, nm, Wn, sV, nm, s->fA + (size_t)q0 * s->qcap, sA, s->qcap, ONE, ZERO,
+                    s->cn_work, s->d_kactive, s->st);
+      fom_mirror(K, q0, p, s->fA, s->qcap, sA, s->d_kactive, s->st);
+    }
+    dense_gemm_cn(K, nm, p, p, Vn, sV, nm, Wn, sV, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, s->d_kactive,
+                  s->st);
+    small_put_herm_block(K, p, s->sm1, s->fA, s->qcap, sA, q0, s->st);
+    fom_pad_diag(K, q0, p, s->fA, s->qcap, sA, s->d_nzero, 1e30, s->st);
+    dense_gemm_cn(K, nm, p, p, Vn, sV, nm, s->Cb, sb, nm, s->fC + q0, (size_t)s->qcap * p, s->qcap, ONE, ZERO,
+                  s->cn_work, s->d_kactive, s->st);
+    CKL(s);
+    return EACG_OK;
+  };
+  TRY(add_block(0));
+  q = p;
+  // rank of the first block
+  CK(cudaMemcpyAsync(s->h_int + K, s->d_nzero, sizeof(int) * K, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  for (int k = 0; k < K; ++k)
+    if (active[k] && s->h_int[K + k] >= p) active[k] = 0;  // rank 0: nothing to solve
+  int j = 0;
+  while (true) {
+    ++j;
+    const size_t sC = (size_t)s->qcap * p;
+    const size_t sA = (size_t)s->qcap * s->qcap;
+    const size_t sV = (size_t)s->qcap * nm;
+    TRY(upload_active());
+    // Y = solve(A Y - Y Sigma = C_j) via C~ = C Q, (A - s_m) y~_m = c~_m, Y = Y~ Q^H
+    dense_gemm_nn(K, q, p, p, s->fC, sC, s->qcap, s->sigv, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
+                  s->d_kactive, s->st);
+    fom_shifted_solve(K, p, q, s->fA, s->qcap, sA, s->eval, s->fYt, s->qcap, sC, s->fY, s->fwork, s->d_kactive,
+                      nullptr, s->st);
+    dense_gemm_nn(K, q, p, p, s->fY, sC, s->qcap, s->sigvh, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
+                  s->d_kactive, s->st);
+    // fYt now holds Y.  Res = C - (W Y - V Y Sigma)
+    dense_gemm_nn(K, nm, q, p, s->fW, sV, nm, s->fYt, sC, s->qcap, s->tmp1, sb, nm, ONE, ZERO, s->d_kactive, s->st);
+    dense_gemm_nn(K, q, p, p, s->fYt, sC, s->qcap, s->sig, (size_t)p * p, p, s->fY, sC, s->qcap, ONE, ZERO,
+                  s->d_kactive, s->st);
+    dense_gemm_nn(K, nm, q, p, s->fV, sV, nm, s->fY, sC, s->qcap, s->tmp1, sb, nm, MONE, ONE, s->d_kactive, s->st);
+    dense_axpby(s->blk, ONE, s->Cb, MONE, s->tmp1, s->tmp1, s->st);
+    dense_norms2(K, sb, s->tmp1, s->d_out + 64, s->st);
+    CKL(s);
+    TRY(sync_read(s, 64 + K));
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+      s->h_int[2 * K + k] = 0;
+      if (!active[k]) continue;
+      iters[k] = j;
+      const double rel = std::sqrt(s->h_out[64 + k]) / cnorm[k];
+      if (!(rel <= s->prm.fom_rtol) && j < s->prm.max_fom) {
+        any = true;
+      } else {
+        s->h_int[2 * K + k] = 1;  // take Y now
+      }
+      if (!std::isfinite(rel)) {
+        s->err = "non-finite FOM residual";
+        return EACG_EBREAKDOWN;
+      }
+    }
+    CK(cudaMemcpyAsync(s->d_take, s->h_int + 2 * K, sizeof(int) * K, cudaMemcpyHostToDevice, s->st));
+    small_take_y(K, q, s->qcap, p, s->fYt, s->fYf, s->d_take, s->st);
+    for (int k = 0; k < K; ++k)
+      if (s->h_int[2 * K + k]) active[k] = 0;
+    if (!any) break;
+    // next block: R_j = P^{-1} Res, orthonormalised against V_j
+    TRY(fom_reserve(s, q + p));
+    TRY(upload_active());
+    dense_tpa(K, p, nm, s->d_kin, s->alpha, s->tmp1, s->tmp2, false, s->st);
+    dense_zero(s->fvt, s->blk, s->st);
+    dense_zero(s->fwt, s->blk, s->st);
+    TRY(orthonormalise(s, s->tmp2, s->fV, q, (size_t)s->qcap * nm, s->fvt, s->d_kactive));
+    CK(cudaMemcpyAsync(s->h_int + K, s->d_nzero, sizeof(int) * K, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    bool any2 = false;
+    for (int k = 0; k < K; ++k) {
+      if (active[k] && s->h_int[K + k] >= p) {
+        // rank 0: the iteration ends with the current Y
+        s->h_int[2 * K + k] = 1;
+        active[k] = 0;
+      } else {
+        s->h_int[2 * K + k] = 0;
+      }
+      any2 |= active[k] != 0;
+    }
+    CK(cudaMemcpyAsync(s->d_take, s->h_int + 2 * K, sizeof(int) * K, cudaMemcpyHostToDevice, s->st));
+    small_take_y(K, q, s->qcap, p, s->fYt, s->fYf, s->d_take, s->st);
+    if (!any2) break;
+    TRY(upload_active());
+    TRY(apply_H_block(s, s->fvt, s->fwt, prec, s->d_kactive));
+    TRY(put_cols(s, s->fvt, s->fwt, q));
+    // the H application above advanced h_apps by all K; keep the per-k count honest
+    {
+      int na = 0;
+      for (int k = 0; k < K; ++k) na += active[k];
+      s->h_apps -= (long long)(K - na) * p;
+    }
+    TRY(add_block(q));
+    q += p;
+  }
+  // X = Phi / mu + V Y_final;  G = Phi - X (Phi^* X)^{-1}
+  const size_t sC = (size_t)s->qcap * p;
+  dense_axpby(s->blk, cr(1.0 / mu), phi, ZERO, nullptr, s->Xb, s->st);
+  dense_gemm_nn(K, nm, q, p, s->fV, (size_t)s->qcap * nm, nm, s->fYf, sC, s->qcap, s->Xb, sb, nm, ONE, ONE, nullptr,
+                s->st);
+  dense_gemm_cn(K, nm, p, p, phi, sb, nm, s->Xb, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
+                s->st);
+  dense_inverse(K, p, s->sm1, s->sm2, nullptr, s->st);
+  dense_copy(g, phi, s->blk, s->st);
+  dense_gemm_nn(K, nm, p, p, s->Xb, sb, nm, s->sm2, (size_t)p * p, p, g, sb, nm, MONE, ONE, nullptr, s->st);
+  CKL(s);
+  int mx = 0;
+  for (int k = 0; k < K; ++k) mx = std::max(mx, iters[k]);
+  s->last_fom_max = mx;
+  if (fom_iters)
+    for (int k = 0; k < K; ++k) fom_iters[k] = iters[k];
+  return EACG_OK;
+}
+
+// ============================================================================ line search
+// f(t) = E(pf(Phi + t eta)), f'(t) = 2 f <R(t), T_{t eta}(eta)> (Algorithm 2 input).  The trial
+// point, its H Phi, R, Lambda, transport of eta and S^{-1} stay in the *_t buffers.
+struct TrialOut {
+  EvalOut ev;
+  double df;
+};
+
+static eacg_status trial(eacg_system* s, double t, int prec, TrialOut* out) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  const size_t sb = (size_t)p * nm;
+  dense_axpby(s->blk, ONE, s->phi, cr(t), s->eta, s->psi_t, s->st);
+  TRY(polar(s, s->psi_t, s->phi_t, s->eval_t, s->evec_t, s->sinv_t));
+  // T(eta) = eta S^{-1} - t Phi+ [[eta S^{-1}, eta S^{-1}]]
+  dense_gemm_nn(K, nm, p, p, s->eta, sb, nm, s->sinv_t, (size_t)p * p, p, s->teta_t, sb, nm, ONE, ZERO, nullptr, s->st);
+  dense_gemm_cn(K, nm, p, p, s->teta_t, sb, nm, s->teta_t, sb, nm, s->sm2, (size_t)p * p, p, ONE, ZERO, s->cn_work,
+                nullptr, s->st);
+  dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm2, (size_t)p * p, p, s->teta_t, sb, nm, cr(-t), ONE, nullptr,
+                s->st);
+  CKL(s);
+  TRY(evaluate(s, s->phi_t, s->hphi_t, s->res_t, s->lam_t, prec, &out->ev));
+  pairing_dev(s, s->res_t, s->teta_t, 0, true);
+  TRY(sync_read(s, 1));
+  out->df = 2.0 * s->occ * s->h_out[0];
+  ++s->ls_total;
+  return EACG_OK;
+}
+
+// Algorithm 2 (with the readings stated in the header): returns the accepted step in *tau;
+// the accepted point is the last trial evaluated.
+static eacg_status modified_secant(eacg_system* s, double f0, double df0, double tau0, int prec, double* tau_out,
+                                   TrialOut* acc, int* trials_out) {
+  const eacg_params& P = s->prm;
+  const double ftol = f0 + P.eps * std::fabs(f0);
+  const double cmax = std::min(P.sigma, 1.0 - 2.0 * P.delta) * std::fabs(df0);
+  int trials = 0;
+  auto ev = [&](double t, TrialOut* o) -> eacg_status {
+    if (trials >= P.max_ls) {
+      s->err = "step-size search reached its trial cap";
+      return EACG_ELINESEARCH;
+    }
+    ++trials;
+    return trial(s, t, prec, o);
+  };
+  double a = 0.0, dfa = df0, b = tau0;
+  TrialOut tb;
+  TRY(ev(b, &tb));
+  double fb = tb.ev.E, dfb = tb.df;
+  double cur_t = b;
+  TrialOut cur = tb;
+  while (!(cur.ev.E <= ftol && std::fabs(cur.df) <= cmax)) {
+    const double den = dfb - dfa;
+    double tau = std::fabs(den) >= 1e-300 ? (a * dfb - b * dfa) / den : NAN;
+    if (!std::isfinite(tau)) {
+      b = P.gamma * b;
+      a = 0.0;
+      dfa = df0;
+      TRY(ev(b, &tb));
+      fb = tb.ev.E;
+      dfb = tb.df;
+      cur_t = b;
+      cur = tb;
+      continue;
+    }
+    if (tau < a) {
+      b = b / P.gamma;
+      a = 0.0;
+      dfa = df0;
+      TRY(ev(b, &tb));
+      fb = tb.ev.E;
+      dfb = tb.df;
+      cur_t = b;
+      cur = tb;
+      continue;
+    }
+    TrialOut tt;
+    TRY(ev(tau, &tt));
+    if (tt.ev.E > ftol && tt.df < 0) {
+      b = P.gamma * b;
+      a = 0.0;
+      dfa = df0;
+      TRY(ev(b, &tb));
+      fb = tb.ev.E;
+      dfb = tb.df;
+      cur_t = b;
+      cur = tb;
+    } else if (tau > b) {
+      a = b;
+      dfa = dfb;
+      b = tau;
+      fb = tt.ev.E;
+      dfb = tt.df;
+      cur_t = tau;
+      cur = tt;
+    } else {
+      if (tt.df >= 0) {
+        b = tau;
+        fb = tt.ev.E;
+        dfb = tt.df;
+      } else {
+        a = tau;
+        dfa = tt.df;
+      }
+      cur_t = tau;
+      cur = tt;
+    }
+  }
+  (void)fb;
+  *tau_out = cur_t;
+  *acc = cur;
+  *trials_out = trials;
+  return EACG_OK;
+}
+
+// T_{tau eta}(g) = (g - Phi+ X) S^{-1}, S X + X S = tau ([[eta, g]] + [[g, eta]]) with S = Sf(Phi + tau eta)
+// from the accepted trial (eigenvectors evec_t, eigenvalues sqrt(eval_t)).
+static eacg_status transport_g(eacg_system* s, double tau) {
+  const int K = s->K, p = s->p, nm = s->n_max;
+  const size_t sb = (size_t)p * nm;
+  dense_gemm_cn(K, nm, p, p, s->eta, sb, nm, s->gv, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
+                s->st);
+  small_add_herm(K, p, s->sm1, tau, s->sm2, s->st);  // sm2 = tau (M + M^H)
+  small_sqrt_vals(K, p, s->eval_t, s->sqd, s->st);
+  dense_lyapunov(K, p, s->evec_t, s->sqd, s->sm2, s->sm3, s->st);
+  dense_copy(s->tmp1, s->gv, s->blk, s->st);
+  dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm3, (size_t)p * p, p, s->tmp1, sb, nm, MONE, ONE, nullptr, s->st);
+  dense_gemm_nn(K, nm, p, p, s->tmp1, sb, nm, s->sinv_t, (size_t)p * p, p, s->tg, sb, nm, ONE, ZERO, nullptr, s->st);
+  CKL(s);
+  return EACG_OK;
+}
+
+// g at the current point: EA gradient, or the preconditioned direction in the warm-up or when
+// <r, g_EA> <= 0.  Returns <r, g> in *rg and the kind (1 EA, 0 preconditioned) in *kind.
+static eacg_status direction(eacg_system* s, int prec, double* rg, int* kind) {
+  if (s->phase == 1) {
+    TRY(ea_gradient(s, s->phi, s->hphi, s->lam, s->gv, prec, nullptr));
+    pairing_dev(s, s->res, s->gv, 0, true);
+    TRY(sync_read(s, 1));
+    if (s->h_out[0] > 0) {
+      *rg = s->h_out[0];
+      *kind = 1;
+      return EACG_OK;
+    }
+  }
+  TRY(precond_gradient(s, s->phi, s->res, s->gv));
+  pairing_dev(s, s->res, s->gv, 0, true);
+  TRY(sync_read(s, 1));
+  *rg = s->h_out[0];
+  *kind = 0;
+  return EACG_OK;
+}
+
+static int step_precision(const eacg_system* s) {
+  if (s->prm.precision == 0) return 0;
+  return s->rnorm > s->prm.switch_res ? 1 : 0;
+}
+
+static void swap_trial_into_current(eacg_system* s) {
+  std::swap(s->phi, s->phi_t);
+  std::swap(s->hphi, s->hphi_t);
+  std::swap(s->res, s->res_t);
+  std::swap(s->lam, s->lam_t);
+  std::swap(s->teta, s->teta_t);
+}
+
+static eacg_status start_iteration(eacg_system* s) {
+  EvalOut ev;
+  s->cur_prec = step_precision(s);
+  s->cur_prec = s->prm.precision ? 1 : 0;
+  TRY(evaluate(s, s->phi, s->hphi, s->res, s->lam, s->cur_prec, &ev));
+  s->E = ev.E;
+  s->rnorm = ev.rnorm;
+  std::memcpy(s->eterms, ev.terms, sizeof(ev.terms));
+  s->phase = (s->prm.max_warm > 0 && s->rnorm > s->prm.warm_res) ? 0 : 1;
+  s->iter = 0;
+  s->warm_iter = 0;
+  s->tau = 1.0;
+  s->fresh = 0;
+  if (s->rnorm <= s->prm.res_tol) return EACG_OK;
+  int kind;
+  s->cur_prec = step_precision(s);
+  TRY(direction(s, s->cur_prec, &s->rg, &kind));
+  dense_axpby(s->blk, MONE, s->gv, ZERO, nullptr, s->eta, s->st);
+  CKL(s);
+  return EACG_OK;
+}
+
+static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
+  if (!s->have_psi) {
+    s->err = "no iterate: call eacg_set_psi first";
+    return EACG_EINVAL;
+  }
+  if (s->fresh) TRY(start_iteration(s));
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (s->rnorm <= s->prm.res_tol) {
+    if (info) {
+      info->E = s->E;
+      info->rnorm = s->rnorm;
+      info->converged = 1;
+      info->phase = s->phase;
+      info->h_band_apps = s->h_apps;
+    }
+    return EACG_OK;
+  }
+  if (s->iter >= s->prm.max_outer) {
+    s->err = "outer iteration cap reached";
+    return EACG_ENOTCONV;
+  }
+  int prec = step_precision(s);
+  // f'(0) = 2 f <r, eta>
+  pairing_dev(s, s->res, s->eta, 0, true);
+  TRY(sync_read(s, 1));
+  const double df0 = 2.0 * s->occ * s->h_out[0];
+  double tau = 0;
+  TrialOut acc;
+  int trials = 0;
+  eacg_status st = modified_secant(s, s->E, df0, s->tau, prec, &tau, &acc, &trials);
+  if (st == EACG_ELINESEARCH && prec == 1) {
+    // FP32 transforms can no longer resolve the energy decrease: continue in FP64
+    s->prm.switch_res = std::max(s->prm.switch_res, 2.0 * s->rnorm);
+    prec = 0;
+    st = modified_secant(s, s->E, df0, s->tau, prec, &tau, &acc, &trials);
+  }
+  if (st != EACG_OK) return st;
+  s->iter += 1;
+  if (s->phase == 0) s->warm_iter += 1;
+  // transport of the old g (needs old Phi, eta, g and the accepted trial's S)
+  TRY(transport_g(s, tau));
+  const bool sw = s->phase == 0 && (acc.ev.rnorm <= s->prm.warm_res || s->warm_iter >= s->prm.max_warm);
+  if (sw) s->phase = 1;
+  swap_trial_into_current(s);
+  s->E = acc.ev.E;
+  s->rnorm = acc.ev.rnorm;
+  std::memcpy(s->eterms, acc.ev.terms, sizeof(acc.ev.terms));
+  s->tau = tau;
+  double beta = 0.0;
+  int kind = 0;
+  if (s->rnorm > s->prm.res_tol) {
+    // the potential in the system is the accepted trial's (the last one evaluated)
+    const int dprec = step_precision(s) && prec;
+    double rgn;
+    TRY(direction(s, dprec, &rgn, &kind));
+    if (sw) {
+      beta = 0.0;
+      s->tau = 1.0;
+    } else {
+      pairing_dev(s, s->res, s->tg, 0, true);
+      TRY(sync_read(s, 1));
+      const double bfr = rgn / s->rg;
+      const double bprp = (rgn - s->h_out[0]) / s->rg;
+      beta = std::max(0.0, std::min(bfr, bprp));
+    }
+    // eta = -g + beta T(eta)
+    dense_axpby(s->blk, MONE, s->gv, cr(beta), s->teta, s->eta, s->st);
+    pairing_dev(s, s->res, s->eta, 0, true);
+    TRY(sync_read(s, 1));
+    if (s->h_out[0] >= 0) {
+      dense_axpby(s->blk, MONE, s->gv, ZERO, nullptr, s->eta, s->st);
+      beta = 0.0;
+    }
+    CKL(s);
+    s->rg = rgn;
+  }
+  if (info) {
+    info->E = s->E;
+    info->rnorm = s->rnorm;
+    info->tau = tau;
+    info->beta = beta;
+    info->fom_iters_max = s->phase == 1 ? s->last_fom_max : 0;
+    info->ls_trials = trials;
+    info->phase = s->phase;
+    info->precision = prec;
+    info->converged = s->rnorm <= s->prm.res_tol;
+    info->h_band_apps = s->h_apps;
+  }
+  return EACG_OK;
+}
+
+// ============================================================================ C ABI
+#define SYS_CHECK(sys)                      \
+  do {                                      \
+    if (!(sys)) return EACG_EINVAL;         \
+  } while (0)
+
+extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params* prm, void* stream,
+                                          eacg_system** out) {
+  if (!out) return EACG_EINVAL;
+  *out = nullptr;
+  std::string why;
+  eacg_status v = validate(m, prm, &why);
+  if (v != EACG_OK) return v;
+  eacg_system* s = new eacg_system();
+  s->st = (cudaStream_t)stream;
+  if (prm)
+    s->prm = *prm;
+  else
+    eacg_default_params(&s->prm);
+  s->N = m->N;
+  s->K = m->nk;
+  s->p = m->nbands;
+  s->natoms = m->natoms;
+  s->npa = m->nproj_per_atom;
+  s->nproj = m->natoms * m->nproj_per_atom;
+  s->hartree = m->hartree;
+  s->xc = m->xc;
+  s->a = m->a;
+  s->omega = m->a * m->a * m->a;
+  s->b = 2.0 * M_PI / m->a;
+  s->ecut = m->ecut;
+  s->occ = m->occ;
+  s->width = m->proj_width;
+  s->thr = (2.0 * m->ecut) / (s->b * s->b);
+  s->kfrac.assign(m->kfrac, m->kfrac + 3 * m->nk);
+  s->kw.assign(m->kweight, m->kweight + m->nk);
+  for (int i = 0; i < m->natoms; ++i) {
+    for (int c = 0; c < 3; ++c) s->pos.push_back(m->pos[3 * i + c]);
+    s->Z.push_back((double)m->Z[i]);
+    s->rc.push_back(m->rc[i]);
+    for (int l = 0; l < m->nproj_per_atom; ++l) s->dvec.push_back(l == 0 ? m->D[2 * i] : m->D[2 * i + 1]);
+  }
+  auto fail = [&](eacg_status st) {
+    eacg_destroy(s);
+    return st;
+  };
+  auto up = [&](double** d, const std::vector<double>& h) -> eacg_status {
+    TRY(dalloc(s, d, sizeof(double) * std::max<size_t>(1, h.size())));
+    if (!h.empty()) {
+      cudaError_t e = cudaMemcpyAsync(*d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s->st);
+      if (e != cudaSuccess) {
+        s->err = cudaGetErrorString(e);
+        return EACG_ECUDA;
+      }
+    }
+    return EACG_OK;
+  };
+  eacg_status st;
+  if ((st = up(&s->d_kfrac, s->kfrac)) != EACG_OK) return fail(st);
+  if ((st = up(&s->d_kw, s->kw)) != EACG_OK) return fail(st);
+  if ((st = up(&s->d_pos, s->pos)) != EACG_OK) return fail(st);
+  if ((st = up(&s->d_Z, s->Z)) != EACG_OK) return fail(st);
+  if ((st = up(&s->d_rc, s->rc)) != EACG_OK) return fail(st);
+  if ((st = up(&s->d_dvec, s->dvec)) != EACG_OK) return fail(st);
+  // FFT plan and twiddles e^{-2 pi i k / N}
+  make_plan(s->N, &s->g.plan);
+  {
+    std::vector<double2> tw(s->N);
+    std::vector<float2> tw32(s->N);
+    for (int k = 0; k < s->N; ++k) {
+      const double ang = 2.0 * M_PI * (double)k / (double)s->N;
+      tw[k] = make_double2(std::cos(ang), -std::sin(ang));
+      tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+    }
+    if ((st = dalloc(s, &s->d_tw64, sizeof(double2) * s->N)) != EACG_OK) return fail(st);
+    if ((st = dalloc(s, &s->d_tw32, sizeof(float2) * s->N)) != EACG_OK) return fail(st);
+    cudaMemcpyAsync(s->d_tw64, tw.data(), sizeof(double2) * s->N, cudaMemcpyHostToDevice, s->st);
+    cudaMemcpyAsync(s->d_tw32, tw32.data(), sizeof(float2) * s->N, cudaMemcpyHostToDevice, s->st);
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) {
+      s->err = "stream synchronise failed during set-up";
+      return fail(EACG_ECUDA);
+    }
+  }
+  if ((st = build_basis(s)) != EACG_OK) return fail(st);
+  s->g.K = s->K;
+  s->g.p = s->p;
+  s->g.n_max = s->n_max;
+  s->g.ncols = s->ncols;
+  s->g.ny = s->ny;
+  s->g.cols_per_cta = std::max(1, std::min(64, 256 / s->g.plan.TPL));
+  s->g.nk = s->d_nk;
+  s->g.xmap = s->d_xmap;
+  s->g.colfy = s->d_colfy;
+  s->g.colfz = s->d_colfz;
+  s->g.ylist = s->d_ylist;
+  s->g.tw64 = s->d_tw64;
+  s->g.tw32 = s->d_tw32;
+  if ((st = build_potential_and_projectors(s)) != EACG_OK) return fail(st);
+  if ((st = alloc_work(s)) != EACG_OK) return fail(st);
+  if (cudaStreamSynchronize(s->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    s->err = "set-up kernels failed";
+    return fail(EACG_ECUDA);
+  }
+  *out = s;
+  return EACG_OK;
+}
+
+extern "C" void eacg_destroy(eacg_system* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->h_out) cudaFreeHost(s->h_out);
+  if (s->h_int) cudaFreeHost(s->h_int);
+  delete s;
+}
+
+extern "C" const char* eacg_last_error(const eacg_system* s) { return s ? s->err.c_str() : "null system"; }
+
+extern "C" eacg_status eacg_get_dims(const eacg_system* s, int* nk_host, int* n_max, int* ncols) {
+  SYS_CHECK(s);
+  if (nk_host)
+    for (int k = 0; k < s->K; ++k) nk_host[k] = s->nk[k];
+  if (n_max) *n_max = s->n_max;
+  if (ncols) *ncols = s->ncols;
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_get_basis(const eacg_system* cs, int* m_dev) {
+  SYS_CHECK(cs);
+  eacg_system* s = const_cast<eacg_system*>(cs);
+  if (!m_dev) return EACG_EINVAL;
+  CK(cudaMemcpyAsync(m_dev, s->d_m, sizeof(int) * 3 * (size_t)s->K * s->n_max, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_set_psi(eacg_system* s, const double* psi_dev) {
+  SYS_CHECK(s);
+  if (!psi_dev) return EACG_EINVAL;
+  CK(cudaMemcpyAsync(s->tmp2, psi_dev, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  TRY(polar(s, s->tmp2, s->phi, s->eval, s->evec, s->sm3));
+  CK(cudaStreamSynchronize(s->st));
+  s->have_psi = 1;
+  s->fresh = 1;
+  s->h_apps = 0;
+  s->ls_total = 0;
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_get_psi(eacg_system* s, double* psi_dev_out) {
+  SYS_CHECK(s);
+  if (!psi_dev_out) return EACG_EINVAL;
+  CK(cudaMemcpyAsync(psi_dev_out, s->phi, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_density(eacg_system* s, const double* psi_dev, double* rho_dev, int precision) {
+  SYS_CHECK(s);
+  if (!psi_dev) return EACG_EINVAL;
+  TRY(density_and_potential(s, reinterpret_cast<const double2*>(psi_dev), precision ? 1 : 0));
+  const size_t N3 = (size_t)s->N * s->N * s->N;
+  if (rho_dev) CK(cudaMemcpyAsync(rho_dev, s->d_rho, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_get_potential(eacg_system* s, double* vtot_dev) {
+  SYS_CHECK(s);
+  if (!vtot_dev) return EACG_EINVAL;
+  const size_t N3 = (size_t)s->N * s->N * s->N;
+  CK(cudaMemcpyAsync(vtot_dev, s->d_vtot, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_apply_H(eacg_system* s, const double* psi_dev, double* hpsi_dev, int precision) {
+  SYS_CHECK(s);
+  if (!psi_dev || !hpsi_dev || psi_dev == hpsi_dev) return EACG_EINVAL;
+  TRY(apply_H_block(s, reinterpret_cast<const double2*>(psi_dev), reinterpret_cast<double2*>(hpsi_dev),
+                    precision ? 1 : 0, nullptr));
+  CK(cudaStreamSynchronize(s->st));
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_energy(eacg_system* s, const double* psi_dev, double* terms, double* lam_dev,
+                                   double* res_dev, double* rnorm, int precision) {
+  SYS_CHECK(s);
+  if (!psi_dev) return EACG_EINVAL;
+  EvalOut ev;
+  CK(cudaMemcpyAsync(s->tmp3, psi_dev, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  TRY(evaluate(s, s->tmp3, s->hphi_t, s->res_t, s->lam_t, precision ? 1 : 0, &ev));
+  if (terms) {
+    for (int i = 0; i < 5; ++i) terms[i] = ev.terms[i];
+    terms[5] = ev.E;
+  }
+  if (rnorm) *rnorm = ev.rnorm;
+  if (lam_dev)
+    CK(cudaMemcpyAsync(lam_dev, s->lam_t, sizeof(double2) * (size_t)s->K * s->p * s->p, cudaMemcpyDeviceToDevice,
+                       s->st));
+  if (res_dev) CK(cudaMemcpyAsync(res_dev, s->res_t, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  s->fresh = 1;  // the trial buffers were used
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_ea_gradient(eacg_system* s, const double* psi_dev, double* g_dev, int* fom_iters,
+                                        int precision) {
+  SYS_CHECK(s);
+  if (!psi_dev || !g_dev) return EACG_EINVAL;
+  EvalOut ev;
+  CK(cudaMemcpyAsync(s->phi_t, psi_dev, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  TRY(evaluate(s, s->phi_t, s->hphi_t, s->res_t, s->lam_t, precision ? 1 : 0, &ev));
+  TRY(ea_gradient(s, s->phi_t, s->hphi_t, s->lam_t, s->teta_t, precision ? 1 : 0, fom_iters));
+  CK(cudaMemcpyAsync(g_dev, s->teta_t, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  s->fresh = 1;
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_retract(eacg_system* s, const double* phi_dev, const double* eta_dev, double tau,
+                                    double* phi_out_dev, double* teta_out_dev) {
+  SYS_CHECK(s);
+  if (!phi_dev || !eta_dev || !phi_out_dev) return EACG_EINVAL;
+  const int K = s->K, p = s->p, nm = s->n_max;
+  const size_t sb = (size_t)p * nm;
+  dense_axpby(s->blk, ONE, reinterpret_cast<const double2*>(phi_dev), cr(tau),
+              reinterpret_cast<const double2*>(eta_dev), s->psi_t, s->st);
+  TRY(polar(s, s->psi_t, s->tmp1, s->eval_t, s->evec_t, s->sinv_t));
+  if (teta_out_dev) {
+    dense_gemm_nn(K, nm, p, p, reinterpret_cast<const double2*>(eta_dev), sb, nm, s->sinv_t, (size_t)p * p, p,
+                  s->tmp2, sb, nm, ONE, ZERO, nullptr, s->st);
+    dense_gemm_cn(K, nm, p, p, s->tmp2, sb, nm, s->tmp2, sb, nm, s->sm2, (size_t)p * p, p, ONE, ZERO, s->cn_work,
+                  nullptr, s->st);
+    dense_gemm_nn(K, nm, p, p, s->tmp1, sb, nm, s->sm2, (size_t)p * p, p, s->tmp2, sb, nm, cr(-tau), ONE, nullptr,
+                  s->st);
+    CK(cudaMemcpyAsync(teta_out_dev, s->tmp2, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  }
+  CK(cudaMemcpyAsync(phi_out_dev, s->tmp1, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  CKL(s);
+  CK(cudaStreamSynchronize(s->st));
+  s->fresh = 1;
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {
+  SYS_CHECK(s);
+  eacg_status st = do_step(s, info);
+  if (st == EACG_OK) {
+    cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+      s->err = cudaGetErrorString(e);
+      return EACG_ECUDA;
+    }
+  }
+  return st;
+}
+
+extern "C" eacg_status eacg_solve(eacg_system* s, eacg_result* out) {
+  SYS_CHECK(s);
+  eacg_status st = EACG_OK;
+  eacg_step_info info;
+  while (true) {
+    st = do_step(s, &info);
+    if (st != EACG_OK || info.converged) break;
+  }
+  if (out) {
+    out->E = s->E;
+    out->rnorm = s->rnorm;
+    out->iterations = s->iter;
+    out->warm_iterations = s->warm_iter;
+    out->status = (int)st;
+    out->ls_trials = s->ls_total;
+    out->h_band_apps = s->h_apps;
+  }
+  cudaError_t e = cudaStreamSynchronize(s->st);
+  if (st == EACG_OK && e != cudaSuccess) {
+    s->err = cudaGetErrorString(e);
+    return EACG_ECUDA;
+  }
+  return st;
+}
+
+extern "C" eacg_status eacg_solve_host(eacg_system* s, const double* psi0_host, double* psi_out_host,
+                                       eacg_result* out) {
+  SYS_CHECK(s);
+  if (!psi0_host) return EACG_EINVAL;
+  CK(cudaMemcpyAsync(s->tmp2, psi0_host, sizeof(double2) * s->blk, cudaMemcpyHostToDevice, s->st));
+  TRY(polar(s, s->tmp2, s->phi, s->eval, s->evec, s->sm3));
+  s->have_psi = 1;
+  s->fresh = 1;
+  s->h_apps = 0;
+  s->ls_total = 0;
+  eacg_status st = eacg_solve(s, out);
+  if (psi_out_host) {
+    CK(cudaMemcpyAsync(psi_out_host, s->phi, sizeof(double2) * s->blk, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+  }
+  return st;
+}

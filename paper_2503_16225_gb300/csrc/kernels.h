@@ -1,0 +1,110 @@
+// Internal launch interface between the C-ABI driver (eacg.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "fft.cuh"
+
+namespace eacg {
+
+// Device-side description of the plane-wave grid of one system.
+struct GridCtx {
+  FftPlan plan;
+  int K, p, n_max, ncols, ny, cols_per_cta;
+  const int* nk;      // [K]
+  const int* xmap;    // [K][ncols][N]
+  const int* colfy;   // [ncols]
+  const int* colfz;   // [ncols]
+  const int* ylist;   // [ny]
+  const void* tw64;   // double2[N]
+  const void* tw32;   // float2[N]
+};
+
+// ---- grid_kernels.cu
+void grid_build_sphere(int N, int K, const double* kfrac_d, double thr, double b, int n_max_cap, int* nk, int* row_off,
+                       int* m, double* kin, int* colmark, cudaStream_t st);
+void grid_columns(int N, const int* colmark, int* colidx, int* colfy, int* colfz, int* ncols, int* ylist, int* ny,
+                  cudaStream_t st);
+void grid_xmap(int N, int K, int n_max, const int* nk, const int* m, const int* colidx, int ncols, int* xmap,
+               cudaStream_t st);
+void grid_fill_int(int* p, size_t n, int v, cudaStream_t st);
+void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, int nbands, const int* kactive,
+                    cudaStream_t st);
+void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
+                    double scale, double2* out, int nbands, const int* kactive, cudaStream_t st);
+void grid_plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
+                  cudaStream_t st);
+void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
+                    double* partial, cudaStream_t st);
+void grid_reduce_groups(const double* partial, int G, size_t n, double* out, cudaStream_t st);
+void grid_fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st);
+void grid_vloc_g(int N, double b, double omega, int natoms, const double* pos, const double* Z, const double* rc,
+                 double2* out, cudaStream_t st);
+void grid_hartree_scale(double2* a, int N, double b, cudaStream_t st);
+void grid_real_to_complex(const double* r, double2* c, size_t n, cudaStream_t st);
+void grid_complex_real_part(const double2* c, double* r, size_t n, cudaStream_t st);
+int grid_vtot_energy(size_t n, const double* vloc, const double* vh, const double* rho, int hartree, int xc,
+                     double* vtot, float* vtot32, double* blocksums, cudaStream_t st);
+void grid_projectors(int K, int n_max, const int* nk, const int* m, const double* kfrac, double b, double omega,
+                     int natoms, const double* pos, int npa, double w, double2* B, cudaStream_t st);
+
+// ---- dense_kernels.cu  (complex double blocks, batched over k with per-k strides)
+// C[k](m x n, ldc) = alpha * A[k]^H B[k] + beta * C[k]; A: L x m (lda), B: L x n (ldb).
+// Deterministic: fixed row chunks reduced in a fixed order.  work must hold
+// K * nchunks * m * n double2 (see dense_cn_work).
+size_t dense_cn_work(int K, int L, int m, int n);
+void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
+                   int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
+                   const int* kactive, cudaStream_t st);
+// C[k](L x n, ldc) = alpha * A[k](L x m, lda) * B[k](m x n, ldb) + beta * C[k].
+void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
+                   int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
+                   cudaStream_t st);
+// Hermitian eigen-decomposition of K matrices p x p (ld p): ascending eigenvalues and
+// unit eigenvectors (columns).  p <= 64.
+void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive, cudaStream_t st);
+// out[k] = V diag(f(w)) V^H with f(x) = x^e (e = -0.5, 0.5) restricted to w > cut; else 0.
+void dense_eig_func(int K, int p, const double2* V, const double* w, double expo, double cut_rel, double2* out,
+                    const int* kactive, cudaStream_t st);
+// Inverse of K general p x p complex matrices (Gauss-Jordan, partial pivoting).
+void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st);
+// Lyapunov S X + X S = M with S = V diag(s) V^H: X = V [(V^H M V)_ij / (s_i + s_j)] V^H.
+void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st);
+// Elementwise helpers on blocks of length n per k (K blocks, stride s).
+void dense_axpby(size_t n, double2 a, const double2* x, double2 b, const double2* y, double2* out, cudaStream_t st);
+void dense_herm(int K, int p, double2* A, cudaStream_t st);
+void dense_shift_diag(int K, int p, const double2* A, double mu, double2* out, cudaStream_t st);
+// partial sums of sum_k wk Re <V_k, W_k> over blocks [K][len]: returns number of partials
+int dense_dot(int K, size_t len, const double2* V, const double2* W, const double* wk, double* partials,
+              cudaStream_t st);
+void dense_sum_partials(const double* partials, int n, double* out, cudaStream_t st);
+// Per-k Frobenius norm squared of blocks [K][len] -> out[K] (deterministic).
+void dense_norms2(int K, size_t len, const double2* V, double* out, cudaStream_t st);
+// Copy / zero helpers
+void dense_copy(double2* dst, const double2* src, size_t n, cudaStream_t st);
+void dense_zero(double2* dst, size_t n, cudaStream_t st);
+// Column-wise TPA preconditioner: out[k][i][g] = in * scale_i / (kin[k][g] + alpha[k][i]).
+void dense_tpa(int K, int p, int n_max, const double* kin, const double* alpha, const double2* in, double2* out,
+               bool unit_gain, cudaStream_t st);
+// alpha[k][i] = sum_g kin[k][g] |phi[k][i][g]|^2
+void dense_kinetic_alpha(int K, int p, int n_max, const double* kin, const double2* phi, double* alpha,
+                         cudaStream_t st);
+// Diagonal scaling of projections: P[k][j][i] *= d[j]
+void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStream_t st);
+// Per-column norms of a p x p matrix block etc.
+void dense_kin_energy(int K, int p, int n_max, const double* kin, const double2* phi, const double* kw, double occ,
+                      double* partials, cudaStream_t st);
+
+// ---- fom_kernels.cu
+// Solve (A[k] - s[k][m] I) y = c for every (k, m): A q x q (lda), c/y columns of q x p (ldc).
+void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s,
+                       const double2* C, int ldc, size_t sC, double2* Y, double2* work, const int* kactive,
+                       int* info, cudaStream_t st);
+// A[k][i][j] for i in [q0, q0 + p) and j < q0: conj of A[k][j][i] (Hermitian mirror).
+void fom_mirror(int K, int q0, int p, double2* A, int lda, size_t sA, const int* kactive, cudaStream_t st);
+// Rows of A with zero new columns: A[k][q0 + i][q0 + i] = big for i < nzero[k].
+void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, double big,
+                  cudaStream_t st);
+
+}  // namespace eacg

@@ -1,0 +1,46 @@
+"""The C-ABI library loads and exports every entry point that include/eacg.h declares
+(no compute call: this runs without a GPU)."""
+import ctypes
+import json
+import os
+import re
+
+from tests.conftest import ROOT, ensure_library
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "eacg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eacg_[a-z_A-Z]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("eacg_create_system", "eacg_apply_H", "eacg_density", "eacg_step", "eacg_solve"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(ensure_library())
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_are_the_paper_constants():
+    ensure_library()
+    import paper_2503_16225_gb300 as E
+    p = E.eacg_default_params()
+    c = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    for key in ("delta", "sigma", "gamma", "eps", "mu", "fom_rtol"):
+        assert getattr(p, key) == c[key]["value"], key
+
+
+def test_bytes_required_and_model_validation_on_host():
+    ensure_library()
+    import synth
+    import paper_2503_16225_gb300 as E
+    n, per = E.eacg_bytes_required(synth.config_diamond(2))
+    assert n > 0 and per > 0
+    bad = dict(synth.config_two_atom(1))
+    bad["N"] = 7   # not a supported FFT size
+    assert E.eacg_bytes_required(bad)[0] == 0
