@@ -165,6 +165,24 @@ eacg_status eacg_ea_gradient(eacg_system* sys, const double* psi_dev, double* g_
 eacg_status eacg_retract(eacg_system* sys, const double* phi_dev, const double* eta_dev, double tau,
                          double* phi_out_dev, double* teta_out_dev);
 
+/* Live kernel timing (no counterpart in the paper; used for roofline reports).
+ * eacg_profile_enable(sys, 1) clears and starts recording CUDA events around the main
+ * kernels of the Hamiltonian application, density, potential and FOM solves on the
+ * system's stream; eacg_profile_read writes up to max entries (name, launches, summed
+ * device milliseconds, summed algorithmic bytes, summed work units = band applications)
+ * and returns their number (negative eacg_status on error).  Reading clears the records. */
+typedef struct {
+  char name[24];
+  long long launches;
+  double ms;
+  double bytes;
+  double units;
+} eacg_kernel_stat;
+eacg_status eacg_profile_enable(eacg_system* sys, int on);
+int eacg_profile_read(eacg_system* sys, eacg_kernel_stat* out, int max);
+/* Number of kernels this library has launched in the process so far. */
+long long eacg_launch_count(void);
+
 /* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
 eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);
 /* Iterates eacg_step until ||R||_F <= res_tol or max_outer; result in *out. */

@@ -18,7 +18,8 @@ __all__ = [
     "eacg_default_params", "eacg_bytes_required", "eacg_create_system", "eacg_destroy", "eacg_last_error",
     "eacg_get_dims", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
-    "eacg_solve_host", "System", "STATUS",
+    "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
+    "System", "STATUS",
 ]
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBREAKDOWN", 5: "ENONCOERCIVE",
@@ -57,6 +58,11 @@ class EacgResult(ctypes.Structure):
                 ("h_band_apps", ctypes.c_longlong)]
 
 
+class EacgKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("units", ctypes.c_double)]
+
+
 class EacgError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -88,6 +94,9 @@ def _load():
         "eacg_step": (ctypes.c_int, [vp, ctypes.POINTER(EacgStepInfo)]),
         "eacg_solve": (ctypes.c_int, [vp, ctypes.POINTER(EacgResult)]),
         "eacg_solve_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(EacgResult)]),
+        "eacg_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "eacg_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(EacgKernelStat), ctypes.c_int]),
+        "eacg_launch_count": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -249,6 +258,24 @@ def eacg_solve_host(sys, psi0_host, psi_out_host, check=True):
     if check:
         _check(sys, code)
     return res
+
+
+def eacg_profile_enable(sys, on=1):
+    _check(sys, lib.eacg_profile_enable(sys, int(on)))
+
+
+def eacg_profile_read(sys):
+    """{kernel name: {launches, ms, bytes, units}} since eacg_profile_enable (then cleared)."""
+    buf = (EacgKernelStat * 32)()
+    n = lib.eacg_profile_read(sys, buf, 32)
+    if n < 0:
+        raise EacgError(-n, eacg_last_error(sys))
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "bytes": buf[i].bytes,
+                                   "units": buf[i].units} for i in range(n)}
+
+
+def eacg_launch_count():
+    return int(lib.eacg_launch_count())
 
 
 class System:

@@ -83,9 +83,13 @@ void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int 
   const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
   const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
   dim3 g1(tiles, nch > 0 ? nch : 1, K);
-  if (nch > 0) k_gemm_cn_partial<<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+  if (nch > 0) {
+    k_gemm_cn_partial<<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+  count_launch();
+  }
   dim3 g2((m * n + 255) / 256, K);
   k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
+  count_launch();
 }
 
 // ----------------------------------------------------------------------------- A B (small B)
@@ -142,6 +146,7 @@ void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int 
   if (K <= 0 || L <= 0 || n <= 0) return;
   dim3 g((L + 127) / 128, K);
   k_gemm_nn<<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
+  count_launch();
 }
 
 // ----------------------------------------------------------------------------- Hermitian eig
@@ -310,6 +315,7 @@ void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V
   cudaFuncSetAttribute(k_heig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int threads = p <= 16 ? 128 : 256;
   k_heig<<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
+  count_launch();
 }
 
 // out = V diag(f(w)) V^H, f(x) = x^expo for x > cut_rel * max(w, 0), else 0
@@ -345,6 +351,7 @@ __global__ void k_eig_func(int p, const double2* __restrict__ V, const double* _
 void dense_eig_func(int K, int p, const double2* V, const double* w, double expo, double cut_rel, double2* out,
                     const int* kactive, cudaStream_t st) {
   k_eig_func<<<K, 128, sizeof(double) * (p + 1), st>>>(p, V, w, expo, cut_rel, out, kactive);
+  count_launch();
 }
 
 // Gauss-Jordan inverse with partial pivoting, one CTA per matrix (p <= 64).
@@ -409,6 +416,7 @@ void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cud
   const size_t sm = sizeof(double2) * 2 * p * p;
   cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_inverse<<<K, 256, sm, st>>>(p, A, Ainv, info);
+  count_launch();
 }
 
 // Lyapunov by the eigenbasis of S.
@@ -460,6 +468,7 @@ void dense_lyapunov(int K, int p, const double2* V, const double* s, const doubl
   const size_t sm = sizeof(double2) * 3 * p * p;
   cudaFuncSetAttribute(k_lyap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_lyap<<<K, 256, sm, st>>>(p, V, s, M, X);
+  count_launch();
 }
 
 // ----------------------------------------------------------------------------- elementwise
@@ -474,6 +483,7 @@ __global__ void k_axpby(size_t n, double2 a, const double2* __restrict__ x, doub
 void dense_axpby(size_t n, double2 a, const double2* x, double2 b, const double2* y, double2* out, cudaStream_t st) {
   const int blocks = (int)min((size_t)2048, (n + 255) / 256);
   k_axpby<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(n, a, x, b, y, out);
+  count_launch();
 }
 
 __global__ void k_herm(int p, double2* A) {
@@ -491,7 +501,8 @@ __global__ void k_herm(int p, double2* A) {
     }
   }
 }
-void dense_herm(int K, int p, double2* A, cudaStream_t st) { k_herm<<<K, 256, 0, st>>>(p, A); }
+void dense_herm(int K, int p, double2* A, cudaStream_t st) { k_herm<<<K, 256, 0, st>>>(p, A);
+  count_launch(); }
 
 __global__ void k_shift_diag(int p, const double2* __restrict__ A, double mu, double2* __restrict__ out) {
   const int k = blockIdx.x;
@@ -504,6 +515,7 @@ __global__ void k_shift_diag(int p, const double2* __restrict__ A, double mu, do
 }
 void dense_shift_diag(int K, int p, const double2* A, double mu, double2* out, cudaStream_t st) {
   k_shift_diag<<<K, 256, 0, st>>>(p, A, mu, out);
+  count_launch();
 }
 
 constexpr int DOT_BLOCKS_PER_K = 32;
@@ -529,6 +541,7 @@ int dense_dot(int K, size_t len, const double2* V, const double2* W, const doubl
               cudaStream_t st) {
   dim3 g(DOT_BLOCKS_PER_K, K);
   k_dot<<<g, 256, 0, st>>>(K, len, V, W, wk, partials);
+  count_launch();
   return K * DOT_BLOCKS_PER_K;
 }
 __global__ void k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
@@ -540,6 +553,7 @@ __global__ void k_sum_partials(const double* __restrict__ p, int n, double* __re
 }
 void dense_sum_partials(const double* partials, int n, double* out, cudaStream_t st) {
   k_sum_partials<<<1, 32, 0, st>>>(partials, n, out);
+  count_launch();
 }
 
 __global__ void k_norms2(size_t len, const double2* __restrict__ V, double* __restrict__ out) {
@@ -558,6 +572,7 @@ __global__ void k_norms2(size_t len, const double2* __restrict__ V, double* __re
 }
 void dense_norms2(int K, size_t len, const double2* V, double* out, cudaStream_t st) {
   k_norms2<<<K, 256, 0, st>>>(len, V, out);
+  count_launch();
 }
 
 void dense_copy(double2* dst, const double2* src, size_t n, cudaStream_t st) {
@@ -580,6 +595,7 @@ void dense_tpa(int K, int p, int n_max, const double* kin, const double* alpha, 
                bool unit_gain, cudaStream_t st) {
   dim3 g(64, K);
   k_tpa<<<g, 256, 0, st>>>(p, n_max, kin, alpha, in, out, unit_gain);
+  count_launch();
 }
 
 __global__ void k_kinetic_alpha(int p, int n_max, const double* __restrict__ kin, const double2* __restrict__ phi,
@@ -602,6 +618,7 @@ void dense_kinetic_alpha(int K, int p, int n_max, const double* kin, const doubl
                          cudaStream_t st) {
   dim3 g(p, K);
   k_kinetic_alpha<<<g, 256, 0, st>>>(p, n_max, kin, phi, alpha);
+  count_launch();
 }
 
 // E_kin partials: per (k, i) f w_k sum_g kin |c|^2
@@ -625,6 +642,7 @@ void dense_kin_energy(int K, int p, int n_max, const double* kin, const double2*
                       double* partials, cudaStream_t st) {
   dim3 g(p, K);
   k_kin_energy<<<g, 256, 0, st>>>(p, n_max, kin, phi, kw, occ, partials);
+  count_launch();
 }
 
 __global__ void k_scale_rows(int m, int n, double2* P, const double* __restrict__ d) {
@@ -636,21 +654,27 @@ __global__ void k_scale_rows(int m, int n, double2* P, const double* __restrict_
 }
 void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStream_t st) {
   k_scale_rows<<<K, 256, 0, st>>>(m, n, P, d);
+  count_launch();
 }
 
 // ----------------------------------------------------------------------------- FOM projected solves
 // One CTA per (m, k): Gaussian elimination with partial pivoting of [A - s_m I | c_m] (q x (q+1),
-// column-major in work), then back substitution; y written to column m of Y (ld q).
+// column-major) in the working precision T, then column-oriented back substitution; y is written
+// (in FP64) to column m of Y (ld ldc).  The working matrix lives in shared memory when it fits,
+// else in the global work buffer (one q x (q+1) slice per (k, m)).
+template <typename T>
 __global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int lda, size_t sA,
                                 const double* __restrict__ s, const double2* __restrict__ C, int ldc, size_t sC,
-                                double2* __restrict__ Y, double2* __restrict__ work, const int* __restrict__ kactive,
-                                int* __restrict__ info) {
+                                double2* __restrict__ Y, cplx<T>* __restrict__ work, const int* __restrict__ kactive,
+                                int* __restrict__ info, int in_smem) {
+  using V = cplx<T>;
   const int m = blockIdx.x, k = blockIdx.y;
   if (kactive && !kactive[k]) return;
-  __shared__ double sv[256];
-  __shared__ int si[256];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T wv[32];
+  __shared__ int wi[32];
   __shared__ int piv;
-  double2* W = work + ((size_t)k * p + m) * (size_t)q * (q + 1);
+  V* W = in_smem ? reinterpret_cast<V*>(smem_raw) : work + ((size_t)k * p + m) * (size_t)q * (q + 1);
   const double2* Ak = A + k * sA;
   const double sm = s[(size_t)k * p + m];
   for (size_t e = threadIdx.x; e < (size_t)q * (q + 1); e += blockDim.x) {
@@ -662,94 +686,123 @@ __global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int
     } else {
       v = C[k * sC + (size_t)m * ldc + i];
     }
-    W[e] = v;
+    W[e] = to_c<T>(v);
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int c = 0; c < q; ++c) {
-    double best = -1.0;
-    int bi = c;
+    // pivot: largest |w_ic|^2 over i >= c, ties to the smaller index
+    T best = (T)-1;
+    int bi = q;
     for (int i = c + threadIdx.x; i < q; i += blockDim.x) {
-      const double v = cabs2(W[(size_t)c * q + i]);
+      const V w = W[(size_t)c * q + i];
+      const T v = w.x * w.x + w.y * w.y;
       if (v > best) {
         best = v;
         bi = i;
       }
     }
-    sv[threadIdx.x] = best;
-    si[threadIdx.x] = bi;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) {
-        const double o = sv[threadIdx.x + h];
-        const int oi = si[threadIdx.x + h];
-        if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-          sv[threadIdx.x] = o;
-          si[threadIdx.x] = oi;
-        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
       }
-      __syncthreads();
     }
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bi;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      piv = si[0];
-      if (!(sv[0] > 0.0) && info) info[k * p + m] = c + 1;
+      T b = wv[0];
+      int r = wi[0];
+      for (int w = 1; w < nwarp; ++w)
+        if (wv[w] > b || (wv[w] == b && wi[w] < r)) {
+          b = wv[w];
+          r = wi[w];
+        }
+      if (!(b > (T)0)) {
+        r = c;
+        if (info) info[k * p + m] = c + 1;
+      }
+      piv = r;
     }
     __syncthreads();
     const int r = piv;
     if (r != c) {
       for (int j = c + threadIdx.x; j <= q; j += blockDim.x) {
-        const double2 t = W[(size_t)j * q + c];
+        const V t = W[(size_t)j * q + c];
         W[(size_t)j * q + c] = W[(size_t)j * q + r];
         W[(size_t)j * q + r] = t;
       }
+      __syncthreads();
     }
-    __syncthreads();
-    const double2 d = W[(size_t)c * q + c];
-    const double dd = cabs2(d);
-    const double2 dinv = dd > 0 ? make_double2(d.x / dd, -d.y / dd) : make_double2(0.0, 0.0);
+    const V d = W[(size_t)c * q + c];
+    const T dd = d.x * d.x + d.y * d.y;
+    V dinv;
+    dinv.x = dd > (T)0 ? d.x / dd : (T)0;
+    dinv.y = dd > (T)0 ? -d.y / dd : (T)0;
     const int rows = q - c - 1;
     for (size_t e = threadIdx.x; e < (size_t)rows * (q - c); e += blockDim.x) {
       const int jj = (int)(e / rows), ii = (int)(e - (size_t)jj * rows);
       const int i = c + 1 + ii, j = c + 1 + jj;
-      const double2 f = cmul(W[(size_t)c * q + i], dinv);
+      const V f = cmul(W[(size_t)c * q + i], dinv);
       W[(size_t)j * q + i] = W[(size_t)j * q + i] - cmul(f, W[(size_t)j * q + c]);
     }
     __syncthreads();
   }
-  // back substitution, rhs in column q
+  // back substitution on the upper triangle, column oriented; rhs (column q) becomes y
+  V* rhs = W + (size_t)q * q;
   for (int i = q - 1; i >= 0; --i) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int j = i + 1 + threadIdx.x; j < q; j += blockDim.x) acc = cfma(W[(size_t)j * q + i], W[(size_t)q * q + j], acc);
-    sv[threadIdx.x] = acc.x;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) sv[threadIdx.x] += sv[threadIdx.x + h];
-      __syncthreads();
-    }
-    const double rx = sv[0];
-    __syncthreads();
-    sv[threadIdx.x] = acc.y;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) sv[threadIdx.x] += sv[threadIdx.x + h];
-      __syncthreads();
-    }
-    const double ry = sv[0];
     if (threadIdx.x == 0) {
-      const double2 d = W[(size_t)i * q + i];
-      const double dd = cabs2(d);
-      const double2 rhs = W[(size_t)q * q + i] - make_double2(rx, ry);
-      W[(size_t)q * q + i] = dd > 0 ? cmul(rhs, make_double2(d.x / dd, -d.y / dd)) : make_double2(0.0, 0.0);
+      const V d = W[(size_t)i * q + i];
+      const T dd = d.x * d.x + d.y * d.y;
+      V yi;
+      if (dd > (T)0) {
+        V di;
+        di.x = d.x / dd;
+        di.y = -d.y / dd;
+        yi = cmul(rhs[i], di);
+      } else {
+        yi.x = 0;
+        yi.y = 0;
+      }
+      rhs[i] = yi;
     }
+    __syncthreads();
+    const V yi = rhs[i];
+    for (int j = threadIdx.x; j < i; j += blockDim.x) rhs[j] = rhs[j] - cmul(W[(size_t)i * q + j], yi);
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < q; i += blockDim.x) Y[k * sC + (size_t)m * ldc + i] = W[(size_t)q * q + i];
+  for (int i = threadIdx.x; i < q; i += blockDim.x) Y[k * sC + (size_t)m * ldc + i] = to_d(rhs[i]);
+}
+
+size_t fom_shifted_work(int K, int p, int q, int prec) {
+  return (size_t)K * p * q * (q + 1) * (prec ? sizeof(float2) : sizeof(double2));
 }
 
 void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s, const double2* C,
-                       int ldc, size_t sC, double2* Y, double2* work, const int* kactive, int* info,
+                       int ldc, size_t sC, double2* Y, void* work, const int* kactive, int* info, int prec,
                        cudaStream_t st) {
   dim3 g(p, K);
-  k_shifted_solve<<<g, 256, 0, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, work, kactive, info);
+  const size_t es = prec ? sizeof(float2) : sizeof(double2);
+  const size_t need = (size_t)q * (q + 1) * es;
+  const bool in_smem = need <= 200 * 1024;
+  const size_t sm = in_smem ? need : 0;
+  const int threads = q <= 64 ? 128 : 256;
+  if (prec) {
+    if (in_smem) cudaFuncSetAttribute(k_shifted_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_shifted_solve<float><<<g, threads, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (float2*)work, kactive, info,
+                                                   in_smem ? 1 : 0);
+  } else {
+    if (in_smem) cudaFuncSetAttribute(k_shifted_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_shifted_solve<double><<<g, threads, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (double2*)work, kactive,
+                                                    info, in_smem ? 1 : 0);
+  }
+  count_launch();
 }
 
 __global__ void k_mirror(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ kactive) {
@@ -762,7 +815,10 @@ __global__ void k_mirror(int q0, int p, double2* A, int lda, size_t sA, const in
   }
 }
 void fom_mirror(int K, int q0, int p, double2* A, int lda, size_t sA, const int* kactive, cudaStream_t st) {
-  if (q0 > 0) k_mirror<<<K, 256, 0, st>>>(q0, p, A, lda, sA, kactive);
+  if (q0 > 0) {
+    k_mirror<<<K, 256, 0, st>>>(q0, p, A, lda, sA, kactive);
+  count_launch();
+  }
 }
 
 __global__ void k_pad_diag(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ nzero, double big) {
@@ -774,6 +830,7 @@ __global__ void k_pad_diag(int q0, int p, double2* A, int lda, size_t sA, const 
 }
 void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, double big, cudaStream_t st) {
   k_pad_diag<<<K, 64, 0, st>>>(q0, p, A, lda, sA, nzero, big);
+  count_launch();
 }
 
 // ----------------------------------------------------------------------------- small helpers
@@ -800,6 +857,7 @@ __global__ void k_orth_scale(int p, const double2* __restrict__ U, const double*
 void small_orth_scale(int K, int p, const double2* U, const double* w, const double* lref, double tol, double2* M,
                       int* nzero, cudaStream_t st) {
   k_orth_scale<<<K, 256, 0, st>>>(p, U, w, lref, tol, M, nzero);
+  count_launch();
 }
 
 __global__ void k_put_herm_block(int p, const double2* __restrict__ src, double2* A, int lda, size_t sA, int q0) {
@@ -814,6 +872,7 @@ __global__ void k_put_herm_block(int p, const double2* __restrict__ src, double2
 }
 void small_put_herm_block(int K, int p, const double2* src, double2* A, int lda, size_t sA, int q0, cudaStream_t st) {
   k_put_herm_block<<<K, 256, 0, st>>>(p, src, A, lda, sA, q0);
+  count_launch();
 }
 
 __global__ void k_take_y(int q, int qcap, int p, const double2* __restrict__ Y, double2* __restrict__ Yf,
@@ -828,6 +887,7 @@ __global__ void k_take_y(int q, int qcap, int p, const double2* __restrict__ Y, 
 }
 void small_take_y(int K, int q, int qcap, int p, const double2* Y, double2* Yf, const int* take, cudaStream_t st) {
   k_take_y<<<K, 256, 0, st>>>(q, qcap, p, Y, Yf, take);
+  count_launch();
 }
 
 __global__ void k_max_eval(int K, int p, const double* __restrict__ w, double* __restrict__ out) {
@@ -839,6 +899,7 @@ __global__ void k_max_eval(int K, int p, const double* __restrict__ w, double* _
 }
 void small_max_eval(int K, int p, const double* w, double* out, cudaStream_t st) {
   k_max_eval<<<(K + 127) / 128, 128, 0, st>>>(K, p, w, out);
+  count_launch();
 }
 
 __global__ void k_conj_transpose(int p, const double2* __restrict__ A, double2* __restrict__ out) {
@@ -850,6 +911,7 @@ __global__ void k_conj_transpose(int p, const double2* __restrict__ A, double2* 
 }
 void small_conj_transpose(int K, int p, const double2* A, double2* out, cudaStream_t st) {
   k_conj_transpose<<<K, 256, 0, st>>>(p, A, out);
+  count_launch();
 }
 
 __global__ void k_add_herm(int p, const double2* __restrict__ A, double sc, double2* __restrict__ out) {
@@ -862,6 +924,7 @@ __global__ void k_add_herm(int p, const double2* __restrict__ A, double sc, doub
 }
 void small_add_herm(int K, int p, const double2* A, double s, double2* out, cudaStream_t st) {
   k_add_herm<<<K, 256, 0, st>>>(p, A, s, out);
+  count_launch();
 }
 
 __global__ void k_sqrt_vals(int n, const double* __restrict__ w, double* __restrict__ out) {
@@ -870,6 +933,7 @@ __global__ void k_sqrt_vals(int n, const double* __restrict__ w, double* __restr
 }
 void small_sqrt_vals(int K, int p, const double* w, double* out, cudaStream_t st) {
   k_sqrt_vals<<<(K * p + 127) / 128, 128, 0, st>>>(K * p, w, out);
+  count_launch();
 }
 
 }  // namespace eacg

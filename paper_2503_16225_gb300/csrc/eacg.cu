@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -97,7 +98,51 @@ struct eacg_system {
   long long h_apps = 0;
   int last_fom_max = 0;
   int ls_total = 0;
+  // ---- live kernel timing
+  struct ProfRec {
+    int slot;
+    cudaEvent_t a, b;
+    double bytes, units;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
 };
+
+namespace {
+std::atomic<long long> g_launches{0};
+const char* const PROF_NAMES[] = {"xpass_inv", "plane_h", "xpass_fwd", "nonlocal", "xpass_inv_rho",
+                                  "plane_rho", "potential", "fom_shifted_solve"};
+enum { P_XINV = 0, P_PLANE_H, P_XFWD, P_NONLOCAL, P_XINV_RHO, P_PLANE_RHO, P_POT, P_FOMSOLVE, P_NSLOTS };
+
+cudaEvent_t prof_event(eacg_system* s) {
+  if (s->evused == s->evpool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    s->evpool.push_back(e);
+  }
+  return s->evpool[s->evused++];
+}
+}  // namespace
+
+void eacg::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Records CUDA events around a kernel (group) when profiling is on.
+#define PROF_RUN(slot, bytes_, units_, ...)                                       \
+  do {                                                                            \
+    cudaEvent_t a_ = nullptr;                                                     \
+    if (s->prof_on) {                                                             \
+      a_ = prof_event(s);                                                         \
+      cudaEventRecord(a_, s->st);                                                 \
+    }                                                                             \
+    __VA_ARGS__;                                                                  \
+    if (s->prof_on) {                                                             \
+      cudaEvent_t b_ = prof_event(s);                                             \
+      cudaEventRecord(b_, s->st);                                                 \
+      s->prof.push_back({(slot), a_, b_, (double)(bytes_), (double)(units_)});    \
+    }                                                                             \
+  } while (0)
 
 // ============================================================================ helpers
 #define CK(call)                                                                  \
@@ -502,19 +547,29 @@ static eacg_status fom_reserve(eacg_system* s, int qneed) {
 // out = H in with the current potential (prec 0: FP64 transforms, 1: FP32).
 static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out, int prec, const int* kactive) {
   const int nb = s->K * s->p;
-  grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st);
-  grid_plane_h(s->g, prec, s->d_tbuf, prec ? (const void*)s->d_vtot32 : (const void*)s->d_vtot, nb, kactive, s->st);
+  // algorithmic bytes per band (see DESIGN): coefficients read/written in FP64, the x-pass
+  // intermediate (N * ncols values of the transform precision) written, read, written, read
+  const double tv = prec ? 8.0 : 16.0;
+  const double inter = (double)s->N * s->ncols * tv;
+  const double coef = (double)s->n_max * 16.0;
   const double N3 = (double)s->N * s->N * s->N;
-  grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st);
+  PROF_RUN(P_XINV, nb * (coef + inter), nb, grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st));
+  PROF_RUN(P_PLANE_H, nb * 2.0 * inter + N3 * (prec ? 4.0 : 8.0), nb,
+           grid_plane_h(s->g, prec, s->d_tbuf, prec ? (const void*)s->d_vtot32 : (const void*)s->d_vtot, nb, kactive,
+                        s->st));
+  PROF_RUN(P_XFWD, nb * (inter + 2.0 * coef), nb,
+           grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
   CKL(s);
   if (s->nproj > 0) {
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
-    dense_gemm_cn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np, ONE,
-                  ZERO, s->cn_work, kactive, s->st);
-    dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
-    dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
-    dense_gemm_nn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm, nm, ONE,
-                  ONE, kactive, s->st);
+    PROF_RUN(P_NONLOCAL, (double)K * np * nm * 16.0 * 2 + 3.0 * nb * coef, nb, {
+      dense_gemm_cn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np,
+                    ONE, ZERO, s->cn_work, kactive, s->st);
+      dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
+      dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
+      dense_gemm_nn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm, nm,
+                    ONE, ONE, kactive, s->st);
+    });
     CKL(s);
   }
   s->h_apps += (long long)s->K * s->p;
@@ -526,20 +581,27 @@ static eacg_status density_and_potential(eacg_system* s, const double2* phi, int
   const int nb = s->K * s->p;
   const int N = s->N;
   const size_t N3 = (size_t)N * N * N;
-  grid_xpass_inv(s->g, prec, phi, s->d_tbuf, nb, nullptr, s->st);
-  grid_plane_rho(s->g, prec, s->d_tbuf, nb, s->rho_groups, s->d_bw, s->d_partial, s->st);
-  grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
+  const double tv = prec ? 8.0 : 16.0;
+  const double inter = (double)s->N * s->ncols * tv;
+  PROF_RUN(P_XINV_RHO, nb * ((double)s->n_max * 16.0 + inter), nb,
+           grid_xpass_inv(s->g, prec, phi, s->d_tbuf, nb, nullptr, s->st));
+  PROF_RUN(P_PLANE_RHO, nb * inter + (double)s->rho_groups * N3 * 8.0, nb, {
+    grid_plane_rho(s->g, prec, s->d_tbuf, nb, s->rho_groups, s->d_bw, s->d_partial, s->st);
+    grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
+  });
   CKL(s);
-  if (s->hartree) {
-    grid_real_to_complex(s->d_rho, s->d_fft3, N3, s->st);
-    grid_fft3(s->g, s->d_fft3, false, s->st);
-    grid_hartree_scale(s->d_fft3, N, s->b, s->st);
-    grid_fft3(s->g, s->d_fft3, true, s->st);
-    grid_complex_real_part(s->d_fft3, s->d_vh, N3, s->st);
-    CKL(s);
-  }
-  const int nblk = grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, s->hartree, s->xc, s->d_vtot, s->d_vtot32,
-                                    s->d_esum, s->st);
+  int nblk = 0;
+  PROF_RUN(P_POT, (double)N3 * 8.0 * 8, 0, {
+    if (s->hartree) {
+      grid_real_to_complex(s->d_rho, s->d_fft3, N3, s->st);
+      grid_fft3(s->g, s->d_fft3, false, s->st);
+      grid_hartree_scale(s->d_fft3, N, s->b, s->st);
+      grid_fft3(s->g, s->d_fft3, true, s->st);
+      grid_complex_real_part(s->d_fft3, s->d_vh, N3, s->st);
+    }
+    nblk = grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, s->hartree, s->xc, s->d_vtot, s->d_vtot32, s->d_esum,
+                            s->st);
+  });
   CKL(s);
   return (nblk == 256) ? EACG_OK : EACG_ECUDA;
 }
@@ -776,8 +838,9 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
     // Y = solve(A Y - Y Sigma = C_j) via C~ = C Q, (A - s_m) y~_m = c~_m, Y = Y~ Q^H
     dense_gemm_nn(K, q, p, p, s->fC, sC, s->qcap, s->sigv, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
                   s->d_kactive, s->st);
-    fom_shifted_solve(K, p, q, s->fA, s->qcap, sA, s->eval, s->fYt, s->qcap, sC, s->fY, s->fwork, s->d_kactive,
-                      nullptr, s->st);
+    PROF_RUN(P_FOMSOLVE, (double)K * p * q * (q + 1) * 16.0 * 2, 0,
+             fom_shifted_solve(K, p, q, s->fA, s->qcap, sA, s->eval, s->fYt, s->qcap, sC, s->fY, s->fwork,
+                               s->d_kactive, nullptr, prec, s->st));
     dense_gemm_nn(K, q, p, p, s->fY, sC, s->qcap, s->sigvh, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
                   s->d_kactive, s->st);
     // fYt now holds Y.  Res = C - (W Y - V Y Sigma)
@@ -999,7 +1062,11 @@ static eacg_status transport_g(eacg_system* s, double tau) {
 // <r, g_EA> <= 0.  Returns <r, g> in *rg and the kind (1 EA, 0 preconditioned) in *kind.
 static eacg_status direction(eacg_system* s, int prec, double* rg, int* kind) {
   if (s->phase == 1) {
-    TRY(ea_gradient(s, s->phi, s->hphi, s->lam, s->gv, prec, nullptr));
+    // The FOM stops at a relative Sylvester residual of 2.5e-2, five orders above FP32
+    // rounding: in mixed mode its H applications and projected solves stay in FP32 at every
+    // residual level (the residual, energy and retraction stay FP64).
+    (void)prec;
+    TRY(ea_gradient(s, s->phi, s->hphi, s->lam, s->gv, s->prm.precision ? 1 : 0, nullptr));
     pairing_dev(s, s->res, s->gv, 0, true);
     TRY(sync_read(s, 1));
     if (s->h_out[0] > 0) {
@@ -1252,6 +1319,7 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
 extern "C" void eacg_destroy(eacg_system* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
+  for (cudaEvent_t e : s->evpool) cudaEventDestroy(e);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_out) cudaFreeHost(s->h_out);
   if (s->h_int) cudaFreeHost(s->h_int);
@@ -1442,3 +1510,36 @@ extern "C" eacg_status eacg_solve_host(eacg_system* s, const double* psi0_host, 
   }
   return st;
 }
+
+extern "C" eacg_status eacg_profile_enable(eacg_system* s, int on) {
+  SYS_CHECK(s);
+  CK(cudaStreamSynchronize(s->st));
+  s->prof.clear();
+  s->evused = 0;
+  s->prof_on = on != 0;
+  return EACG_OK;
+}
+
+extern "C" int eacg_profile_read(eacg_system* s, eacg_kernel_stat* out, int max) {
+  if (!s) return -(int)EACG_EINVAL;
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return -(int)EACG_ECUDA;
+  eacg_kernel_stat acc[P_NSLOTS];
+  std::memset(acc, 0, sizeof(acc));
+  for (int i = 0; i < P_NSLOTS; ++i) std::snprintf(acc[i].name, sizeof(acc[i].name), "%s", PROF_NAMES[i]);
+  for (const auto& r : s->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return -(int)EACG_ECUDA;
+    acc[r.slot].launches += 1;
+    acc[r.slot].ms += ms;
+    acc[r.slot].bytes += r.bytes;
+    acc[r.slot].units += r.units;
+  }
+  s->prof.clear();
+  s->evused = 0;
+  int n = 0;
+  for (int i = 0; i < P_NSLOTS && n < max; ++i)
+    if (acc[i].launches > 0) out[n++] = acc[i];
+  return n;
+}
+
+extern "C" long long eacg_launch_count(void) { return g_launches.load(); }

@@ -494,6 +494,7 @@ static void launch_xinv(const GridCtx& g, const double2* psi, void* tbuf, const 
   cudaFuncSetAttribute(k_xpass_inv<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_xpass_inv<T, E><<<grid, threads, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf, g.plan,
                                                (const cplx<T>*)tw, cpc, kactive);
+  count_launch();
 }
 
 template <typename T, int E>
@@ -506,6 +507,7 @@ static void launch_xfwd(const GridCtx& g, const void* tbuf, const void* tw, cons
   cudaFuncSetAttribute(k_xpass_fwd<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_xpass_fwd<T, E><<<grid, threads, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, g.plan, (const cplx<T>*)tw,
                                                cpc, g.n_max, g.p, g.nk, psi_in, kin, scale, out, kactive);
+  count_launch();
 }
 
 template <typename T>
@@ -528,6 +530,7 @@ static void launch_plane_h(const GridCtx& g, void* tbuf, const void* tw, const v
   dim3 grid(g.plan.N, nbands);
   k_plane_h<T, E><<<grid, plane_threads(g.plan), sm, st>>>((cplx<T>*)tbuf, g.ncols, g.colfy, g.colfz, g.ylist, g.ny,
                                                            (const T*)v, g.plan, (const cplx<T>*)tw, g.p, kactive);
+  count_launch();
 }
 
 template <typename T, int E>
@@ -542,6 +545,7 @@ static void launch_plane_rho(const GridCtx& g, const void* tbuf, const void* tw,
   dim3 grid(g.plan.N, groups);
   k_plane_rho<T, E><<<grid, threads, sm, st>>>((const cplx<T>*)tbuf, g.ncols, g.colfy, g.colfz, g.ylist, g.ny,
                                                g.plan, (const cplx<T>*)tw, nbands, bpg, bw, partial);
+  count_launch();
 }
 
 #define EACG_DISPATCH_E(E_, CALL)                              \
@@ -593,6 +597,7 @@ void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, in
 
 void grid_reduce_groups(const double* partial, int G, size_t n, double* out, cudaStream_t st) {
   k_reduce_groups<<<(int)min((size_t)1024, (n + 255) / 256), 256, 0, st>>>(partial, G, n, out);
+  count_launch();
 }
 
 template <int E, bool INV>
@@ -604,6 +609,7 @@ static void launch_fft3(const GridCtx& g, double2* a, int axis, cudaStream_t st)
   const int blocks = (N * N + lpc - 1) / lpc;
   cudaFuncSetAttribute(k_fft3_axis<E, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_fft3_axis<E, INV><<<blocks, threads, sm, st>>>(a, axis, g.plan, (const double2*)g.tw64, lpc);
+  count_launch();
 }
 
 void grid_fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
@@ -619,39 +625,50 @@ void grid_fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
 void grid_build_sphere(int N, int K, const double* kfrac_d, double thr, double b, int n_max_cap, int* nk, int* row_off,
                        int* m, double* kin, int* colmark, cudaStream_t st) {
   k_sphere_build<<<K, 256, 0, st>>>(N, kfrac_d, thr, b, n_max_cap, nk, row_off, m, kin, colmark);
+  count_launch();
 }
 void grid_columns(int N, const int* colmark, int* colidx, int* colfy, int* colfz, int* ncols, int* ylist, int* ny,
                   cudaStream_t st) {
   k_columns<<<1, 32, 0, st>>>(N, colmark, colidx, colfy, colfz, ncols, ylist, ny);
+  count_launch();
 }
 void grid_xmap(int N, int K, int n_max, const int* nk, const int* m, const int* colidx, int ncols, int* xmap,
                cudaStream_t st) {
   k_fill_int<<<256, 256, 0, st>>>(xmap, (size_t)K * ncols * N, -1);
+  count_launch();
   dim3 grid((n_max + 255) / 256, K);
   k_xmap<<<grid, 256, 0, st>>>(N, K, n_max, nk, m, colidx, ncols, xmap);
+  count_launch();
 }
-void grid_fill_int(int* p, size_t n, int v, cudaStream_t st) { k_fill_int<<<256, 256, 0, st>>>(p, n, v); }
+void grid_fill_int(int* p, size_t n, int v, cudaStream_t st) { k_fill_int<<<256, 256, 0, st>>>(p, n, v);
+  count_launch(); }
 void grid_vloc_g(int N, double b, double omega, int natoms, const double* pos, const double* Z, const double* rc,
                  double2* out, cudaStream_t st) {
   k_vloc_g<<<1024, 256, 0, st>>>(N, b, omega, natoms, pos, Z, rc, out);
+  count_launch();
 }
-void grid_hartree_scale(double2* a, int N, double b, cudaStream_t st) { k_hartree_scale<<<1024, 256, 0, st>>>(a, N, b); }
+void grid_hartree_scale(double2* a, int N, double b, cudaStream_t st) { k_hartree_scale<<<1024, 256, 0, st>>>(a, N, b);
+  count_launch(); }
 void grid_real_to_complex(const double* r, double2* c, size_t n, cudaStream_t st) {
   k_real_to_complex<<<1024, 256, 0, st>>>(r, c, n);
+  count_launch();
 }
 void grid_complex_real_part(const double2* c, double* r, size_t n, cudaStream_t st) {
   k_complex_real_part<<<1024, 256, 0, st>>>(c, r, n);
+  count_launch();
 }
 int grid_vtot_energy(size_t n, const double* vloc, const double* vh, const double* rho, int hartree, int xc,
                      double* vtot, float* vtot32, double* blocksums, cudaStream_t st) {
   const int blocks = 256;
   k_vtot_energy<<<blocks, 256, 0, st>>>(n, vloc, vh, rho, hartree, xc, vtot, vtot32, blocksums);
+  count_launch();
   return blocks;
 }
 void grid_projectors(int K, int n_max, const int* nk, const int* m, const double* kfrac, double b, double omega,
                      int natoms, const double* pos, int npa, double w, double2* B, cudaStream_t st) {
   dim3 grid(256, K);
   k_projectors<<<grid, 256, 0, st>>>(K, n_max, nk, m, kfrac, b, omega, natoms, pos, npa, w, B);
+  count_launch();
 }
 
 }  // namespace eacg

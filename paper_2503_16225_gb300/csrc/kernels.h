@@ -8,6 +8,9 @@
 
 namespace eacg {
 
+// Counts one kernel launch of this library (defined in eacg.cu).
+void count_launch();
+
 // Device-side description of the plane-wave grid of one system.
 struct GridCtx {
   FftPlan plan;
@@ -98,9 +101,12 @@ void dense_kin_energy(int K, int p, int n_max, const double* kin, const double2*
 
 // ---- fom_kernels.cu
 // Solve (A[k] - s[k][m] I) y = c for every (k, m): A q x q (lda), c/y columns of q x p (ldc).
+// prec 0: FP64 elimination, 1: FP32 elimination (FP64 in and out).  work: fom_shifted_work bytes
+// (used only when q x (q+1) does not fit in shared memory).
+size_t fom_shifted_work(int K, int p, int q, int prec);
 void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s,
-                       const double2* C, int ldc, size_t sC, double2* Y, double2* work, const int* kactive,
-                       int* info, cudaStream_t st);
+                       const double2* C, int ldc, size_t sC, double2* Y, void* work, const int* kactive,
+                       int* info, int prec, cudaStream_t st);
 // A[k][i][j] for i in [q0, q0 + p) and j < q0: conj of A[k][j][i] (Hermitian mirror).
 void fom_mirror(int K, int q0, int p, double2* A, int lda, size_t sA, const int* kactive, cudaStream_t st);
 // Rows of A with zero new columns: A[k][q0 + i][q0 + i] = big for i < nzero[k].
