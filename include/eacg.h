@@ -183,6 +183,22 @@ int eacg_profile_read(eacg_system* sys, eacg_kernel_stat* out, int max);
 /* Number of kernels this library has launched in the process so far. */
 long long eacg_launch_count(void);
 
+/* Allocation-free block overlaps (the paper has no counterpart; this serves callers that
+ * cannot allocate device memory, e.g. code inside a pool that forbids cudaMalloc or a step
+ * that must not allocate between graph replays).  Computes c_k = a_k^* b_k for k < K, where
+ * a_k, b_k are n x p complex double blocks (column-major, ld n, laid out [K][p][n]) and c_k
+ * is p x p column-major ([K][p][p]); all three are caller-owned device buffers.  Needs no
+ * system and calls no allocator: its scratch is a fixed device array of
+ * EACG_NOALLOC_MAX_PARTIALS complex doubles (8 MiB), held by every GPU that loads the library
+ * until the process exits, and shared by all calls.  Returns EACG_EINVAL when
+ * K * ceil(n / 1024) * p * p exceeds EACG_NOALLOC_MAX_PARTIALS or an argument is invalid.
+ * The first call on a device looks up the scratch address for that device (make it before
+ * any stream capture).  stream: cudaStream_t or NULL; the call returns after synchronising
+ * it.  Calls that overlap on the GPU (other host threads or streams) race on the scratch. */
+#define EACG_NOALLOC_MAX_PARTIALS 524288
+eacg_status eacg_overlap_noalloc(int K, int n, int p, const double* a_dev, const double* b_dev, double* c_dev,
+                                 void* stream);
+
 /* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
 eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);
 /* Iterates eacg_step until ||R||_F <= res_tol or max_outer; result in *out. */

@@ -97,6 +97,7 @@ def _load():
         "eacg_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "eacg_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(EacgKernelStat), ctypes.c_int]),
         "eacg_launch_count": (ctypes.c_longlong, []),
+        "eacg_overlap_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -276,6 +277,13 @@ def eacg_profile_read(sys):
 
 def eacg_launch_count():
     return int(lib.eacg_launch_count())
+
+
+def eacg_overlap_noalloc(a, b, c, stream=None):
+    """c[k] = a[k]^* b[k] for complex128 tensors a, b [K, p, n] and c [K, p, p] (column-major
+    p x p per k), through the allocation-free entry point; returns the eacg_status code."""
+    K, p, n = a.shape
+    return int(lib.eacg_overlap_noalloc(K, n, p, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
 
 
 class System:
