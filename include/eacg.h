@@ -168,14 +168,17 @@ eacg_status eacg_retract(eacg_system* sys, const double* phi_dev, const double* 
 /* Live kernel timing (no counterpart in the paper; used for roofline reports).
  * eacg_profile_enable(sys, 1) clears and starts recording CUDA events around the main
  * kernels of the Hamiltonian application, density, potential and FOM solves on the
- * system's stream; eacg_profile_read writes up to max entries (name, launches, summed
- * device milliseconds, summed algorithmic bytes, summed work units = band applications)
- * and returns their number (negative eacg_status on error).  Reading clears the records. */
+ * system's stream; eacg_profile_read writes up to max entries (name with the precision of
+ * the variant, launches, summed device milliseconds, summed algorithmic bytes, summed
+ * algorithmic FLOPs (5 N log2 N per N-point transform), summed work units = band
+ * applications) and returns their number (negative eacg_status on error).  Reading clears
+ * the records. */
 typedef struct {
   char name[24];
   long long launches;
   double ms;
   double bytes;
+  double flops;
   double units;
 } eacg_kernel_stat;
 eacg_status eacg_profile_enable(eacg_system* sys, int on);

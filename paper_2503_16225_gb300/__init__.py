@@ -60,7 +60,7 @@ class EacgResult(ctypes.Structure):
 
 class EacgKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("units", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double), ("units", ctypes.c_double)]
 
 
 class EacgError(RuntimeError):
@@ -272,7 +272,7 @@ def eacg_profile_read(sys):
     if n < 0:
         raise EacgError(-n, eacg_last_error(sys))
     return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "bytes": buf[i].bytes,
-                                   "units": buf[i].units} for i in range(n)}
+                                   "flops": buf[i].flops, "units": buf[i].units} for i in range(n)}
 
 
 def eacg_launch_count():

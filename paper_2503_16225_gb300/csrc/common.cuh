@@ -74,5 +74,13 @@ template <typename V>
 __device__ __forceinline__ double2 to_d(V a) {
   return make_double2((double)a.x, (double)a.y);
 }
+// complex conversion between any of float2 / double2
+template <typename D, typename S>
+__device__ __forceinline__ D cvt(S a) {
+  D r;
+  r.x = (decltype(r.x))a.x;
+  r.y = (decltype(r.y))a.y;
+  return r;
+}
 
 }  // namespace eacg

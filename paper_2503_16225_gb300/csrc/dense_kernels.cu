@@ -7,6 +7,8 @@
 // not depend on scheduling.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -21,6 +23,8 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // 
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
 // ----------------------------------------------------------------------------- A^H B
+// Templated on the block precision T (double or float): A and B are cplx<T>, the products
+// are accumulated in T within a chunk of rows, the chunk partials and the result are FP64.
 constexpr int CN_TILE = 16;
 constexpr int CN_CHUNK = 1024;  // rows per partial
 constexpr int CN_SUB = 32;      // rows staged per step
@@ -30,9 +34,18 @@ size_t dense_cn_work(int K, int L, int m, int n) {
   return (size_t)K * nch * m * n;
 }
 
-__global__ void k_gemm_cn_partial(int L, int m, int n, const double2* __restrict__ A, size_t sA, int lda,
-                                  const double2* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+
+template <typename T>
+__global__ void k_gemm_cn_partial(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
+                                  const cplx<T>* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
                                   const int* __restrict__ kactive) {
+  using V = cplx<T>;
   const int k = blockIdx.z;
   if (kactive && !kactive[k]) return;
   const int tiles_m = (m + CN_TILE - 1) / CN_TILE;
@@ -40,25 +53,28 @@ __global__ void k_gemm_cn_partial(int L, int m, int n, const double2* __restrict
   const int ch = blockIdx.y, nch = gridDim.y;
   const int ti = threadIdx.x % CN_TILE, tj = threadIdx.x / CN_TILE;
   const int i0 = tm * CN_TILE, j0 = tn * CN_TILE;
-  __shared__ double2 sa[CN_SUB][CN_TILE + 1];
-  __shared__ double2 sb[CN_SUB][CN_TILE + 1];
-  const double2* Ak = A + k * sA;
-  const double2* Bk = B + k * sB;
-  double2 acc = make_double2(0.0, 0.0);
+  __shared__ V sa[CN_SUB][CN_TILE + 1];
+  __shared__ V sb[CN_SUB][CN_TILE + 1];
+  const V* Ak = A + k * sA;
+  const V* Bk = B + k * sB;
+  V zero;
+  zero.x = 0;
+  zero.y = 0;
+  V acc = zero;
   const int l_beg = ch * CN_CHUNK, l_end = min(L, l_beg + CN_CHUNK);
   for (int l0 = l_beg; l0 < l_end; l0 += CN_SUB) {
     for (int e = threadIdx.x; e < CN_SUB * CN_TILE; e += blockDim.x) {
       const int c = e / CN_SUB, r = e - c * CN_SUB;
       const int l = l0 + r;
-      sa[r][c] = (l < l_end && i0 + c < m) ? Ak[(size_t)(i0 + c) * lda + l] : make_double2(0.0, 0.0);
-      sb[r][c] = (l < l_end && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + l] : make_double2(0.0, 0.0);
+      sa[r][c] = (l < l_end && i0 + c < m) ? Ak[(size_t)(i0 + c) * lda + l] : zero;
+      sb[r][c] = (l < l_end && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + l] : zero;
     }
     __syncthreads();
 #pragma unroll 8
     for (int r = 0; r < CN_SUB; ++r) acc = cfmac(sa[r][ti], sb[r][tj], acc);
     __syncthreads();
   }
-  if (i0 + ti < m && j0 + tj < n) part[(((size_t)k * nch + ch) * n + (j0 + tj)) * m + (i0 + ti)] = acc;
+  if (i0 + ti < m && j0 + tj < n) part[(((size_t)k * nch + ch) * n + (j0 + tj)) * m + (i0 + ti)] = to_d(acc);
 }
 
 __global__ void k_gemm_cn_reduce(int m, int n, int nch, const double2* __restrict__ part, double2* __restrict__ C,
@@ -76,51 +92,70 @@ __global__ void k_gemm_cn_reduce(int m, int n, int nch, const double2* __restric
   }
 }
 
-void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
-                   int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
-                   const int* kactive, cudaStream_t st) {
+template <typename T>
+static void gemm_cn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const cplx<T>* B, size_t sB,
+                      int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
+                      const int* kactive, cudaStream_t st) {
   if (K <= 0 || m <= 0 || n <= 0) return;
   const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
   const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
   dim3 g1(tiles, nch > 0 ? nch : 1, K);
   if (nch > 0) {
-    k_gemm_cn_partial<<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
-  count_launch();
+    k_gemm_cn_partial<T><<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+    count_launch();
   }
   dim3 g2((m * n + 255) / 256, K);
   k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
   count_launch();
 }
 
+void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
+                   int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
+                   const int* kactive, cudaStream_t st) {
+  gemm_cn_t<double>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, work, kactive, st);
+}
+void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const float2* B, size_t sB,
+                     int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
+                     const int* kactive, cudaStream_t st) {
+  gemm_cn_t<float>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, work, kactive, st);
+}
+
 // ----------------------------------------------------------------------------- A B (small B)
+// C (L x n, cplx<T>) = alpha A (L x m, cplx<T>) B (m x n, FP64, staged in T) + beta C.
 constexpr int NN_COLS = 8;
 constexpr int NN_ROWS = 64;
-__global__ void k_gemm_nn(int L, int m, int n, const double2* __restrict__ A, size_t sA, int lda,
-                          const double2* __restrict__ B, size_t sB, int ldb, double2* __restrict__ C, size_t sC,
+template <typename T>
+__global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
+                          const double2* __restrict__ B, size_t sB, int ldb, cplx<T>* __restrict__ C, size_t sC,
                           int ldc, double2 alpha, double2 beta, const int* __restrict__ kactive) {
+  using V = cplx<T>;
   const int k = blockIdx.y;
   if (kactive && !kactive[k]) return;
-  __shared__ double2 sb[NN_ROWS][NN_COLS];
+  __shared__ V sb[NN_ROWS][NN_COLS];
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  const double2* Ak = A + k * sA;
+  const V* Ak = A + k * sA;
   const double2* Bk = B + k * sB;
-  double2* Ck = C + k * sC;
+  V* Ck = C + k * sC;
   const bool bz = (beta.x == 0.0 && beta.y == 0.0);
+  const V al = to_c<T>(alpha), be = to_c<T>(beta);
+  V zero;
+  zero.x = 0;
+  zero.y = 0;
   for (int j0 = 0; j0 < n; j0 += NN_COLS) {
-    double2 acc[NN_COLS];
+    V acc[NN_COLS];
 #pragma unroll
-    for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = make_double2(0.0, 0.0);
+    for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = zero;
     for (int i0 = 0; i0 < m; i0 += NN_ROWS) {
       __syncthreads();
       for (int e = threadIdx.x; e < NN_ROWS * NN_COLS; e += blockDim.x) {
         const int r = e / NN_COLS, c = e - r * NN_COLS;
-        sb[r][c] = (i0 + r < m && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + i0 + r] : make_double2(0.0, 0.0);
+        sb[r][c] = (i0 + r < m && j0 + c < n) ? to_c<T>(Bk[(size_t)(j0 + c) * ldb + i0 + r]) : zero;
       }
       __syncthreads();
       if (l < L) {
         const int iend = min(NN_ROWS, m - i0);
         for (int r = 0; r < iend; ++r) {
-          const double2 a = Ak[(size_t)(i0 + r) * lda + l];
+          const V a = Ak[(size_t)(i0 + r) * lda + l];
 #pragma unroll
           for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = cfma(a, sb[r][jj], acc[jj]);
         }
@@ -130,9 +165,9 @@ __global__ void k_gemm_nn(int L, int m, int n, const double2* __restrict__ A, si
 #pragma unroll
       for (int jj = 0; jj < NN_COLS; ++jj) {
         if (j0 + jj < n) {
-          double2* cp = Ck + (size_t)(j0 + jj) * ldc + l;
-          double2 r = cmul(alpha, acc[jj]);
-          if (!bz) r = r + cmul(beta, *cp);
+          V* cp = Ck + (size_t)(j0 + jj) * ldc + l;
+          V r = cmul(al, acc[jj]);
+          if (!bz) r = r + cmul(be, *cp);
           *cp = r;
         }
       }
@@ -140,12 +175,91 @@ __global__ void k_gemm_nn(int L, int m, int n, const double2* __restrict__ A, si
   }
 }
 
+template <typename T>
+static void gemm_nn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const double2* B, size_t sB,
+                      int ldb, cplx<T>* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
+                      cudaStream_t st) {
+  if (K <= 0 || L <= 0 || n <= 0) return;
+  dim3 g((L + 127) / 128, K);
+  k_gemm_nn<T><<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
+  count_launch();
+}
+
 void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                    cudaStream_t st) {
-  if (K <= 0 || L <= 0 || n <= 0) return;
-  dim3 g((L + 127) / 128, K);
-  k_gemm_nn<<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
+  gemm_nn_t<double>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
+}
+void dense_gemm_nn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B, size_t sB,
+                     int ldb, float2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
+                     cudaStream_t st) {
+  gemm_nn_t<float>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
+}
+
+// ----------------------------------------------------------------------------- FP32 block helpers
+__global__ void k_to32(size_t n, const double2* __restrict__ x, double sc, float2* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = make_float2((float)(sc * x[i].x), (float)(sc * x[i].y));
+}
+__global__ void k_to64(size_t n, const float2* __restrict__ x, double2* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = make_double2((double)x[i].x, (double)x[i].y);
+}
+// out = a x + b y (y may be null), FP32 blocks with FP64 scalars
+__global__ void k_axpby32(size_t n, double2 a, const float2* __restrict__ x, double2 b, const float2* __restrict__ y,
+                          float2* __restrict__ out) {
+  const float2 af = make_float2((float)a.x, (float)a.y), bf = make_float2((float)b.x, (float)b.y);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float2 r = cmul(af, x[i]);
+    if (y) r = r + cmul(bf, y[i]);
+    out[i] = r;
+  }
+}
+__global__ void k_norms2_32(size_t len, const float2* __restrict__ V, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int k = blockIdx.x;
+  const float2* v = V + (size_t)k * len;
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < len; i += blockDim.x) s += (double)v[i].x * v[i].x + (double)v[i].y * v[i].y;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+    if (threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = sh[0];
+}
+__global__ void k_tpa32(int p, int n_max, const double* __restrict__ kin, const double* __restrict__ alpha,
+                        const float2* __restrict__ in, float2* __restrict__ out) {
+  const int k = blockIdx.y;
+  const size_t tot = (size_t)p * n_max;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n_max), g = (int)(e % n_max);
+    const float f = (float)(1.0 / (kin[(size_t)k * n_max + g] + alpha[(size_t)k * p + i]));
+    const float2 v = in[(size_t)k * tot + e];
+    out[(size_t)k * tot + e] = make_float2(v.x * f, v.y * f);
+  }
+}
+void dense_to32(size_t n, const double2* x, double sc, float2* y, cudaStream_t st) {
+  k_to32<<<(int)std::min((size_t)2048, (n + 255) / 256 + 1), 256, 0, st>>>(n, x, sc, y);
+  count_launch();
+}
+void dense_to64(size_t n, const float2* x, double2* y, cudaStream_t st) {
+  k_to64<<<(int)std::min((size_t)2048, (n + 255) / 256 + 1), 256, 0, st>>>(n, x, y);
+  count_launch();
+}
+void dense_axpby32(size_t n, double2 a, const float2* x, double2 b, const float2* y, float2* out, cudaStream_t st) {
+  k_axpby32<<<(int)std::min((size_t)2048, (n + 255) / 256 + 1), 256, 0, st>>>(n, a, x, b, y, out);
+  count_launch();
+}
+void dense_norms2_32(int K, size_t len, const float2* V, double* out, cudaStream_t st) {
+  k_norms2_32<<<K, 256, 0, st>>>(len, V, out);
+  count_launch();
+}
+void dense_tpa32(int K, int p, int n_max, const double* kin, const double* alpha, const float2* in, float2* out,
+                 cudaStream_t st) {
+  dim3 g(64, K);
+  k_tpa32<<<g, 256, 0, st>>>(p, n_max, kin, alpha, in, out);
   count_launch();
 }
 
@@ -159,16 +273,14 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
   const int pe = p + (p & 1);  // even number of slots (a dummy index when p is odd)
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* V = A + p * p;
-  int* slot = reinterpret_cast<int*>(V + p * p);   // [pe] current pairing order
-  double* rot = reinterpret_cast<double*>(slot + pe + (pe & 1));  // [pe/2][4]: c, s, cos phi, sin phi
-  double* red = rot + 2 * pe;                      // [2]
+  double* rot = reinterpret_cast<double*>(V + p * p);  // [pe/2][4]: c, s, cos phi, sin phi
+  double* red = rot + 2 * pe;                          // [2]
   const double2* Ak = Ag + k * sA;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     A[e] = Ak[e];
     const int j = e / p, i = e - j * p;
     V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
-  for (int i = threadIdx.x; i < pe; i += blockDim.x) slot[i] = i;
   __syncthreads();
   // symmetrise exactly
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -184,7 +296,9 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
   }
   __syncthreads();
   const int npair = pe / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  // round-robin pairing (circle method): slot 0 fixed, slots 1..pe-1 rotate by one per round
+  auto slot = [pe](int pos, int round) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (pe - 1); };
+  for (int sweep = 0; sweep < 20; ++sweep) {
     if (threadIdx.x == 0) {
       double off = 0.0, dia = 0.0;
       for (int j = 0; j < p; ++j)
@@ -199,12 +313,17 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
       red[1] = dia;
     }
     __syncthreads();
-    if (!(red[0] > 1e-32 * (red[0] + red[1]))) break;
+    // converged when the off-diagonal norm is below 1e-14 of the matrix norm (above the
+    // rounding floor sqrt(p) eps ||A|| of the rotations, at the accuracy of LAPACK's eigh)
+    const double fro2 = red[0] + red[1];
+    const bool done = !(red[0] > 1e-28 * fro2);
     __syncthreads();
+    if (done) break;
+    const double negligible = 1e-16 * sqrt(fro2) / p;
     for (int round = 0; round < pe - 1; ++round) {
-      // rotation parameters for each pair (top[t] = slot[t], bot[t] = slot[pe-1-t])
+      // rotation parameters for each pair
       for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-        int i = slot[t], j = slot[pe - 1 - t];
+        int i = slot(t, round), j = slot(pe - 1 - t, round);
         if (i > j) {
           const int q = i;
           i = j;
@@ -214,7 +333,7 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
         if (j < p) {
           const double2 b = A[j * p + i];
           const double r = sqrt(cabs2(b));
-          if (r > 1e-300) {
+          if (r > 1e-300 && r > negligible) {
             const double a = A[i * p + i].x, d = A[j * p + j].x;
             const double zeta = (d - a) / (2.0 * r);
             const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -233,7 +352,7 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
       // columns: (A_ki, A_kj) <- (c A_ki - s e^{-i phi} A_kj, s A_ki + c e^{-i phi} A_kj); same for V
       for (int e = threadIdx.x; e < npair * p; e += blockDim.x) {
         const int t = e / p, r = e - t * p;
-        int i = slot[t], j = slot[pe - 1 - t];
+        int i = slot(t, round), j = slot(pe - 1 - t, round);
         if (i > j) {
           const int q = i;
           i = j;
@@ -254,10 +373,11 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
         }
       }
       __syncthreads();
-      // rows: (A_ik, A_jk) <- (c A_ik - s e^{i phi} A_jk, s A_ik + c e^{i phi} A_jk)
+      // rows: (A_ik, A_jk) <- (c A_ik - s e^{i phi} A_jk, s A_ik + c e^{i phi} A_jk); the annihilated
+      // pair is set to exactly zero and the diagonal kept real
       for (int e = threadIdx.x; e < npair * p; e += blockDim.x) {
         const int t = e / p, col = e - t * p;
-        int i = slot[t], j = slot[pe - 1 - t];
+        int i = slot(t, round), j = slot(pe - 1 - t, round);
         if (i > j) {
           const int q = i;
           i = j;
@@ -267,29 +387,14 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
         const double c = rot[4 * t], s = rot[4 * t + 1];
         const double2 ep = make_double2(rot[4 * t + 2], rot[4 * t + 3]);
         const double2 ai = A[col * p + i], aj = cmul(ep, A[col * p + j]);
-        A[col * p + i] = make_double2(c * ai.x - s * aj.x, c * ai.y - s * aj.y);
-        A[col * p + j] = make_double2(s * ai.x + c * aj.x, s * ai.y + c * aj.y);
-      }
-      __syncthreads();
-      // exact zero of the annihilated pairs, then rotate the pairing (slot 0 fixed)
-      if (threadIdx.x == 0) {
-        for (int t = 0; t < npair; ++t) {
-          int i = slot[t], j = slot[pe - 1 - t];
-          if (i > j) {
-            const int q = i;
-            i = j;
-            j = q;
-          }
-          if (j < p && rot[4 * t + 1] != 0.0) {
-            A[j * p + i] = make_double2(0.0, 0.0);
-            A[i * p + j] = make_double2(0.0, 0.0);
-          }
-          A[i * p + i].y = 0.0;
-          if (j < p) A[j * p + j].y = 0.0;
-        }
-        const int last = slot[pe - 1];
-        for (int q = pe - 1; q > 1; --q) slot[q] = slot[q - 1];
-        slot[1] = last;
+        double2 ni = make_double2(c * ai.x - s * aj.x, c * ai.y - s * aj.y);
+        double2 nj = make_double2(s * ai.x + c * aj.x, s * ai.y + c * aj.y);
+        if (s != 0.0 && col == j) ni = make_double2(0.0, 0.0);  // (i, j)
+        if (s != 0.0 && col == i) nj = make_double2(0.0, 0.0);  // (j, i)
+        if (col == i) ni.y = 0.0;
+        if (col == j) nj.y = 0.0;
+        A[col * p + i] = ni;
+        A[col * p + j] = nj;
       }
       __syncthreads();
     }
@@ -311,9 +416,9 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
 void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
                 cudaStream_t st) {
   const int pe = p + (p & 1);
-  const size_t sm = sizeof(double2) * 2 * p * p + sizeof(int) * (pe + 2) + sizeof(double) * (2 * pe + 2) + 16;
-  cudaFuncSetAttribute(k_heig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int threads = p <= 16 ? 128 : 256;
+  const size_t sm = sizeof(double2) * 2 * p * p + sizeof(double) * (2 * pe + 2) + 16;
+  ensure_smem((const void*)k_heig, sm);
+  const int threads = p <= 16 ? 64 : 256;
   k_heig<<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
   count_launch();
 }
@@ -414,7 +519,7 @@ __global__ void k_inverse(int p, const double2* __restrict__ A, double2* __restr
 
 void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st) {
   const size_t sm = sizeof(double2) * 2 * p * p;
-  cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ensure_smem((const void*)k_inverse, sm);
   k_inverse<<<K, 256, sm, st>>>(p, A, Ainv, info);
   count_launch();
 }
@@ -466,7 +571,7 @@ __global__ void k_lyap(int p, const double2* __restrict__ Vg, const double* __re
 
 void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st) {
   const size_t sm = sizeof(double2) * 3 * p * p;
-  cudaFuncSetAttribute(k_lyap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ensure_smem((const void*)k_lyap, sm);
   k_lyap<<<K, 256, sm, st>>>(p, V, s, M, X);
   count_launch();
 }
@@ -659,9 +764,24 @@ void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStre
 
 // ----------------------------------------------------------------------------- FOM projected solves
 // One CTA per (m, k): Gaussian elimination with partial pivoting of [A - s_m I | c_m] (q x (q+1),
-// column-major) in the working precision T, then column-oriented back substitution; y is written
-// (in FP64) to column m of Y (ld ldc).  The working matrix lives in shared memory when it fits,
-// else in the global work buffer (one q x (q+1) slice per (k, m)).
+// column-major) in the working precision T, then back substitution; y is written (in FP64) to
+// column m of Y (ld ldc).  The pivot search of column c + 1 is fused into the elimination of
+// column c: each thread keeps the largest packed (|w|^2, row) key it produced, a warp shuffle
+// reduces the keys and one shared atomic per warp combines them.  Ties go to the smaller row.
+// Two barriers per column (row swap, elimination) and one per back-substitution row.  The
+// working matrix lives in shared memory when it fits, else in the global work buffer.
+__device__ __forceinline__ unsigned long long piv_key(float v, int row) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - (unsigned)row);
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
 template <typename T>
 __global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int lda, size_t sA,
                                 const double* __restrict__ s, const double2* __restrict__ C, int ldc, size_t sC,
@@ -671,12 +791,17 @@ __global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int
   const int m = blockIdx.x, k = blockIdx.y;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T wv[32];
-  __shared__ int wi[32];
-  __shared__ int piv;
+  __shared__ unsigned long long key[2];
   V* W = in_smem ? reinterpret_cast<V*>(smem_raw) : work + ((size_t)k * p + m) * (size_t)q * (q + 1);
   const double2* Ak = A + k * sA;
   const double sm = s[(size_t)k * p + m];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    key[0] = 0ull;
+    key[1] = 0ull;
+  }
+  __syncthreads();
+  unsigned long long mine = 0ull;
   for (size_t e = threadIdx.x; e < (size_t)q * (q + 1); e += blockDim.x) {
     const int j = (int)(e / q), i = (int)(e - (size_t)j * q);
     double2 v;
@@ -686,97 +811,75 @@ __global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int
     } else {
       v = C[k * sC + (size_t)m * ldc + i];
     }
-    W[e] = to_c<T>(v);
+    const V w = to_c<T>(v);
+    W[e] = w;
+    if (j == 0) {
+      const unsigned long long kk = piv_key((float)(w.x * w.x + w.y * w.y), i);
+      mine = kk > mine ? kk : mine;
+    }
   }
+  mine = warp_max_key(mine);
+  if (lane == 0 && mine) atomicMax(&key[0], mine);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int c = 0; c < q; ++c) {
-    // pivot: largest |w_ic|^2 over i >= c, ties to the smaller index
-    T best = (T)-1;
-    int bi = q;
-    for (int i = c + threadIdx.x; i < q; i += blockDim.x) {
-      const V w = W[(size_t)c * q + i];
-      const T v = w.x * w.x + w.y * w.y;
-      if (v > best) {
-        best = v;
-        bi = i;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      wv[warp] = best;
-      wi[warp] = bi;
-    }
-    __syncthreads();
+    const unsigned long long kc = key[c & 1];
+    int r = (int)(0xffffffffu - (unsigned)(kc & 0xffffffffull));
+    r = min(max(r, c), q - 1);  // rows c..q-1 each posted a key, so r is in range; keep it there
     if (threadIdx.x == 0) {
-      T b = wv[0];
-      int r = wi[0];
-      for (int w = 1; w < nwarp; ++w)
-        if (wv[w] > b || (wv[w] == b && wi[w] < r)) {
-          b = wv[w];
-          r = wi[w];
-        }
-      if (!(b > (T)0)) {
-        r = c;
-        if (info) info[k * p + m] = c + 1;
-      }
-      piv = r;
+      key[(c + 1) & 1] = 0ull;
+      if ((kc >> 32) == 0ull && info) info[k * p + m] = c + 1;
     }
-    __syncthreads();
-    const int r = piv;
     if (r != c) {
       for (int j = c + threadIdx.x; j <= q; j += blockDim.x) {
         const V t = W[(size_t)j * q + c];
         W[(size_t)j * q + c] = W[(size_t)j * q + r];
         W[(size_t)j * q + r] = t;
       }
-      __syncthreads();
     }
+    __syncthreads();
     const V d = W[(size_t)c * q + c];
     const T dd = d.x * d.x + d.y * d.y;
     V dinv;
     dinv.x = dd > (T)0 ? d.x / dd : (T)0;
     dinv.y = dd > (T)0 ? -d.y / dd : (T)0;
     const int rows = q - c - 1;
+    mine = 0ull;
     for (size_t e = threadIdx.x; e < (size_t)rows * (q - c); e += blockDim.x) {
       const int jj = (int)(e / rows), ii = (int)(e - (size_t)jj * rows);
       const int i = c + 1 + ii, j = c + 1 + jj;
       const V f = cmul(W[(size_t)c * q + i], dinv);
-      W[(size_t)j * q + i] = W[(size_t)j * q + i] - cmul(f, W[(size_t)j * q + c]);
-    }
-    __syncthreads();
-  }
-  // back substitution on the upper triangle, column oriented; rhs (column q) becomes y
-  V* rhs = W + (size_t)q * q;
-  for (int i = q - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) {
-      const V d = W[(size_t)i * q + i];
-      const T dd = d.x * d.x + d.y * d.y;
-      V yi;
-      if (dd > (T)0) {
-        V di;
-        di.x = d.x / dd;
-        di.y = -d.y / dd;
-        yi = cmul(rhs[i], di);
-      } else {
-        yi.x = 0;
-        yi.y = 0;
+      const V nw = W[(size_t)j * q + i] - cmul(f, W[(size_t)j * q + c]);
+      W[(size_t)j * q + i] = nw;
+      if (jj == 0) {
+        const unsigned long long kk = piv_key((float)(nw.x * nw.x + nw.y * nw.y), i);
+        mine = kk > mine ? kk : mine;
       }
-      rhs[i] = yi;
     }
-    __syncthreads();
-    const V yi = rhs[i];
-    for (int j = threadIdx.x; j < i; j += blockDim.x) rhs[j] = rhs[j] - cmul(W[(size_t)i * q + j], yi);
+    mine = warp_max_key(mine);
+    if (lane == 0 && mine) atomicMax(&key[(c + 1) & 1], mine);
     __syncthreads();
   }
+  // back substitution on the upper triangle, column oriented; every thread computes y_c itself
+  // (nobody writes rhs[c] in step c), then updates its share of rhs[0..c)
+  V* rhs = W + (size_t)q * q;
+  for (int c = q - 1; c >= 0; --c) {
+    const V d = W[(size_t)c * q + c];
+    const T dd = d.x * d.x + d.y * d.y;
+    V yc;
+    if (dd > (T)0) {
+      V di;
+      di.x = d.x / dd;
+      di.y = -d.y / dd;
+      yc = cmul(rhs[c], di);
+    } else {
+      yc.x = 0;
+      yc.y = 0;
+    }
+    for (int i = threadIdx.x; i < c; i += blockDim.x) rhs[i] = rhs[i] - cmul(W[(size_t)c * q + i], yc);
+    __syncthreads();
+    if (threadIdx.x == 0) rhs[c] = yc;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < q; i += blockDim.x) Y[k * sC + (size_t)m * ldc + i] = to_d(rhs[i]);
 }
 
@@ -794,11 +897,11 @@ void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA
   const size_t sm = in_smem ? need : 0;
   const int threads = q <= 64 ? 128 : 256;
   if (prec) {
-    if (in_smem) cudaFuncSetAttribute(k_shifted_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (in_smem) ensure_smem((const void*)k_shifted_solve<float>, sm);
     k_shifted_solve<float><<<g, threads, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (float2*)work, kactive, info,
                                                    in_smem ? 1 : 0);
   } else {
-    if (in_smem) cudaFuncSetAttribute(k_shifted_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (in_smem) ensure_smem((const void*)k_shifted_solve<double>, sm);
     k_shifted_solve<double><<<g, threads, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (double2*)work, kactive,
                                                     info, in_smem ? 1 : 0);
   }

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -67,13 +69,14 @@ struct eacg_system {
   float* d_vtot32 = nullptr;
   double2* d_fft3 = nullptr;
   double2 *d_B = nullptr, *d_P = nullptr, *d_P2 = nullptr;
+  float2* d_B32 = nullptr;
   void* d_tbuf = nullptr;
   int rho_groups = 1;
   // blocks
   double2 *phi = nullptr, *hphi = nullptr, *res = nullptr, *eta = nullptr, *gv = nullptr, *teta = nullptr,
           *tg = nullptr, *psi_t = nullptr, *phi_t = nullptr, *hphi_t = nullptr, *res_t = nullptr, *teta_t = nullptr,
           *tmp1 = nullptr, *tmp2 = nullptr, *tmp3 = nullptr, *Xb = nullptr, *Cb = nullptr, *fvt = nullptr,
-          *fwt = nullptr;
+          *fwt = nullptr, *c32 = nullptr;
   // small [K][p][p]
   double2 *lam = nullptr, *lam_t = nullptr, *sm1 = nullptr, *sm2 = nullptr, *sm3 = nullptr, *evec = nullptr,
           *evec_t = nullptr, *sinv_t = nullptr, *sig = nullptr, *sigv = nullptr, *sigvh = nullptr;
@@ -91,6 +94,7 @@ struct eacg_system {
   double2 *fV = nullptr, *fW = nullptr, *fA = nullptr, *fC = nullptr, *fY = nullptr, *fYt = nullptr, *fYf = nullptr,
           *fwork = nullptr;
   size_t fwork_elems = 0;
+  size_t fom_es = sizeof(double2);  // element bytes of the Krylov blocks V, W
   // ---- iteration state
   int fresh = 1, have_psi = 0, phase = 0, iter = 0, warm_iter = 0, cur_prec = 0;
   double E = 0, rnorm = 0, tau = 1, rg = 0;
@@ -102,7 +106,7 @@ struct eacg_system {
   struct ProfRec {
     int slot;
     cudaEvent_t a, b;
-    double bytes, units;
+    double bytes, flops, units;
   };
   bool prof_on = false;
   std::vector<ProfRec> prof;
@@ -112,9 +116,17 @@ struct eacg_system {
 
 namespace {
 std::atomic<long long> g_launches{0};
-const char* const PROF_NAMES[] = {"xpass_inv", "plane_h", "xpass_fwd", "nonlocal", "xpass_inv_rho",
-                                  "plane_rho", "potential", "fom_shifted_solve"};
-enum { P_XINV = 0, P_PLANE_H, P_XFWD, P_NONLOCAL, P_XINV_RHO, P_PLANE_RHO, P_POT, P_FOMSOLVE, P_NSLOTS };
+// slots of the FP64 variants; the FP32 variant of a slot is slot + P_F32
+const char* const PROF_NAMES[] = {"xpass_inv_f64",  "plane_h_f64",  "xpass_fwd_f64", "nonlocal_f64",
+                                  "xpass_rho_f64",  "plane_rho_f64", "fom_solve_f64", "potential",
+                                  "xpass_inv_f32",  "plane_h_f32",  "xpass_fwd_f32", "nonlocal_f32",
+                                  "xpass_rho_f32",  "plane_rho_f32", "fom_solve_f32", "unused",
+                                  "fom_setup",      "fom_residual", "fom_orth",      "fom_block",
+                                  "trial_retract",  "fom_final",    "unused2",       "unused3"};
+enum { P_XINV = 0, P_PLANE_H, P_XFWD, P_NONLOCAL, P_XINV_RHO, P_PLANE_RHO, P_FOMSOLVE, P_POT, P_F32,
+       P_FOM_SETUP = 16, P_FOM_RES, P_FOM_ORTH, P_FOM_BLOCK, P_TRIAL_RET, P_FOM_FINAL, P_NSLOTS = 24 };
+// algorithmic FLOPs of one N-point complex transform (5 N log2 N convention)
+inline double fft_flops(int N) { return 5.0 * N * std::log2((double)N); }
 
 cudaEvent_t prof_event(eacg_system* s) {
   if (s->evused == s->evpool.size()) {
@@ -128,8 +140,24 @@ cudaEvent_t prof_event(eacg_system* s) {
 
 void eacg::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+std::mutex g_smem_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_set;
+}  // namespace
+
+void eacg::ensure_smem(const void* func, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  size_t& cur = g_smem_set[{dev, func}];
+  if (bytes > cur) {
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+      cur = bytes;
+  }
+}
+
 // Records CUDA events around a kernel (group) when profiling is on.
-#define PROF_RUN(slot, bytes_, units_, ...)                                       \
+#define PROF_RUN(slot, bytes_, flops_, units_, ...)                                       \
   do {                                                                            \
     cudaEvent_t a_ = nullptr;                                                     \
     if (s->prof_on) {                                                             \
@@ -140,7 +168,7 @@ void eacg::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
     if (s->prof_on) {                                                             \
       cudaEvent_t b_ = prof_event(s);                                             \
       cudaEventRecord(b_, s->st);                                                 \
-      s->prof.push_back({(slot), a_, b_, (double)(bytes_), (double)(units_)});    \
+      s->prof.push_back({(slot), a_, b_, (double)(bytes_), (double)(flops_), (double)(units_)}); \
     }                                                                             \
   } while (0)
 
@@ -425,6 +453,9 @@ static eacg_status build_potential_and_projectors(eacg_system* s) {
     grid_projectors(s->K, s->n_max, s->d_nk, s->d_m, s->d_kfrac, s->b, s->omega, s->natoms, s->d_pos, s->npa,
                     s->width, s->d_B, s->st);
     CKL(s);
+    TRY(dalloc(s, &s->d_B32, sizeof(float2) * (size_t)s->K * s->nproj * s->n_max));
+    dense_to32((size_t)s->K * s->nproj * s->n_max, s->d_B, 1.0, s->d_B32, s->st);
+    CKL(s);
   }
   return EACG_OK;
 }
@@ -434,7 +465,7 @@ static eacg_status alloc_work(eacg_system* s) {
   s->blk = (size_t)K * p * s->n_max;
   const size_t bb = sizeof(double2) * s->blk;
   double2** blocks[] = {&s->phi, &s->hphi, &s->res, &s->eta, &s->gv, &s->teta, &s->tg, &s->psi_t, &s->phi_t,
-                        &s->hphi_t, &s->res_t, &s->teta_t, &s->tmp1, &s->tmp2, &s->tmp3, &s->Xb, &s->Cb, &s->fvt, &s->fwt};
+                        &s->hphi_t, &s->res_t, &s->teta_t, &s->tmp1, &s->tmp2, &s->tmp3, &s->Xb, &s->Cb, &s->fvt, &s->fwt, &s->c32};
   for (auto b : blocks) TRY(dalloc(s, b, bb));
   const size_t sp = sizeof(double2) * (size_t)K * p * p;
   double2** smalls[] = {&s->lam, &s->lam_t, &s->sm1, &s->sm2, &s->sm3, &s->evec, &s->evec_t, &s->sinv_t,
@@ -445,7 +476,7 @@ static eacg_status alloc_work(eacg_system* s) {
   // tbuf: one FP64 complex value per (band, jx, column)
   TRY(dalloc(s, &s->d_tbuf, sizeof(double2) * (size_t)K * p * N * s->ncols));
   // rho groups: enough CTAs to fill the GPU
-  s->rho_groups = std::max(1, std::min(K * p, (2 * 152 + N - 1) / N));
+  s->rho_groups = std::max(1, std::min(K * p, (8 * 152 + N - 1) / N));
   TRY(dalloc(s, &s->d_partial, sizeof(double) * (size_t)s->rho_groups * N * N * N));
   TRY(dalloc(s, &s->d_bw, sizeof(double) * (size_t)K * p));
   {
@@ -476,12 +507,15 @@ static eacg_status alloc_work(eacg_system* s) {
 }
 
 // Krylov storage for q columns per k; grows by doubling and keeps the contents.
+// Strides and leading dimensions in elements of es bytes (16: complex128, 8: complex64).
 static eacg_status copy_cols(eacg_system* s, double2* dst, int ldd, size_t sd, const double2* src, int lds, size_t ss,
-                             int rows, int cols) {
+                             int rows, int cols, size_t es = sizeof(double2)) {
   if (!src || rows <= 0 || cols <= 0) return EACG_OK;
+  char* d = reinterpret_cast<char*>(dst);
+  const char* c = reinterpret_cast<const char*>(src);
   for (int k = 0; k < s->K; ++k) {
-    CK(cudaMemcpy2DAsync(dst + k * sd, sizeof(double2) * ldd, src + k * ss, sizeof(double2) * lds,
-                         sizeof(double2) * rows, cols, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpy2DAsync(d + k * sd * es, es * ldd, c + k * ss * es, es * lds, es * rows, cols,
+                         cudaMemcpyDeviceToDevice, s->st));
   }
   return EACG_OK;
 }
@@ -502,8 +536,8 @@ static eacg_status fom_reserve(eacg_system* s, int qneed) {
   TRY(dalloc(s, &nYf, sizeof(double2) * (size_t)K * qc * p));
   const int oc = s->qcap;
   if (oc > 0) {
-    TRY(copy_cols(s, nV, nm, (size_t)qc * nm, s->fV, nm, (size_t)oc * nm, nm, oc));
-    TRY(copy_cols(s, nW, nm, (size_t)qc * nm, s->fW, nm, (size_t)oc * nm, nm, oc));
+    TRY(copy_cols(s, nV, nm, (size_t)qc * nm, s->fV, nm, (size_t)oc * nm, nm, oc, s->fom_es));
+    TRY(copy_cols(s, nW, nm, (size_t)qc * nm, s->fW, nm, (size_t)oc * nm, nm, oc, s->fom_es));
     TRY(copy_cols(s, nA, qc, (size_t)qc * qc, s->fA, oc, (size_t)oc * oc, oc, oc));
     TRY(copy_cols(s, nC, qc, (size_t)qc * p, s->fC, oc, (size_t)oc * p, oc, p));
     TRY(copy_cols(s, nY, qc, (size_t)qc * p, s->fY, oc, (size_t)oc * p, oc, p));
@@ -553,16 +587,20 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
   const double inter = (double)s->N * s->ncols * tv;
   const double coef = (double)s->n_max * 16.0;
   const double N3 = (double)s->N * s->N * s->N;
-  PROF_RUN(P_XINV, nb * (coef + inter), nb, grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st));
-  PROF_RUN(P_PLANE_H, nb * 2.0 * inter + N3 * (prec ? 4.0 : 8.0), nb,
+  const int off = prec ? P_F32 : 0;
+  const double fx = nb * s->ncols * fft_flops(s->N);
+  const double fp = nb * 2.0 * s->N * (s->ny + s->N) * fft_flops(s->N);
+  PROF_RUN(P_XINV + off, nb * (coef + inter), fx, nb,
+           grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st));
+  PROF_RUN(P_PLANE_H + off, nb * 2.0 * inter + N3 * (prec ? 4.0 : 8.0), fp, nb,
            grid_plane_h(s->g, prec, s->d_tbuf, prec ? (const void*)s->d_vtot32 : (const void*)s->d_vtot, nb, kactive,
                         s->st));
-  PROF_RUN(P_XFWD, nb * (inter + 2.0 * coef), nb,
+  PROF_RUN(P_XFWD + off, nb * (inter + 2.0 * coef), fx, nb,
            grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
   CKL(s);
   if (s->nproj > 0) {
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
-    PROF_RUN(P_NONLOCAL, (double)K * np * nm * 16.0 * 2 + 3.0 * nb * coef, nb, {
+    PROF_RUN(P_NONLOCAL, (double)K * np * nm * 16.0 * 2 + 3.0 * nb * coef, 16.0 * K * np * nm * p, nb, {
       dense_gemm_cn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np,
                     ONE, ZERO, s->cn_work, kactive, s->st);
       dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
@@ -583,15 +621,17 @@ static eacg_status density_and_potential(eacg_system* s, const double2* phi, int
   const size_t N3 = (size_t)N * N * N;
   const double tv = prec ? 8.0 : 16.0;
   const double inter = (double)s->N * s->ncols * tv;
-  PROF_RUN(P_XINV_RHO, nb * ((double)s->n_max * 16.0 + inter), nb,
+  const int off = prec ? P_F32 : 0;
+  PROF_RUN(P_XINV_RHO + off, nb * ((double)s->n_max * 16.0 + inter), nb * s->ncols * fft_flops(s->N), nb,
            grid_xpass_inv(s->g, prec, phi, s->d_tbuf, nb, nullptr, s->st));
-  PROF_RUN(P_PLANE_RHO, nb * inter + (double)s->rho_groups * N3 * 8.0, nb, {
+  PROF_RUN(P_PLANE_RHO + off, nb * inter + (double)s->rho_groups * N3 * 8.0,
+           nb * (double)s->N * (s->ny + s->N) * fft_flops(s->N), nb, {
     grid_plane_rho(s->g, prec, s->d_tbuf, nb, s->rho_groups, s->d_bw, s->d_partial, s->st);
     grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
   });
   CKL(s);
   int nblk = 0;
-  PROF_RUN(P_POT, (double)N3 * 8.0 * 8, 0, {
+  PROF_RUN(P_POT, (double)N3 * 8.0 * 8, 6.0 * N * N * fft_flops(N), 0, {
     if (s->hartree) {
       grid_real_to_complex(s->d_rho, s->d_fft3, N3, s->st);
       grid_fft3(s->g, s->d_fft3, false, s->st);
@@ -715,68 +755,171 @@ static eacg_status precond_gradient(eacg_system* s, const double2* phi, const do
   return EACG_OK;
 }
 
+// Kernel wrappers of one block precision for the FOM: T = double (FP64 mode) or float
+// (mixed mode, FP32 Krylov blocks and transforms; small projected matrices stay FP64).
+template <typename T>
+struct FomOps;
+template <>
+struct FomOps<double> {
+  using V = double2;
+  static constexpr double drop_tol = 1e-12;
+  static void cn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const V* B, size_t sB, int ldb,
+                 double2* C, size_t sC, int ldc, double2 al, double2 be, double2* w, const int* ka, cudaStream_t st) {
+    dense_gemm_cn(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, w, ka, st);
+  }
+  static void nn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const double2* B, size_t sB, int ldb,
+                 V* C, size_t sC, int ldc, double2 al, double2 be, const int* ka, cudaStream_t st) {
+    dense_gemm_nn(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, ka, st);
+  }
+  static void axpby(size_t n, double2 a, const V* x, double2 b, const V* y, V* o, cudaStream_t st) {
+    dense_axpby(n, a, x, b, y, o, st);
+  }
+  static void norms2(int K, size_t len, const V* v, double* o, cudaStream_t st) { dense_norms2(K, len, v, o, st); }
+  static void tpa(int K, int p, int nm, const double* kin, const double* al, const V* in, V* out, cudaStream_t st) {
+    dense_tpa(K, p, nm, kin, al, in, out, false, st);
+  }
+};
+template <>
+struct FomOps<float> {
+  using V = float2;
+  static constexpr double drop_tol = 1e-6;
+  static void cn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const V* B, size_t sB, int ldb,
+                 double2* C, size_t sC, int ldc, double2 al, double2 be, double2* w, const int* ka, cudaStream_t st) {
+    dense_gemm_cn32(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, w, ka, st);
+  }
+  static void nn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const double2* B, size_t sB, int ldb,
+                 V* C, size_t sC, int ldc, double2 al, double2 be, const int* ka, cudaStream_t st) {
+    dense_gemm_nn32(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, ka, st);
+  }
+  static void axpby(size_t n, double2 a, const V* x, double2 b, const V* y, V* o, cudaStream_t st) {
+    dense_axpby32(n, a, x, b, y, o, st);
+  }
+  static void norms2(int K, size_t len, const V* v, double* o, cudaStream_t st) { dense_norms2_32(K, len, v, o, st); }
+  static void tpa(int K, int p, int nm, const double* kin, const double* al, const V* in, V* out, cudaStream_t st) {
+    dense_tpa32(K, p, nm, kin, al, in, out, st);
+  }
+};
+
+// H applied to FP32 blocks with FP32 transforms (the FOM of the mixed mode).
+static eacg_status apply_H_block32(eacg_system* s, const float2* in, float2* out, const int* kactive) {
+  const int nb = s->K * s->p;
+  const double inter = (double)s->N * s->ncols * 8.0;
+  const double coef = (double)s->n_max * 8.0;
+  const double N3 = (double)s->N * s->N * s->N;
+  const double fx = nb * s->ncols * fft_flops(s->N);
+  const double fp = nb * 2.0 * s->N * (s->ny + s->N) * fft_flops(s->N);
+  PROF_RUN(P_XINV + P_F32, nb * (coef + inter), fx, nb,
+           grid_xpass_inv32(s->g, in, s->d_tbuf, nb, kactive, s->st));
+  PROF_RUN(P_PLANE_H + P_F32, nb * 2.0 * inter + N3 * 4.0, fp, nb,
+           grid_plane_h(s->g, 1, s->d_tbuf, s->d_vtot32, nb, kactive, s->st));
+  PROF_RUN(P_XFWD + P_F32, nb * (inter + 2.0 * coef), fx, nb,
+           grid_xpass_fwd32(s->g, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
+  CKL(s);
+  if (s->nproj > 0) {
+    const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
+    PROF_RUN(P_NONLOCAL + P_F32, (double)K * np * nm * 8.0 * 2 + 3.0 * nb * coef, 16.0 * K * np * nm * p, nb, {
+      dense_gemm_cn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np,
+                      ONE, ZERO, s->cn_work, kactive, s->st);
+      dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
+      dense_gemm_nn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm,
+                      nm, ONE, ONE, kactive, s->st);
+    });
+    CKL(s);
+  }
+  s->h_apps += (long long)s->K * s->p;
+  return EACG_OK;
+}
+
+static eacg_status apply_H_t(eacg_system* s, const double2* in, double2* out, const int* ka) {
+  return apply_H_block(s, in, out, 0, ka);
+}
+static eacg_status apply_H_t(eacg_system* s, const float2* in, float2* out, const int* ka) {
+  return apply_H_block32(s, in, out, ka);
+}
+
 // Rank-revealing orthonormalisation of R (n x p per k) against the first q columns of V
-// (Algorithm 4, reading: two projections, eigen-decomposition of the Gram matrix with
-// relative drop tolerance 1e-12 against the Gram of R before projection, second pass).
+// (Algorithm 4, reading: two projections, eigen-decomposition of the Gram matrix with a
+// relative drop tolerance against the Gram of R before projection, second pass).
 // Result into out (n x p per k, dropped directions as leading zero columns), nzero[k].
-static eacg_status orthonormalise(eacg_system* s, double2* R, const double2* V, int q, size_t sV, double2* out,
-                                  const int* kactive) {
+template <typename T>
+static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, int q, size_t sV, cplx<T>* out,
+                                  cplx<T>* scratch, const int* kactive) {
+  using O = FomOps<T>;
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
   // reference: largest Gram eigenvalue before projection
-  dense_gemm_cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
+  O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
   dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
   small_max_eval(K, p, s->sval, s->lref, s->st);
   if (q > 0) {
     for (int pass = 0; pass < 2; ++pass) {
-      dense_gemm_cn(K, nm, q, p, V, sV, nm, R, sb, nm, s->fYt, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work,
-                    kactive, s->st);
-      dense_gemm_nn(K, nm, q, p, V, sV, nm, s->fYt, (size_t)s->qcap * p, s->qcap, R, sb, nm, MONE, ONE, kactive, s->st);
+      O::cn(K, nm, q, p, V, sV, nm, R, sb, nm, s->fYt, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work, kactive,
+            s->st);
+      O::nn(K, nm, q, p, V, sV, nm, s->fYt, (size_t)s->qcap * p, s->qcap, R, sb, nm, MONE, ONE, kactive, s->st);
     }
   }
   // first pass
-  dense_gemm_cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
+  O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
   dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
-  small_orth_scale(K, p, s->sm2, s->sval, s->lref, 1e-12, s->sm3, s->d_nzero, s->st);
-  dense_gemm_nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, s->tmp3, sb, nm, ONE, ZERO, kactive, s->st);
+  small_orth_scale(K, p, s->sm2, s->sval, s->lref, O::drop_tol, s->sm3, s->d_nzero, s->st);
+  O::nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, scratch, sb, nm, ONE, ZERO, kactive, s->st);
   // second pass on the kept block
-  dense_gemm_cn(K, nm, p, p, s->tmp3, sb, nm, s->tmp3, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work,
-                kactive, s->st);
+  O::cn(K, nm, p, p, scratch, sb, nm, scratch, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive,
+        s->st);
   dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
   small_max_eval(K, p, s->sval, s->lref, s->st);
-  small_orth_scale(K, p, s->sm2, s->sval, s->lref, 1e-12, s->sm3, s->d_info, s->st);
-  dense_gemm_nn(K, nm, p, p, s->tmp3, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st);
+  small_orth_scale(K, p, s->sm2, s->sval, s->lref, O::drop_tol, s->sm3, s->d_info, s->st);
+  O::nn(K, nm, p, p, scratch, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st);
   CKL(s);
   return EACG_OK;
 }
 
 // Copies contiguous [K][p][n_max] blocks into columns [q0, q0 + p) of the Krylov storage.
-static eacg_status put_cols(eacg_system* s, const double2* v, const double2* w, int q0) {
-  const size_t wb = sizeof(double2) * (size_t)s->p * s->n_max;
-  const size_t dp = sizeof(double2) * (size_t)s->qcap * s->n_max;
-  CK(cudaMemcpy2DAsync(s->fV + (size_t)q0 * s->n_max, dp, v, wb, wb, s->K, cudaMemcpyDeviceToDevice, s->st));
-  CK(cudaMemcpy2DAsync(s->fW + (size_t)q0 * s->n_max, dp, w, wb, wb, s->K, cudaMemcpyDeviceToDevice, s->st));
+template <typename V>
+static eacg_status put_cols(eacg_system* s, const V* v, const V* w, int q0) {
+  const size_t wb = sizeof(V) * (size_t)s->p * s->n_max;
+  const size_t dp = sizeof(V) * (size_t)s->qcap * s->n_max;
+  V* fV = reinterpret_cast<V*>(s->fV);
+  V* fW = reinterpret_cast<V*>(s->fW);
+  CK(cudaMemcpy2DAsync(fV + (size_t)q0 * s->n_max, dp, v, wb, wb, s->K, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpy2DAsync(fW + (size_t)q0 * s->n_max, dp, w, wb, wb, s->K, cudaMemcpyDeviceToDevice, s->st));
   return EACG_OK;
 }
 
-// Energy-adaptive gradient by the preconditioned block FOM, per k (Algorithm 4, Sec. 5.2).
-// Uses the current potential (the one of phi).  fom_iters: host array of K ints or NULL.
-static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2* hphi, const double2* lam,
-                               double2* g, int prec, int* fom_iters) {
+// Energy-adaptive gradient by the preconditioned block FOM, per k (Algorithm 4, Sec. 5.2),
+// with Krylov blocks of precision T.  Uses the current potential (the one of phi).
+// fom_iters: host array of K ints or NULL.
+template <typename T>
+static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const double2* hphi, const double2* lam,
+                                 double2* g, int* fom_iters) {
+  using O = FomOps<T>;
+  using V = cplx<T>;
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
   const double mu = s->prm.mu;
+  const bool f32 = sizeof(T) == 4;
+  s->fom_es = sizeof(V);
   TRY(fom_reserve(s, 2 * p));
   // Sigma = Lambda - mu I, its eigenpairs and Q^H
   dense_shift_diag(K, p, lam, mu, s->sig, s->st);
   dense_heig(K, p, s->sig, (size_t)p * p, s->eval, s->sigv, nullptr, s->st);
   small_conj_transpose(K, p, s->sigv, s->sigvh, s->st);
   dense_kinetic_alpha(K, p, nm, s->d_kin, phi, s->alpha, s->st);
-  // C = Phi - (H X0 - X0 Sigma), X0 = Phi / mu, H X0 = H Phi / mu
+  // C = Phi - (H X0 - X0 Sigma), X0 = Phi / mu, H X0 = H Phi / mu  (FP64, then in T)
   dense_copy(s->Cb, hphi, s->blk, s->st);
   dense_gemm_nn(K, nm, p, p, phi, sb, nm, s->sig, (size_t)p * p, p, s->Cb, sb, nm, MONE, ONE, nullptr, s->st);
   dense_axpby(s->blk, ONE, phi, cr(-1.0 / mu), s->Cb, s->Cb, s->st);
   dense_norms2(K, sb, s->Cb, s->d_out + 64, s->st);
+  V* C = reinterpret_cast<V*>(s->Cb);
+  if (f32) {
+    C = reinterpret_cast<V*>(s->c32);
+    dense_to32(s->blk, s->Cb, 1.0, reinterpret_cast<float2*>(s->c32), s->st);
+  }
+  V* t1 = reinterpret_cast<V*>(s->tmp1);
+  V* t2 = reinterpret_cast<V*>(s->tmp2);
+  V* t3 = reinterpret_cast<V*>(s->tmp3);
+  V* vt = reinterpret_cast<V*>(s->fvt);
+  V* wt = reinterpret_cast<V*>(s->fwt);
   CKL(s);
   TRY(sync_read(s, 64 + K));
   std::vector<double> cnorm(K);
@@ -794,30 +937,30 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
   cudaMemsetAsync(s->fYf, 0, sizeof(double2) * (size_t)K * s->qcap * p, s->st);
   cudaMemsetAsync(s->fA, 0, sizeof(double2) * (size_t)K * s->qcap * s->qcap, s->st);
   // V_1 = orth(P^{-1} C), W_1 = H V_1, A_1 = herm(V_1^* W_1), C_1 = V_1^* C
-  dense_tpa(K, p, nm, s->d_kin, s->alpha, s->Cb, s->tmp2, false, s->st);
-  dense_zero(s->fvt, s->blk, s->st);
-  dense_zero(s->fwt, s->blk, s->st);
-  TRY(orthonormalise(s, s->tmp2, nullptr, 0, 0, s->fvt, s->d_kactive));
-  TRY(apply_H_block(s, s->fvt, s->fwt, prec, s->d_kactive));
-  TRY(put_cols(s, s->fvt, s->fwt, 0));
+  O::tpa(K, p, nm, s->d_kin, s->alpha, C, t2, s->st);
+  cudaMemsetAsync(vt, 0, sizeof(V) * s->blk, s->st);
+  cudaMemsetAsync(wt, 0, sizeof(V) * s->blk, s->st);
+  TRY(orthonormalise<T>(s, t2, nullptr, 0, 0, vt, t3, s->d_kactive));
+  TRY(apply_H_t(s, vt, wt, s->d_kactive));
+  TRY(put_cols(s, vt, wt, 0));
   int q = 0;
   auto add_block = [&](int q0) -> eacg_status {
     // columns [q0, q0 + p) of V and W are new: fill A and C
     const size_t sV = (size_t)s->qcap * nm;
     const size_t sA = (size_t)s->qcap * s->qcap;
-    double2* Vn = s->fV + (size_t)q0 * nm;
-    double2* Wn = s->fW + (size_t)q0 * nm;
+    V* fV = reinterpret_cast<V*>(s->fV);
+    V* Vn = fV + (size_t)q0 * nm;
+    V* Wn = reinterpret_cast<V*>(s->fW) + (size_t)q0 * nm;
     if (q0 > 0) {
-      dense_gemm_cn(K, nm, q0, p, s->fV, sV, nm, Wn, sV, nm, s->fA + (size_t)q0 * s->qcap, sA, s->qcap, ONE, ZERO,
-                    s->cn_work, s->d_kactive, s->st);
+      O::cn(K, nm, q0, p, fV, sV, nm, Wn, sV, nm, s->fA + (size_t)q0 * s->qcap, sA, s->qcap, ONE, ZERO, s->cn_work,
+            s->d_kactive, s->st);
       fom_mirror(K, q0, p, s->fA, s->qcap, sA, s->d_kactive, s->st);
     }
-    dense_gemm_cn(K, nm, p, p, Vn, sV, nm, Wn, sV, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, s->d_kactive,
-                  s->st);
+    O::cn(K, nm, p, p, Vn, sV, nm, Wn, sV, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, s->d_kactive, s->st);
     small_put_herm_block(K, p, s->sm1, s->fA, s->qcap, sA, q0, s->st);
     fom_pad_diag(K, q0, p, s->fA, s->qcap, sA, s->d_nzero, 1e30, s->st);
-    dense_gemm_cn(K, nm, p, p, Vn, sV, nm, s->Cb, sb, nm, s->fC + q0, (size_t)s->qcap * p, s->qcap, ONE, ZERO,
-                  s->cn_work, s->d_kactive, s->st);
+    O::cn(K, nm, p, p, Vn, sV, nm, C, sb, nm, s->fC + q0, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work,
+          s->d_kactive, s->st);
     CKL(s);
     return EACG_OK;
   };
@@ -834,22 +977,27 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
     const size_t sC = (size_t)s->qcap * p;
     const size_t sA = (size_t)s->qcap * s->qcap;
     const size_t sV = (size_t)s->qcap * nm;
+    V* fV = reinterpret_cast<V*>(s->fV);
+    V* fW = reinterpret_cast<V*>(s->fW);
     TRY(upload_active());
     // Y = solve(A Y - Y Sigma = C_j) via C~ = C Q, (A - s_m) y~_m = c~_m, Y = Y~ Q^H
     dense_gemm_nn(K, q, p, p, s->fC, sC, s->qcap, s->sigv, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
                   s->d_kactive, s->st);
-    PROF_RUN(P_FOMSOLVE, (double)K * p * q * (q + 1) * 16.0 * 2, 0,
+    PROF_RUN(P_FOMSOLVE + (f32 ? P_F32 : 0), (double)K * p * q * (q + 1) * (f32 ? 8.0 : 16.0) * 2,
+             (double)K * p * (8.0 / 3.0) * q * q * q, 0,
              fom_shifted_solve(K, p, q, s->fA, s->qcap, sA, s->eval, s->fYt, s->qcap, sC, s->fY, s->fwork,
-                               s->d_kactive, nullptr, prec, s->st));
-    dense_gemm_nn(K, q, p, p, s->fY, sC, s->qcap, s->sigvh, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
-                  s->d_kactive, s->st);
-    // fYt now holds Y.  Res = C - (W Y - V Y Sigma)
-    dense_gemm_nn(K, nm, q, p, s->fW, sV, nm, s->fYt, sC, s->qcap, s->tmp1, sb, nm, ONE, ZERO, s->d_kactive, s->st);
-    dense_gemm_nn(K, q, p, p, s->fYt, sC, s->qcap, s->sig, (size_t)p * p, p, s->fY, sC, s->qcap, ONE, ZERO,
-                  s->d_kactive, s->st);
-    dense_gemm_nn(K, nm, q, p, s->fV, sV, nm, s->fY, sC, s->qcap, s->tmp1, sb, nm, MONE, ONE, s->d_kactive, s->st);
-    dense_axpby(s->blk, ONE, s->Cb, MONE, s->tmp1, s->tmp1, s->st);
-    dense_norms2(K, sb, s->tmp1, s->d_out + 64, s->st);
+                               s->d_kactive, nullptr, f32 ? 1 : 0, s->st));
+    PROF_RUN(P_FOM_RES, 2.0 * K * q * nm * sizeof(V) + 2.0 * s->blk * sizeof(V), 16.0 * K * nm * q * p, 0, {
+      dense_gemm_nn(K, q, p, p, s->fY, sC, s->qcap, s->sigvh, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
+                    s->d_kactive, s->st);
+      // fYt now holds Y.  Res = C - (W Y - V Y Sigma)
+      O::nn(K, nm, q, p, fW, sV, nm, s->fYt, sC, s->qcap, t1, sb, nm, ONE, ZERO, s->d_kactive, s->st);
+      dense_gemm_nn(K, q, p, p, s->fYt, sC, s->qcap, s->sig, (size_t)p * p, p, s->fY, sC, s->qcap, ONE, ZERO,
+                    s->d_kactive, s->st);
+      O::nn(K, nm, q, p, fV, sV, nm, s->fY, sC, s->qcap, t1, sb, nm, MONE, ONE, s->d_kactive, s->st);
+      O::axpby(s->blk, ONE, C, MONE, t1, t1, s->st);
+      O::norms2(K, sb, t1, s->d_out + 64, s->st);
+    });
     CKL(s);
     TRY(sync_read(s, 64 + K));
     bool any = false;
@@ -858,7 +1006,8 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
       if (!active[k]) continue;
       iters[k] = j;
       const double rel = std::sqrt(s->h_out[64 + k]) / cnorm[k];
-      if (!(rel <= s->prm.fom_rtol) && j < s->prm.max_fom) {
+      // the projected solves keep their pivot bookkeeping for at most 1024 Krylov columns
+      if (!(rel <= s->prm.fom_rtol) && j < s->prm.max_fom && q + p <= 1024) {
         any = true;
       } else {
         s->h_int[2 * K + k] = 1;  // take Y now
@@ -875,11 +1024,13 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
     if (!any) break;
     // next block: R_j = P^{-1} Res, orthonormalised against V_j
     TRY(fom_reserve(s, q + p));
+    fV = reinterpret_cast<V*>(s->fV);
     TRY(upload_active());
-    dense_tpa(K, p, nm, s->d_kin, s->alpha, s->tmp1, s->tmp2, false, s->st);
-    dense_zero(s->fvt, s->blk, s->st);
-    dense_zero(s->fwt, s->blk, s->st);
-    TRY(orthonormalise(s, s->tmp2, s->fV, q, (size_t)s->qcap * nm, s->fvt, s->d_kactive));
+    O::tpa(K, p, nm, s->d_kin, s->alpha, t1, t2, s->st);
+    cudaMemsetAsync(vt, 0, sizeof(V) * s->blk, s->st);
+    cudaMemsetAsync(wt, 0, sizeof(V) * s->blk, s->st);
+    PROF_RUN(P_FOM_ORTH, 4.0 * K * q * nm * sizeof(V), 32.0 * K * nm * q * p, 0,
+             TRY(orthonormalise<T>(s, t2, fV, q, (size_t)s->qcap * nm, vt, t3, s->d_kactive)));
     CK(cudaMemcpyAsync(s->h_int + K, s->d_nzero, sizeof(int) * K, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     bool any2 = false;
@@ -897,27 +1048,36 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
     small_take_y(K, q, s->qcap, p, s->fYt, s->fYf, s->d_take, s->st);
     if (!any2) break;
     TRY(upload_active());
-    TRY(apply_H_block(s, s->fvt, s->fwt, prec, s->d_kactive));
-    TRY(put_cols(s, s->fvt, s->fwt, q));
+    TRY(apply_H_t(s, vt, wt, s->d_kactive));
+    TRY(put_cols(s, vt, wt, q));
     // the H application above advanced h_apps by all K; keep the per-k count honest
     {
       int na = 0;
       for (int k = 0; k < K; ++k) na += active[k];
       s->h_apps -= (long long)(K - na) * p;
     }
-    TRY(add_block(q));
+    PROF_RUN(P_FOM_BLOCK, 1.0 * K * q * nm * sizeof(V), 8.0 * K * nm * q * p, 0, TRY(add_block(q)));
     q += p;
   }
   // X = Phi / mu + V Y_final;  G = Phi - X (Phi^* X)^{-1}
   const size_t sC = (size_t)s->qcap * p;
-  dense_axpby(s->blk, cr(1.0 / mu), phi, ZERO, nullptr, s->Xb, s->st);
-  dense_gemm_nn(K, nm, q, p, s->fV, (size_t)s->qcap * nm, nm, s->fYf, sC, s->qcap, s->Xb, sb, nm, ONE, ONE, nullptr,
-                s->st);
-  dense_gemm_cn(K, nm, p, p, phi, sb, nm, s->Xb, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
-                s->st);
-  dense_inverse(K, p, s->sm1, s->sm2, nullptr, s->st);
-  dense_copy(g, phi, s->blk, s->st);
-  dense_gemm_nn(K, nm, p, p, s->Xb, sb, nm, s->sm2, (size_t)p * p, p, g, sb, nm, MONE, ONE, nullptr, s->st);
+  PROF_RUN(P_FOM_FINAL, 1.0 * K * q * nm * sizeof(V) + 6.0 * s->blk * 16, 8.0 * K * nm * q * p, 0, {
+    dense_axpby(s->blk, cr(1.0 / mu), phi, ZERO, nullptr, s->Xb, s->st);
+    if (!f32) {
+      dense_gemm_nn(K, nm, q, p, s->fV, (size_t)s->qcap * nm, nm, s->fYf, sC, s->qcap, s->Xb, sb, nm, ONE, ONE,
+                    nullptr, s->st);
+    } else {
+      O::nn(K, nm, q, p, reinterpret_cast<V*>(s->fV), (size_t)s->qcap * nm, nm, s->fYf, sC, s->qcap, t1, sb, nm, ONE,
+            ZERO, nullptr, s->st);
+      dense_to64(s->blk, reinterpret_cast<float2*>(s->tmp1), s->tmp3, s->st);
+      dense_axpby(s->blk, ONE, s->Xb, ONE, s->tmp3, s->Xb, s->st);
+    }
+    dense_gemm_cn(K, nm, p, p, phi, sb, nm, s->Xb, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
+                  s->st);
+    dense_inverse(K, p, s->sm1, s->sm2, nullptr, s->st);
+    dense_copy(g, phi, s->blk, s->st);
+    dense_gemm_nn(K, nm, p, p, s->Xb, sb, nm, s->sm2, (size_t)p * p, p, g, sb, nm, MONE, ONE, nullptr, s->st);
+  });
   CKL(s);
   int mx = 0;
   for (int k = 0; k < K; ++k) mx = std::max(mx, iters[k]);
@@ -925,6 +1085,13 @@ static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2
   if (fom_iters)
     for (int k = 0; k < K; ++k) fom_iters[k] = iters[k];
   return EACG_OK;
+}
+
+// prec 0: FP64 FOM; 1: FP32 Krylov blocks, transforms and projected solves.
+static eacg_status ea_gradient(eacg_system* s, const double2* phi, const double2* hphi, const double2* lam,
+                               double2* g, int prec, int* fom_iters) {
+  if (prec) return ea_gradient_t<float>(s, phi, hphi, lam, g, fom_iters);
+  return ea_gradient_t<double>(s, phi, hphi, lam, g, fom_iters);
 }
 
 // ============================================================================ line search
@@ -939,13 +1106,16 @@ static eacg_status trial(eacg_system* s, double t, int prec, TrialOut* out) {
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
   dense_axpby(s->blk, ONE, s->phi, cr(t), s->eta, s->psi_t, s->st);
-  TRY(polar(s, s->psi_t, s->phi_t, s->eval_t, s->evec_t, s->sinv_t));
-  // T(eta) = eta S^{-1} - t Phi+ [[eta S^{-1}, eta S^{-1}]]
-  dense_gemm_nn(K, nm, p, p, s->eta, sb, nm, s->sinv_t, (size_t)p * p, p, s->teta_t, sb, nm, ONE, ZERO, nullptr, s->st);
-  dense_gemm_cn(K, nm, p, p, s->teta_t, sb, nm, s->teta_t, sb, nm, s->sm2, (size_t)p * p, p, ONE, ZERO, s->cn_work,
-                nullptr, s->st);
-  dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm2, (size_t)p * p, p, s->teta_t, sb, nm, cr(-t), ONE, nullptr,
-                s->st);
+  PROF_RUN(P_TRIAL_RET, 8.0 * s->blk * 16, 40.0 * s->blk * p, 0, {
+    TRY(polar(s, s->psi_t, s->phi_t, s->eval_t, s->evec_t, s->sinv_t));
+    // T(eta) = eta S^{-1} - t Phi+ [[eta S^{-1}, eta S^{-1}]]
+    dense_gemm_nn(K, nm, p, p, s->eta, sb, nm, s->sinv_t, (size_t)p * p, p, s->teta_t, sb, nm, ONE, ZERO, nullptr,
+                  s->st);
+    dense_gemm_cn(K, nm, p, p, s->teta_t, sb, nm, s->teta_t, sb, nm, s->sm2, (size_t)p * p, p, ONE, ZERO,
+                  s->cn_work, nullptr, s->st);
+    dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm2, (size_t)p * p, p, s->teta_t, sb, nm, cr(-t), ONE, nullptr,
+                  s->st);
+  });
   CKL(s);
   TRY(evaluate(s, s->phi_t, s->hphi_t, s->res_t, s->lam_t, prec, &out->ev));
   pairing_dev(s, s->res_t, s->teta_t, 0, true);
@@ -1532,6 +1702,7 @@ extern "C" int eacg_profile_read(eacg_system* s, eacg_kernel_stat* out, int max)
     acc[r.slot].launches += 1;
     acc[r.slot].ms += ms;
     acc[r.slot].bytes += r.bytes;
+    acc[r.slot].flops += r.flops;
     acc[r.slot].units += r.units;
   }
   s->prof.clear();

@@ -122,8 +122,8 @@ __global__ void k_fill_int(int* p, size_t n, int v) {
 // ----------------------------------------------------------------------------- x passes
 // Inverse x pass: per CTA, cols_per_cta columns of one band.  Shared: twiddles, lines
 // with pitch N + 1.  Output tbuf[band][jx][col].
-template <typename T, int E>
-__global__ void k_xpass_inv(const double2* __restrict__ psi, int n_max, int p, const int* __restrict__ xmap,
+template <typename T, int E, typename TIO>
+__global__ void k_xpass_inv(const TIO* __restrict__ psi, int n_max, int p, const int* __restrict__ xmap,
                             int ncols, cplx<T>* __restrict__ tbuf, FftPlan pl, const cplx<T>* __restrict__ tw_g,
                             int cols_per_cta, const int* __restrict__ kactive) {
   using V = cplx<T>;
@@ -138,13 +138,13 @@ __global__ void k_xpass_inv(const double2* __restrict__ psi, int n_max, int p, c
   const int nc = min(cols_per_cta, ncols - c0);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
   const int* xm = xmap + ((size_t)k * ncols + c0) * N;
-  const double2* src = psi + (size_t)band * n_max;
+  const TIO* src = psi + (size_t)band * n_max;
   for (int e = threadIdx.x; e < nc * N; e += blockDim.x) {
     const int c = e / N, fx = e - c * N;
     const int id = xm[e];
     V v;
     if (id >= 0) {
-      v = to_c<T>(src[id]);
+      v = cvt<V>(src[id]);
     } else {
       v.x = 0;
       v.y = 0;
@@ -161,11 +161,11 @@ __global__ void k_xpass_inv(const double2* __restrict__ psi, int n_max, int p, c
 }
 
 // Forward x pass and gather: out = scale * FFT + kin * psi_in (kin may be null).
-template <typename T, int E>
+template <typename T, int E, typename TIO>
 __global__ void k_xpass_fwd(const cplx<T>* __restrict__ tbuf, const int* __restrict__ xmap, int ncols, FftPlan pl,
                             const cplx<T>* __restrict__ tw_g, int cols_per_cta, int n_max, int p,
-                            const int* __restrict__ nk, const double2* __restrict__ psi_in,
-                            const double* __restrict__ kin, double scale, double2* __restrict__ out,
+                            const int* __restrict__ nk, const TIO* __restrict__ psi_in,
+                            const double* __restrict__ kin, double scale, TIO* __restrict__ out,
                             const int* __restrict__ kactive) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -186,8 +186,8 @@ __global__ void k_xpass_fwd(const cplx<T>* __restrict__ tbuf, const int* __restr
   __syncthreads();
   fft_lines<V, E, false>(lines, nc, LP, 1, pl, tw);
   const int* xm = xmap + ((size_t)k * ncols + c0) * N;
-  double2* o = out + (size_t)band * n_max;
-  const double2* pin = psi_in + (size_t)band * n_max;
+  TIO* o = out + (size_t)band * n_max;
+  const TIO* pin = psi_in + (size_t)band * n_max;
   const double* kk = kin ? kin + (size_t)k * n_max : nullptr;
   for (int e = threadIdx.x; e < nc * N; e += blockDim.x) {
     const int c = e / N, fx = e - c * N;
@@ -195,15 +195,15 @@ __global__ void k_xpass_fwd(const cplx<T>* __restrict__ tbuf, const int* __restr
     if (id >= 0) {
       double2 v = cscale(to_d(lines[c * LP + fx]), scale);
       if (kk) {
-        const double2 s = pin[id];
+        const double2 s = to_d(pin[id]);
         v.x += kk[id] * s.x;
         v.y += kk[id] * s.y;
       }
-      o[id] = v;
+      o[id] = cvt<TIO>(v);
     }
   }
   if (blockIdx.x == 0) {
-    for (int i = nk[k] + threadIdx.x; i < n_max; i += blockDim.x) o[i] = make_double2(0.0, 0.0);
+    for (int i = nk[k] + threadIdx.x; i < n_max; i += blockDim.x) o[i] = cvt<TIO>(make_double2(0.0, 0.0));
   }
 }
 
@@ -484,29 +484,30 @@ __global__ void k_projectors(int K, int n_max, const int* __restrict__ nk, const
 }
 
 // ----------------------------------------------------------------------------- launchers
-template <typename T, int E>
-static void launch_xinv(const GridCtx& g, const double2* psi, void* tbuf, const void* tw, int nbands,
+template <typename T, int E, typename TIO>
+static void launch_xinv(const GridCtx& g, const TIO* psi, void* tbuf, const void* tw, int nbands,
                         const int* kactive, cudaStream_t st) {
   const int cpc = g.cols_per_cta;
   dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
   const int threads = min(1024, max(32, cpc * g.plan.TPL));
   const size_t sm = sizeof(cplx<T>) * (g.plan.N + (size_t)cpc * (g.plan.N + 1));
-  cudaFuncSetAttribute(k_xpass_inv<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_xpass_inv<T, E><<<grid, threads, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf, g.plan,
-                                               (const cplx<T>*)tw, cpc, kactive);
+  ensure_smem((const void*)k_xpass_inv<T, E, TIO>, sm);
+  k_xpass_inv<T, E, TIO><<<grid, threads, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf, g.plan,
+                                                    (const cplx<T>*)tw, cpc, kactive);
   count_launch();
 }
 
-template <typename T, int E>
-static void launch_xfwd(const GridCtx& g, const void* tbuf, const void* tw, const double2* psi_in, const double* kin,
-                        double scale, double2* out, int nbands, const int* kactive, cudaStream_t st) {
+template <typename T, int E, typename TIO>
+static void launch_xfwd(const GridCtx& g, const void* tbuf, const void* tw, const TIO* psi_in, const double* kin,
+                        double scale, TIO* out, int nbands, const int* kactive, cudaStream_t st) {
   const int cpc = g.cols_per_cta;
   dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
   const int threads = min(1024, max(32, cpc * g.plan.TPL));
   const size_t sm = sizeof(cplx<T>) * (g.plan.N + (size_t)cpc * (g.plan.N + 1));
-  cudaFuncSetAttribute(k_xpass_fwd<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_xpass_fwd<T, E><<<grid, threads, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, g.plan, (const cplx<T>*)tw,
-                                               cpc, g.n_max, g.p, g.nk, psi_in, kin, scale, out, kactive);
+  ensure_smem((const void*)k_xpass_fwd<T, E, TIO>, sm);
+  k_xpass_fwd<T, E, TIO><<<grid, threads, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, g.plan,
+                                                    (const cplx<T>*)tw, cpc, g.n_max, g.p, g.nk, psi_in, kin, scale,
+                                                    out, kactive);
   count_launch();
 }
 
@@ -526,7 +527,7 @@ template <typename T, int E>
 static void launch_plane_h(const GridCtx& g, void* tbuf, const void* tw, const void* v, int nbands,
                            const int* kactive, cudaStream_t st) {
   const size_t sm = plane_smem<T>(g.plan.N, g.ny);
-  cudaFuncSetAttribute(k_plane_h<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ensure_smem((const void*)k_plane_h<T, E>, sm);
   dim3 grid(g.plan.N, nbands);
   k_plane_h<T, E><<<grid, plane_threads(g.plan), sm, st>>>((cplx<T>*)tbuf, g.ncols, g.colfy, g.colfz, g.ylist, g.ny,
                                                            (const T*)v, g.plan, (const cplx<T>*)tw, g.p, kactive);
@@ -537,7 +538,7 @@ template <typename T, int E>
 static void launch_plane_rho(const GridCtx& g, const void* tbuf, const void* tw, int nbands, int groups,
                              const double* bw, double* partial, cudaStream_t st) {
   const size_t sm = plane_smem<T>(g.plan.N, g.ny);
-  cudaFuncSetAttribute(k_plane_rho<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ensure_smem((const void*)k_plane_rho<T, E>, sm);
   int threads = plane_threads(g.plan);
   const int need = (g.plan.N * g.plan.N + RHO_NPT - 1) / RHO_NPT;
   while (threads < need) threads += g.plan.TPL;
@@ -560,21 +561,32 @@ static void launch_plane_rho(const GridCtx& g, const void* tbuf, const void* tw,
 void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, int nbands, const int* kactive,
                     cudaStream_t st) {
   if (prec == 0) {
-    EACG_DISPATCH_E(g.plan.E, (launch_xinv<double, EE>(g, psi, tbuf, g.tw64, nbands, kactive, st)));
+    EACG_DISPATCH_E(g.plan.E, (launch_xinv<double, EE, double2>(g, psi, tbuf, g.tw64, nbands, kactive, st)));
   } else {
-    EACG_DISPATCH_E(g.plan.E, (launch_xinv<float, EE>(g, psi, tbuf, g.tw32, nbands, kactive, st)));
+    EACG_DISPATCH_E(g.plan.E, (launch_xinv<float, EE, double2>(g, psi, tbuf, g.tw32, nbands, kactive, st)));
   }
 }
 
 void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
                     double scale, double2* out, int nbands, const int* kactive, cudaStream_t st) {
   if (prec == 0) {
-    EACG_DISPATCH_E(g.plan.E,
-                    (launch_xfwd<double, EE>(g, tbuf, g.tw64, psi_in, kin, scale, out, nbands, kactive, st)));
+    EACG_DISPATCH_E(g.plan.E, (launch_xfwd<double, EE, double2>(g, tbuf, g.tw64, psi_in, kin, scale, out, nbands,
+                                                                kactive, st)));
   } else {
-    EACG_DISPATCH_E(g.plan.E,
-                    (launch_xfwd<float, EE>(g, tbuf, g.tw32, psi_in, kin, scale, out, nbands, kactive, st)));
+    EACG_DISPATCH_E(g.plan.E, (launch_xfwd<float, EE, double2>(g, tbuf, g.tw32, psi_in, kin, scale, out, nbands,
+                                                               kactive, st)));
   }
+}
+
+void grid_xpass_inv32(const GridCtx& g, const float2* psi, void* tbuf, int nbands, const int* kactive,
+                      cudaStream_t st) {
+  EACG_DISPATCH_E(g.plan.E, (launch_xinv<float, EE, float2>(g, psi, tbuf, g.tw32, nbands, kactive, st)));
+}
+
+void grid_xpass_fwd32(const GridCtx& g, const void* tbuf, const float2* psi_in, const double* kin, double scale,
+                      float2* out, int nbands, const int* kactive, cudaStream_t st) {
+  EACG_DISPATCH_E(g.plan.E,
+                  (launch_xfwd<float, EE, float2>(g, tbuf, g.tw32, psi_in, kin, scale, out, nbands, kactive, st)));
 }
 
 void grid_plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
@@ -607,7 +619,7 @@ static void launch_fft3(const GridCtx& g, double2* a, int axis, cudaStream_t st)
   const size_t sm = sizeof(double2) * ((size_t)N + (size_t)lpc * (N + 1));
   const int threads = min(1024, lpc * g.plan.TPL);
   const int blocks = (N * N + lpc - 1) / lpc;
-  cudaFuncSetAttribute(k_fft3_axis<E, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ensure_smem((const void*)k_fft3_axis<E, INV>, sm);
   k_fft3_axis<E, INV><<<blocks, threads, sm, st>>>(a, axis, g.plan, (const double2*)g.tw64, lpc);
   count_launch();
 }

@@ -10,6 +10,11 @@ namespace eacg {
 
 // Counts one kernel launch of this library (defined in eacg.cu).
 void count_launch();
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
+// The limit is a process-wide property of the kernel, so it only ever grows: systems of
+// different sizes running concurrently in several host threads never lower it under each
+// other's launches (defined in eacg.cu).
+void ensure_smem(const void* func, size_t bytes);
 
 // Device-side description of the plane-wave grid of one system.
 struct GridCtx {
@@ -36,6 +41,11 @@ void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, 
                     cudaStream_t st);
 void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
                     double scale, double2* out, int nbands, const int* kactive, cudaStream_t st);
+// FP32 blocks in and out (FP32 transforms): used by the FOM of the mixed-precision mode.
+void grid_xpass_inv32(const GridCtx& g, const float2* psi, void* tbuf, int nbands, const int* kactive,
+                      cudaStream_t st);
+void grid_xpass_fwd32(const GridCtx& g, const void* tbuf, const float2* psi_in, const double* kin, double scale,
+                      float2* out, int nbands, const int* kactive, cudaStream_t st);
 void grid_plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
                   cudaStream_t st);
 void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
@@ -64,6 +74,20 @@ void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int 
 void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                    cudaStream_t st);
+// FP32-block variants: A, B (cn) / A, C (nn) complex64, FP32 accumulation; small factors and
+// the cn result stay FP64.
+void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const float2* B, size_t sB,
+                     int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
+                     const int* kactive, cudaStream_t st);
+void dense_gemm_nn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B, size_t sB,
+                     int ldb, float2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
+                     cudaStream_t st);
+void dense_to32(size_t n, const double2* x, double sc, float2* y, cudaStream_t st);
+void dense_to64(size_t n, const float2* x, double2* y, cudaStream_t st);
+void dense_axpby32(size_t n, double2 a, const float2* x, double2 b, const float2* y, float2* out, cudaStream_t st);
+void dense_norms2_32(int K, size_t len, const float2* V, double* out, cudaStream_t st);
+void dense_tpa32(int K, int p, int n_max, const double* kin, const double* alpha, const float2* in, float2* out,
+                 cudaStream_t st);
 // Hermitian eigen-decomposition of K matrices p x p (ld p): ascending eigenvalues and
 // unit eigenvectors (columns).  p <= 64.
 void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive, cudaStream_t st);

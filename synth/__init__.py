@@ -86,17 +86,16 @@ def config_diamond_supercell(reps: int, seed: int = 3, kgrid=(1, 1, 1), ecut: fl
                    [0.8] * nat, 4, 0.7, D, ecut, N, 2 * nat, kgrid, seed)
 
 
+GRID_SIZES = (16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96)
+
+
 def smooth_grid_size(nmin: int) -> int:
-    """Smallest n >= nmin of the form 2^a 3^b 5^c (FFT-friendly)."""
-    n = max(nmin, 2)
-    while True:
-        m = n
-        for f in (2, 3, 5):
-            while m % f == 0:
-                m //= f
-        if m == 1:
+    """Smallest FFT grid edge n >= nmin from GRID_SIZES (edges built from radices 2, 3, 4 or
+    2, 4, 5 that the transforms support)."""
+    for n in GRID_SIZES:
+        if n >= nmin:
             return n
-        n += 1
+    raise ValueError(f"no supported grid size >= {nmin}")
 
 
 def config_serving_request(i: int):
