@@ -22,6 +22,36 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // 
 }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// FP64 reciprocal square root and reciprocal by Newton-Raphson from an FP32 seed: two steps
+// take the seed's ~1e-7 relative error to FP64 rounding (quadratic convergence), using only
+// multiply-adds, which GB300 executes far faster than its FP64 divide and square-root
+// sequences.  The argument (positive, normal) is first scaled by an exact power of two into
+// [1, 4) so that the FP32 seed never under- or overflows.
+//   y <- y (3 - x y^2) / 2          for 1 / sqrt(x)
+//   y <- y (2 - x y)                for 1 / x
+__device__ __forceinline__ double pow2(int e) {  // 2^e for -1022 <= e <= 1023
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+__device__ __forceinline__ int exponent_of(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int half = exponent_of(x) >> 1;  // floor(e / 2)
+  const double xs = x * pow2(-2 * half);  // in [1, 4)
+  double y = (double)rsqrtf((float)xs);
+  y = y * fma(-0.5 * xs * y, y, 1.5);
+  y = y * fma(-0.5 * xs * y, y, 1.5);
+  return y * pow2(-half);
+}
+__device__ __forceinline__ double rcp_nr(double x) {
+  const int e = exponent_of(x);
+  const double xs = x * pow2(-e);  // in [1, 2)
+  double y = (double)(1.0f / (float)xs);
+  y = y * fma(-xs, y, 2.0);
+  y = y * fma(-xs, y, 2.0);
+  return y * pow2(-e);
+}
+
 // ----------------------------------------------------------------------------- A^H B
 // Templated on the block precision T (double or float): A and B are cplx<T>, the products
 // are accumulated in T within a chunk of rows, the chunk partials and the result are FP64.
@@ -264,62 +294,85 @@ void dense_tpa32(int K, int p, int n_max, const double* kin, const double* alpha
 }
 
 // ----------------------------------------------------------------------------- Hermitian eig
-// Parallel cyclic Jacobi (round-robin pairs) on one p x p Hermitian matrix per CTA.
+// Parallel cyclic Jacobi (round-robin pairs) on one p x p Hermitian matrix per CTA, FP64.
+// The rotation parameters use multiply-add refinements of FP32 reciprocal / rsqrt seeds in
+// FP64 (no FP64 divide or square root).  Converged when the off-diagonal norm is below
+// 1e-14 of the matrix norm.
+template <typename T>
+struct JacobiMath;
+template <>
+struct JacobiMath<double> {
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt_nr(x); }
+  static __device__ __forceinline__ double rcp(double x) { return rcp_nr(x); }
+  static constexpr double tol2 = 1e-28, neg = 1e-16, tiny = 1e-280;
+};
+template <typename T>
 __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double* __restrict__ w,
                        double2* __restrict__ Vg, const int* __restrict__ kactive) {
+  using V2 = cplx<T>;
+  using M = JacobiMath<T>;
   const int k = blockIdx.x;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int pe = p + (p & 1);  // even number of slots (a dummy index when p is odd)
-  double2* A = reinterpret_cast<double2*>(smem_raw);
-  double2* V = A + p * p;
-  double* rot = reinterpret_cast<double*>(V + p * p);  // [pe/2][4]: c, s, cos phi, sin phi
-  double* red = rot + 2 * pe;                          // [2]
+  V2* A = reinterpret_cast<V2*>(smem_raw);
+  V2* V = A + p * p;
+  T* rot = reinterpret_cast<T*>(V + p * p);  // [pe/2][4]: c, s, cos phi, sin phi
+  T* red = rot + 2 * pe;                     // [2 + 2 * warps]
   const double2* Ak = Ag + k * sA;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    A[e] = Ak[e];
     const int j = e / p, i = e - j * p;
-    V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  // symmetrise exactly
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int j = e / p, i = e - j * p;
-    if (i < j) {
-      const double2 a = A[j * p + i], b = A[i * p + j];
-      const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-      A[j * p + i] = h;
-      A[i * p + j] = cconj(h);
-    } else if (i == j) {
-      A[e].y = 0.0;
-    }
+    // symmetrise exactly while loading: upper from (A_ij + conj A_ji) / 2
+    const double2 a = Ak[(size_t)j * p + i], b = Ak[(size_t)i * p + j];
+    double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    if (i == j) h.y = 0.0;
+    A[e] = to_c<T>(h);
+    V[e].x = (T)(i == j ? 1 : 0);
+    V[e].y = (T)0;
   }
   __syncthreads();
   const int npair = pe / 2;
   // round-robin pairing (circle method): slot 0 fixed, slots 1..pe-1 rotate by one per round
   auto slot = [pe](int pos, int round) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (pe - 1); };
   for (int sweep = 0; sweep < 20; ++sweep) {
-    if (threadIdx.x == 0) {
-      double off = 0.0, dia = 0.0;
-      for (int j = 0; j < p; ++j)
-        for (int i = 0; i < p; ++i) {
-          const double a2 = cabs2(A[j * p + i]);
-          if (i == j)
-            dia += a2;
-          else
-            off += a2;
+    {
+      // off-diagonal and diagonal squared norms: fixed per-thread strides, then a fixed
+      // shuffle tree per warp and a fixed warp order (deterministic)
+      T off = 0, dia = 0;
+      for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int j = e / p, i = e - j * p;
+        const T a2 = A[e].x * A[e].x + A[e].y * A[e].y;
+        if (i == j)
+          dia += a2;
+        else
+          off += a2;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_down_sync(0xffffffffu, off, o);
+        dia += __shfl_down_sync(0xffffffffu, dia, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        red[2 + 2 * (threadIdx.x >> 5)] = off;
+        red[3 + 2 * (threadIdx.x >> 5)] = dia;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        T so = 0, sd = 0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+          so += red[2 + 2 * wi];
+          sd += red[3 + 2 * wi];
         }
-      red[0] = off;
-      red[1] = dia;
+        red[0] = so;
+        red[1] = sd;
+      }
     }
     __syncthreads();
-    // converged when the off-diagonal norm is below 1e-14 of the matrix norm (above the
-    // rounding floor sqrt(p) eps ||A|| of the rotations, at the accuracy of LAPACK's eigh)
-    const double fro2 = red[0] + red[1];
-    const bool done = !(red[0] > 1e-28 * fro2);
+    const T fro2 = red[0] + red[1];
+    const bool done = !(red[0] > M::tol2 * fro2);
     __syncthreads();
     if (done) break;
-    const double negligible = 1e-16 * sqrt(fro2) / p;
+    const T negligible = M::neg * sqrt(fro2) / p;
     for (int round = 0; round < pe - 1; ++round) {
       // rotation parameters for each pair
       for (int t = threadIdx.x; t < npair; t += blockDim.x) {
@@ -329,18 +382,21 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
           i = j;
           j = q;
         }
-        double c = 1.0, s = 0.0, cf = 1.0, sf = 0.0;
+        T c = 1, s = 0, cf = 1, sf = 0;
         if (j < p) {
-          const double2 b = A[j * p + i];
-          const double r = sqrt(cabs2(b));
-          if (r > 1e-300 && r > negligible) {
-            const double a = A[i * p + i].x, d = A[j * p + j].x;
-            const double zeta = (d - a) / (2.0 * r);
-            const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+          const V2 b = A[j * p + i];
+          const T r2 = b.x * b.x + b.y * b.y;
+          if (r2 > M::tiny && r2 > negligible * negligible) {
+            const T a = A[i * p + i].x, d = A[j * p + j].x;
+            const T ir = M::rsq(r2);                       // 1 / |b|
+            const T zeta = (T)0.5 * (d - a) * ir;
+            const T h = (T)1 + zeta * zeta;
+            const T den = fabs(zeta) + h * M::rsq(h);      // |zeta| + sqrt(1 + zeta^2)
+            const T tt = (zeta >= 0 ? (T)1 : (T)-1) * M::rcp(den);
+            c = M::rsq((T)1 + tt * tt);
             s = tt * c;
-            cf = b.x / r;   // e^{i phi} = b / r
-            sf = b.y / r;
+            cf = b.x * ir;  // e^{i phi} = b / |b|
+            sf = b.y * ir;
           }
         }
         rot[4 * t + 0] = c;
@@ -359,17 +415,19 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
           j = q;
         }
         if (j >= p) continue;
-        const double c = rot[4 * t], s = rot[4 * t + 1];
-        const double2 em = make_double2(rot[4 * t + 2], -rot[4 * t + 3]);  // e^{-i phi}
+        const T c = rot[4 * t], s = rot[4 * t + 1];
+        V2 em;
+        em.x = rot[4 * t + 2];
+        em.y = -rot[4 * t + 3];  // e^{-i phi}
         {
-          const double2 ai = A[i * p + r], aj = cmul(em, A[j * p + r]);
-          A[i * p + r] = make_double2(c * ai.x - s * aj.x, c * ai.y - s * aj.y);
-          A[j * p + r] = make_double2(s * ai.x + c * aj.x, s * ai.y + c * aj.y);
+          const V2 ai = A[i * p + r], aj = cmul(em, A[j * p + r]);
+          A[i * p + r] = cscale(ai, c) - cscale(aj, s);
+          A[j * p + r] = cscale(ai, s) + cscale(aj, c);
         }
         {
-          const double2 vi = V[i * p + r], vj = cmul(em, V[j * p + r]);
-          V[i * p + r] = make_double2(c * vi.x - s * vj.x, c * vi.y - s * vj.y);
-          V[j * p + r] = make_double2(s * vi.x + c * vj.x, s * vi.y + c * vj.y);
+          const V2 vi = V[i * p + r], vj = cmul(em, V[j * p + r]);
+          V[i * p + r] = cscale(vi, c) - cscale(vj, s);
+          V[j * p + r] = cscale(vi, s) + cscale(vj, c);
         }
       }
       __syncthreads();
@@ -384,15 +442,17 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
           j = q;
         }
         if (j >= p) continue;
-        const double c = rot[4 * t], s = rot[4 * t + 1];
-        const double2 ep = make_double2(rot[4 * t + 2], rot[4 * t + 3]);
-        const double2 ai = A[col * p + i], aj = cmul(ep, A[col * p + j]);
-        double2 ni = make_double2(c * ai.x - s * aj.x, c * ai.y - s * aj.y);
-        double2 nj = make_double2(s * ai.x + c * aj.x, s * ai.y + c * aj.y);
-        if (s != 0.0 && col == j) ni = make_double2(0.0, 0.0);  // (i, j)
-        if (s != 0.0 && col == i) nj = make_double2(0.0, 0.0);  // (j, i)
-        if (col == i) ni.y = 0.0;
-        if (col == j) nj.y = 0.0;
+        const T c = rot[4 * t], s = rot[4 * t + 1];
+        V2 ep;
+        ep.x = rot[4 * t + 2];
+        ep.y = rot[4 * t + 3];
+        const V2 ai = A[col * p + i], aj = cmul(ep, A[col * p + j]);
+        V2 ni = cscale(ai, c) - cscale(aj, s);
+        V2 nj = cscale(ai, s) + cscale(aj, c);
+        if (s != (T)0 && col == j) ni.x = ni.y = (T)0;  // (i, j)
+        if (s != (T)0 && col == i) nj.x = nj.y = (T)0;  // (j, i)
+        if (col == i) ni.y = (T)0;
+        if (col == j) nj.y = (T)0;
         A[col * p + i] = ni;
         A[col * p + j] = nj;
       }
@@ -402,24 +462,69 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
   __syncthreads();
   // sort ascending by rank (ties by index) and write out
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    const double wi = A[i * p + i].x;
+    const T wi = A[i * p + i].x;
     int rank = 0;
     for (int j = 0; j < p; ++j) {
-      const double wj = A[j * p + j].x;
+      const T wj = A[j * p + j].x;
       if (wj < wi || (wj == wi && j < i)) ++rank;
     }
-    w[(size_t)k * p + rank] = wi;
-    for (int r = 0; r < p; ++r) Vg[(size_t)k * p * p + (size_t)rank * p + r] = V[i * p + r];
+    w[(size_t)k * p + rank] = (double)wi;
+    for (int r = 0; r < p; ++r) Vg[(size_t)k * p * p + (size_t)rank * p + r] = to_d(V[i * p + r]);
   }
+}
+
+template <typename T>
+static void heig_t(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
+                   cudaStream_t st) {
+  const int pe = p + (p & 1);
+  const size_t sm = sizeof(cplx<T>) * 2 * p * p + sizeof(T) * (2 * pe + 2 + 16) + 16;
+  ensure_smem((const void*)k_heig<T>, sm);
+  const int threads = p <= 16 ? 64 : 256;
+  k_heig<T><<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
+  count_launch();
 }
 
 void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
                 cudaStream_t st) {
-  const int pe = p + (p & 1);
-  const size_t sm = sizeof(double2) * 2 * p * p + sizeof(double) * (2 * pe + 2) + 16;
-  ensure_smem((const void*)k_heig, sm);
-  const int threads = p <= 16 ? 64 : 256;
-  k_heig<<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
+  heig_t<double>(K, p, A, sA, w, V, kactive, st);
+}
+// Largest eigenvalue of K Hermitian positive semidefinite p x p matrices by 24 power
+// iterations from the all-ones vector (Rayleigh quotient of the last iterate), FP64.
+__global__ void k_power_max(int p, const double2* __restrict__ G, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  __shared__ double2 x[64];
+  __shared__ double2 y[64];
+  __shared__ double nrm;
+  const double2* Gk = G + (size_t)k * p * p;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) x[i] = make_double2(1.0, 0.0);
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < 24; ++it) {
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+      double2 a = make_double2(0.0, 0.0);
+      for (int j = 0; j < p; ++j) a = cfma(Gk[(size_t)j * p + i], x[j], a);
+      y[i] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double yy = 0.0, xy = 0.0;
+      for (int i = 0; i < p; ++i) {
+        yy += cabs2(y[i]);
+        xy += x[i].x * y[i].x + x[i].y * y[i].y;
+      }
+      double xx = 0.0;
+      for (int i = 0; i < p; ++i) xx += cabs2(x[i]);
+      lam = xx > 0.0 ? xy / xx : 0.0;
+      nrm = yy > 0.0 ? 1.0 / sqrt(yy) : 0.0;
+      out[k] = lam;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x) x[i] = cscale(y[i], nrm);
+    __syncthreads();
+  }
+}
+void small_power_max(int K, int p, const double2* G, double* out, cudaStream_t st) {
+  k_power_max<<<K, 32, 0, st>>>(p, G, out);
   count_launch();
 }
 

@@ -847,10 +847,9 @@ static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, 
   using O = FomOps<T>;
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
-  // reference: largest Gram eigenvalue before projection
+  // reference: largest Gram eigenvalue before projection (power iteration)
   O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
-  dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
-  small_max_eval(K, p, s->sval, s->lref, s->st);
+  small_power_max(K, p, s->sm1, s->lref, s->st);
   if (q > 0) {
     for (int pass = 0; pass < 2; ++pass) {
       O::cn(K, nm, q, p, V, sV, nm, R, sb, nm, s->fYt, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work, kactive,
@@ -858,7 +857,7 @@ static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, 
       O::nn(K, nm, q, p, V, sV, nm, s->fYt, (size_t)s->qcap * p, s->qcap, R, sb, nm, MONE, ONE, kactive, s->st);
     }
   }
-  // first pass
+  // first (rank-revealing) pass
   O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
   dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
   small_orth_scale(K, p, s->sm2, s->sval, s->lref, O::drop_tol, s->sm3, s->d_nzero, s->st);
