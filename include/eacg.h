@@ -62,7 +62,7 @@ typedef struct {
   double proj_width;       /* bohr                                             */
   const double* D;         /* host, natoms x 2 (Ha)                            */
   double ecut;             /* basis: 1/2 |k+G|^2 <= ecut (Ha)                  */
-  int N;                   /* FFT grid edge, 2^a 3^b or 2^a 5^c, 8 <= N <= 96  */
+  int N;                   /* FFT grid edge: 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80 or 96 */
   int nbands;              /* p: occupied orbitals per k-point                 */
   int nk;                  /* K: number of k-points                            */
   const double* kfrac;     /* host, K x 3 fractional coordinates (units of 2 pi / a) */

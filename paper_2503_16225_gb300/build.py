@@ -1,4 +1,4 @@
-"""In-tree build of libeacg.so for sm_103a (nvcc, three translation units in parallel)."""
+"""In-tree build of libeacg.so for sm_103a (nvcc, the translation units compiled in parallel)."""
 from __future__ import annotations
 
 import os
@@ -11,7 +11,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeacg.so")
-SOURCES = ["grid_kernels.cu", "dense_kernels.cu", "eacg.cu", "noalloc.cu"]
+SOURCES = [
+    "grid_fft_xl.cu", "grid_fft_large.cu", "grid_fft_mid.cu", "grid_fft_48.cu", "grid_fft_small.cu",
+    "grid_kernels.cu", "dense_kernels.cu", "eacg.cu", "noalloc.cu",
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

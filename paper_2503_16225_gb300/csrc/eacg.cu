@@ -60,7 +60,7 @@ struct eacg_system {
   size_t blk = 0;  // elements of one [K][p][n_max] block
   // ---- device allocations (freed in destroy)
   std::vector<void*> allocs;
-  int *d_nk = nullptr, *d_m = nullptr, *d_xmap = nullptr, *d_colfy = nullptr, *d_colfz = nullptr, *d_ylist = nullptr;
+  int *d_nk = nullptr, *d_m = nullptr, *d_xmap = nullptr, *d_cmapy = nullptr, *d_rowmask = nullptr, *d_ylist = nullptr;
   double *d_kfrac = nullptr, *d_kin = nullptr, *d_kw = nullptr, *d_pos = nullptr, *d_Z = nullptr, *d_rc = nullptr;
   double *d_dvec = nullptr, *d_bw = nullptr;
   double2* d_tw64 = nullptr;
@@ -218,61 +218,6 @@ static void dfree(eacg_system* s, void* p) {
   cudaFree(p);
 }
 
-static bool make_plan(int N, FftPlan* pl) {
-  std::memset(pl, 0, sizeof(*pl));
-  pl->N = N;
-  int n = N, np = 0;
-  int rad[16];
-  while (n % 4 == 0) {
-    rad[np++] = 4;
-    n /= 4;
-  }
-  while (n % 2 == 0) {
-    rad[np++] = 2;
-    n /= 2;
-  }
-  while (n % 3 == 0) {
-    rad[np++] = 3;
-    n /= 3;
-  }
-  while (n % 5 == 0) {
-    rad[np++] = 5;
-    n /= 5;
-  }
-  if (n != 1 || np > 8 || np == 0) return false;
-  bool h3 = false, h5 = false, h4 = false;
-  for (int i = 0; i < np; ++i) {
-    h3 |= rad[i] == 3;
-    h5 |= rad[i] == 5;
-    h4 |= rad[i] == 4;
-  }
-  if (h3 && h5) return false;
-  int E;
-  if (h5)
-    E = 20;
-  else if (h3)
-    E = 12;
-  else
-    E = (N >= 32) ? 8 : 4;
-  if (!h4 && E == 20) E = 20;
-  if (N % E != 0) {
-    if (!h3 && !h5 && N % 4 == 0)
-      E = 4;
-    else
-      return false;
-  }
-  pl->E = E;
-  pl->TPL = N / E;
-  pl->npass = np;
-  int ns = 1;
-  for (int i = 0; i < np; ++i) {
-    pl->radix[i] = rad[i];
-    pl->ns[i] = ns;
-    ns *= rad[i];
-  }
-  return true;
-}
-
 static eacg_status sync_read(eacg_system* s, int ndouble) {
 
 
@@ -311,9 +256,8 @@ static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::st
     *why = "nbands > 64 is not supported by this build";
     return EACG_EUNSUPPORTED;
   }
-  FftPlan pl;
-  if (!make_plan(m->N, &pl)) {
-    *why = "grid size N must be 2^a 3^b or 2^a 5^c";
+  if (!grid_supported(m->N)) {
+    *why = "grid size N must be one of 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96";
     return EACG_EUNSUPPORTED;
   }
   if (prm && (!(prm->mu > 0) || prm->max_ls < 1 || prm->max_fom < 1)) {
@@ -402,10 +346,10 @@ static eacg_status build_basis(eacg_system* s) {
   TRY(dalloc(s, &s->d_kin, sizeof(double) * (size_t)K * s->n_max));
   grid_build_sphere(N, K, s->d_kfrac, s->thr, s->b, s->n_max, s->d_nk, d_rowoff, s->d_m, s->d_kin, d_colmark, s->st);
   CKL(s);
-  TRY(dalloc(s, &s->d_colfy, sizeof(int) * N * N));
-  TRY(dalloc(s, &s->d_colfz, sizeof(int) * N * N));
+  TRY(dalloc(s, &s->d_cmapy, sizeof(int) * N * (N + 1)));
+  TRY(dalloc(s, &s->d_rowmask, sizeof(int) * N));
   TRY(dalloc(s, &s->d_ylist, sizeof(int) * N));
-  grid_columns(N, d_colmark, d_colidx, s->d_colfy, s->d_colfz, d_scal, s->d_ylist, d_scal + 1, s->st);
+  grid_columns(N, d_colmark, d_colidx, s->d_cmapy, s->d_rowmask, d_scal, s->d_ylist, d_scal + 1, s->st);
   CKL(s);
   int hs[2];
   CK(cudaMemcpyAsync(hs, d_scal, sizeof(int) * 2, cudaMemcpyDeviceToHost, s->st));
@@ -1442,8 +1386,8 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   if ((st = up(&s->d_Z, s->Z)) != EACG_OK) return fail(st);
   if ((st = up(&s->d_rc, s->rc)) != EACG_OK) return fail(st);
   if ((st = up(&s->d_dvec, s->dvec)) != EACG_OK) return fail(st);
-  // FFT plan and twiddles e^{-2 pi i k / N}
-  make_plan(s->N, &s->g.plan);
+  // FFT twiddles e^{-2 pi i k / N}
+  s->g.N = s->N;
   {
     std::vector<double2> tw(s->N);
     std::vector<float2> tw32(s->N);
@@ -1467,11 +1411,10 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   s->g.n_max = s->n_max;
   s->g.ncols = s->ncols;
   s->g.ny = s->ny;
-  s->g.cols_per_cta = std::max(1, std::min(64, 256 / s->g.plan.TPL));
   s->g.nk = s->d_nk;
   s->g.xmap = s->d_xmap;
-  s->g.colfy = s->d_colfy;
-  s->g.colfz = s->d_colfz;
+  s->g.cmapy = s->d_cmapy;
+  s->g.rowmask = s->d_rowmask;
   s->g.ylist = s->d_ylist;
   s->g.tw64 = s->d_tw64;
   s->g.tw32 = s->d_tw32;

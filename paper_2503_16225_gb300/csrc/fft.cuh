@@ -1,27 +1,53 @@
-// Shared-memory Stockham FFT passes for one line of length N = prod(radices).
+// Line FFTs of compile-time length N for the plane-wave transforms.
 //
-// A line lives in shared memory; TPL = N / E threads own it.  In every pass of
-// radix R each thread loads E values (E / R butterflies) into registers, the
-// CTA synchronises, then each thread twiddles, applies the radix-R DFT and
-// stores its outputs in the autosorted position.  The whole CTA calls every
-// pass (the barriers are uniform); threads without a line pass active=false.
+// A line of length N = N1 * N2 (N1 a multiple of N2) is owned by N2 threads.  Writing
+// i = t + N2 m and k = k1 + N1 k2 (t, k2 < N2; m, k1 < N1),
 //
-// Transform convention: forward X_m = sum_j x_j e^{-2 pi i m j / N}, inverse
-// with +i; neither is normalised.  The twiddle table tw[k] = e^{-2 pi i k / N}
-// (k < N) is read from shared memory and conjugated for the inverse.
+//   X[k1 + N1 k2] = sum_t w_N2^{t k2} w_N^{t k1} sum_m x[t + N2 m] w_N1^{m k1},
+//
+// so thread t first forms the N1-point DFT of its strided values in registers and applies
+// the twiddles w_N^{t k1} (step 1), the values go through shared memory once, and thread t
+// then forms the N2-point DFTs of the columns k1 = t + N2 j (j < N1 / N2), again in
+// registers (step 2).  The register DFTs are mixed-radix Cooley-Tukey with every index
+// known at compile time.  Twiddles come from a per-line table tw[e] = e^{-2 pi i e / N} in
+// shared memory; all threads of a warp read the same entry (broadcast).
+//
+// Convention: forward X_k = sum_j x_j e^{-2 pi i k j / N}, inverse with +i; neither is
+// normalised.
+//
+// Thread layout: line index fastest.  With L lines in flight, thread i works on line
+// i % L at slot i / L, so the 16 (FP32) or 8 (FP64) threads of one shared-memory
+// wavefront touch 16 or 8 distinct lines at the same element index; line pitches are odd
+// in elements, which puts them in distinct banks.
 #pragma once
 #include "common.cuh"
 
 namespace eacg {
 
-struct FftPlan {
-  int N;      // line length
-  int E;      // values per thread (template argument of the kernels)
-  int TPL;    // threads per line = N / E
-  int npass;  // number of radix passes
-  int radix[8];
-  int ns[8];  // product of the radices of the earlier passes
-};
+template <int N>
+struct LinePlan;
+#define EACG_LINE_PLAN(N_, A_, B_)             \
+  template <>                                  \
+  struct LinePlan<N_> {                        \
+    static constexpr int N1 = A_, N2 = B_;     \
+  };
+EACG_LINE_PLAN(8, 4, 2)
+EACG_LINE_PLAN(12, 6, 2)
+EACG_LINE_PLAN(16, 4, 4)
+EACG_LINE_PLAN(20, 10, 2)
+EACG_LINE_PLAN(24, 12, 2)
+EACG_LINE_PLAN(32, 8, 4)
+EACG_LINE_PLAN(36, 12, 3)
+EACG_LINE_PLAN(40, 20, 2)
+EACG_LINE_PLAN(48, 12, 4)
+EACG_LINE_PLAN(64, 16, 4)
+EACG_LINE_PLAN(72, 12, 6)
+EACG_LINE_PLAN(80, 20, 4)
+EACG_LINE_PLAN(96, 24, 4)
+#undef EACG_LINE_PLAN
+
+// The supported line lengths (every N with a LinePlan), for host-side checks and dispatch.
+#define EACG_FOR_EACH_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(64) X(72) X(80) X(96)
 
 template <int R, bool INV, typename V>
 __device__ __forceinline__ void dft_small(V* v) {
@@ -63,86 +89,120 @@ __device__ __forceinline__ void dft_small(V* v) {
   }
 }
 
-template <typename V, int E, int R, bool INV>
-__device__ __forceinline__ void fft_pass(V* line, int es, int t, int TPL, int N, int Ns, const V* tw,
-                                         bool active) {
-  constexpr int B = E / R;
-  V v[E];
-  const int NR = N / R;
-  if (active) {
+// x * w_N^e (conjugated for the inverse), e in [0, N) known at compile time or uniform.
+template <int N, bool INV, typename V>
+__device__ __forceinline__ V twiddle(V x, int e, const V* tw) {
+  V w = tw[e];
+  if (INV) w.y = -w.y;
+  return cmul(x, w);
+}
+
+template <int M>
+struct FirstRadix {
+  static constexpr int R = (M % 4 == 0) ? 4 : (M % 2 == 0) ? 2 : (M % 3 == 0) ? 3 : 5;
+};
+
+// In-register DFT of length M (M divides N) on a[0..M), natural order in and out.
+// M = R Q with m = r + R q, k = u + Q s: A[u + Q s] = sum_r w_R^{r s} w_M^{r u} (DFT_Q a[r + R .])[u].
+template <int M, int N, bool INV, typename V>
+__device__ __forceinline__ void reg_dft(V* a, const V* tw) {
+  if constexpr (M == 2 || M == 3 || M == 4 || M == 5) {
+    dft_small<M, INV>(a);
+  } else if constexpr (M > 1) {
+    constexpr int R = FirstRadix<M>::R, Q = M / R;
+    V c[R][Q];
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const int j = t + b * TPL;
+    for (int r = 0; r < R; ++r) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b * R + r] = line[(j + r * NR) * es];
-    }
-  }
-  __syncthreads();
-  if (active) {
-    const int step = N / (Ns * R);
+      for (int q = 0; q < Q; ++q) c[r][q] = a[r + R * q];
+      reg_dft<Q, N, INV>(c[r], tw);
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const int j = t + b * TPL;
-      const int jm = j % Ns;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        V w = tw[r * jm * step];
-        if (INV) w.y = -w.y;
-        v[b * R + r] = cmul(v[b * R + r], w);
+      for (int u = 1; u < Q; ++u) {
+        const int e = (r * u) % M;
+        if (e == 0) continue;
+        if (4 * e == M) {
+          c[r][u] = mul_mi<INV>(c[r][u]);
+        } else {
+          c[r][u] = twiddle<N, INV>(c[r][u], e * (N / M), tw);
+        }
       }
-      dft_small<R, INV>(&v[b * R]);
-      const int d = (j / Ns) * Ns * R + jm;
-#pragma unroll
-      for (int r = 0; r < R; ++r) line[(d + r * Ns) * es] = v[b * R + r];
     }
+#pragma unroll
+    for (int u = 0; u < Q; ++u) {
+      V d[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) d[r] = c[r][u];
+      dft_small<R, INV>(d);
+#pragma unroll
+      for (int s = 0; s < R; ++s) a[u + Q * s] = d[s];
+    }
+  }
+}
+
+// Step 1 of slot t: a[m] = x[t + N2 m] in; a[k1] = w_N^{t k1} sum_m x[t + N2 m] w_N1^{m k1} out.
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void line_step1(V* a, int t, const V* tw) {
+  constexpr int N1 = LinePlan<N>::N1;
+  reg_dft<N1, N, INV>(a, tw);
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) a[k1] = twiddle<N, INV>(a[k1], t * k1, tw);  // t k1 < N
+}
+
+// Step 2 of slot t: a[j N2 + tt] = step-1 value of slot tt at k1 = t + N2 j in;
+// a[j N2 + k2] = X[(t + N2 j) + N1 k2] out.
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void line_step2(V* a, const V* tw) {
+  constexpr int N1 = LinePlan<N>::N1, N2 = LinePlan<N>::N2;
+#pragma unroll
+  for (int j = 0; j < N1 / N2; ++j) reg_dft<N2, N, INV>(a + j * N2, tw);
+}
+
+// One transform phase over nlines lines (nlines <= lines in flight = blockDim.x / N2).
+// Step-1 inputs come from load(l, i); step-1 outputs go to *scratch(l, position); step-2
+// outputs X[o] go to store(l, o, X[o], q), q < N1 being the output's ordinal within the
+// thread (the same for every call).  The CTA synchronises between the steps and after the
+// phase, and with MIDSYNC also between the step-2 loads and the stores (needed when the
+// scratch slots of a line are the places its outputs are stored to).  Every thread must
+// call it.
+template <int N, bool INV, bool MIDSYNC, typename V, typename Scratch, typename Load, typename Store>
+__device__ __forceinline__ void fft_phase(int nlines, const V* tw, const Scratch& scratch, const Load& load,
+                                          const Store& store) {
+  constexpr int N1 = LinePlan<N>::N1, N2 = LinePlan<N>::N2;
+  const int L = blockDim.x / N2;
+  const int l = threadIdx.x % L, t = threadIdx.x / L;
+  const bool act = t < N2 && l < nlines;
+  V a[N1];
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) a[m] = load(l, t + N2 * m);
+    line_step1<N, INV>(a, t, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) *scratch(l, t + N2 * k1) = a[k1];
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < N1 / N2; ++j)
+#pragma unroll
+      for (int tt = 0; tt < N2; ++tt) a[j * N2 + tt] = *scratch(l, tt + N2 * (t + N2 * j));
+    line_step2<N, INV>(a, tw);
+  }
+  if (MIDSYNC) __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < N1 / N2; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) store(l, (t + N2 * j) + N1 * k2, a[j * N2 + k2], j * N2 + k2);
   }
   __syncthreads();
 }
 
-// Full transform of one line (all passes).  Must be reached by every thread of the CTA.
-template <typename V, int E, bool INV>
-__device__ __forceinline__ void fft_line(V* line, int es, int t, const FftPlan& pl, const V* tw, bool active) {
-  for (int s = 0; s < pl.npass; ++s) {
-    const int R = pl.radix[s], Ns = pl.ns[s];
-    if (R == 2) {
-      if constexpr (E % 2 == 0) fft_pass<V, E, 2, INV>(line, es, t, pl.TPL, pl.N, Ns, tw, active);
-    } else if (R == 3) {
-      if constexpr (E % 3 == 0) fft_pass<V, E, 3, INV>(line, es, t, pl.TPL, pl.N, Ns, tw, active);
-    } else if (R == 4) {
-      if constexpr (E % 4 == 0) fft_pass<V, E, 4, INV>(line, es, t, pl.TPL, pl.N, Ns, tw, active);
-    } else if (R == 5) {
-      if constexpr (E % 5 == 0) fft_pass<V, E, 5, INV>(line, es, t, pl.TPL, pl.N, Ns, tw, active);
-    }
-  }
-}
-
-// Transform nlines lines of one CTA: line l starts at base + l * lstride, elements es apart.
-// Threads are grouped TPL per line; the trip count is uniform across the CTA.
-template <typename V, int E, bool INV>
-__device__ __forceinline__ void fft_lines(V* base, int nlines, int lstride, int es, const FftPlan& pl,
-                                          const V* tw) {
-  const int TPL = pl.TPL;
-  const int per = blockDim.x / TPL;
-  const int g = threadIdx.x / TPL, t = threadIdx.x - g * TPL;
-  for (int l0 = 0; l0 < nlines; l0 += per) {
-    const int l = l0 + g;
-    const bool active = (g < per) && (l < nlines);
-    fft_line<V, E, INV>(base + (size_t)(active ? l : 0) * lstride, es, t, pl, tw, active);
-  }
-}
-
-// Same with a list of line offsets (lines that are not equally spaced).
-template <typename V, int E, bool INV>
-__device__ __forceinline__ void fft_lines_list(V* base, const int* offs, int nlines, int es, const FftPlan& pl,
-                                               const V* tw) {
-  const int TPL = pl.TPL;
-  const int per = blockDim.x / TPL;
-  const int g = threadIdx.x / TPL, t = threadIdx.x - g * TPL;
-  for (int l0 = 0; l0 < nlines; l0 += per) {
-    const int l = l0 + g;
-    const bool active = (g < per) && (l < nlines);
-    fft_line<V, E, INV>(base + (active ? offs[l] : 0), es, t, pl, tw, active);
-  }
-}
+// Scratch lines A[l * AP + position] (AP odd) distinct from the phase's inputs and outputs.
+template <typename V>
+struct PitchedScratch {
+  V* A;
+  int AP;
+  __device__ __forceinline__ V* operator()(int l, int pos) const { return A + (size_t)l * AP + pos; }
+};
 
 }  // namespace eacg

@@ -1,0 +1,382 @@
+// Kernels of the pruned 3D FFT pair of the Hamiltonian and of the density, and of the
+// full 3D FFT of the potential build, for one compile-time grid size N (sm_103a).
+//
+// The transform of one band runs as
+//   x pass  over the disk columns (my, mz) of the cutoff sphere          k_xpass_inv
+//   plane   per x-plane jx: z over the rows that hold columns, y over
+//           every jz, potential multiply, y back, z back onto the columns k_plane_h
+//   x pass  back, gathered onto the sphere (+ kinetic term)               k_xpass_fwd
+// and the density replaces the last three by k_plane_rho.  Every line transform is the
+// two-step register FFT of fft.cuh; lines are read from and written to their final place
+// by the phase functors, so no kernel zeroes, scatters or gathers a plane separately.
+//
+// Layouts: psi[K][p][n_max]; tbuf[band][jx][col]; xmap[k][fx][col] (sphere index or -1);
+// cmapy[l][N + 1] (column of (ylist[l], fz) or -1); rowmask[fy] (1 if row fy holds columns);
+// real-space grids [jx][jy][jz].
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace eacg {
+
+constexpr int XPASS_THREADS = 256;  // x-pass CTA: 256 / N2 columns of one band
+
+// Inverse x pass: sphere coefficients gathered straight into the step-1 registers; the
+// transformed columns are written to tbuf[band][jx][col] (coalesced over columns).
+template <typename T, int N, typename TIO>
+__global__ void __launch_bounds__(XPASS_THREADS)
+    k_xpass_inv(const TIO* __restrict__ psi, int n_max, int p, const int* __restrict__ xmap, int ncols,
+                cplx<T>* __restrict__ tbuf, const cplx<T>* __restrict__ tw_g, const int* __restrict__ kactive) {
+  using V = cplx<T>;
+  constexpr int N2 = LinePlan<N>::N2;
+  __shared__ V tw[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* A = reinterpret_cast<V*>(smem_raw);
+  const int band = blockIdx.y, k = band / p;
+  if (kactive && !kactive[k]) return;
+  const int cpc = blockDim.x / N2;
+  const int c0 = blockIdx.x * cpc;
+  const int nc = min(cpc, ncols - c0);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int* xm = xmap + (size_t)k * N * ncols + c0;
+  const TIO* src = psi + (size_t)band * n_max;
+  V* dst = tbuf + (size_t)band * N * ncols + c0;
+  fft_phase<N, true, false>(
+      nc, tw, PitchedScratch<V>{A, N + 1},
+      [&](int l, int fx) {
+        const int id = xm[(size_t)fx * ncols + l];
+        return id >= 0 ? cvt<V>(src[id]) : mk<V>(0, 0);
+      },
+      [&](int l, int jx, V x, int) { dst[(size_t)jx * ncols + l] = x; });
+}
+
+// Forward x pass and gather: out = scale * FFT + kin * psi_in (kin may be null); the padding
+// beyond n_k is zeroed.
+template <typename T, int N, typename TIO>
+__global__ void __launch_bounds__(XPASS_THREADS)
+    k_xpass_fwd(const cplx<T>* __restrict__ tbuf, const int* __restrict__ xmap, int ncols,
+                const cplx<T>* __restrict__ tw_g, int n_max, int p, const int* __restrict__ nk,
+                const TIO* __restrict__ psi_in, const double* __restrict__ kin, double scale, TIO* __restrict__ out,
+                const int* __restrict__ kactive) {
+  using V = cplx<T>;
+  constexpr int N2 = LinePlan<N>::N2;
+  __shared__ V tw[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* A = reinterpret_cast<V*>(smem_raw);
+  const int band = blockIdx.y, k = band / p;
+  if (kactive && !kactive[k]) return;
+  const int cpc = blockDim.x / N2;
+  const int c0 = blockIdx.x * cpc;
+  const int nc = min(cpc, ncols - c0);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int* xm = xmap + (size_t)k * N * ncols + c0;
+  const V* src = tbuf + (size_t)band * N * ncols + c0;
+  TIO* o = out + (size_t)band * n_max;
+  const TIO* pin = psi_in + (size_t)band * n_max;
+  const double* kk = kin ? kin + (size_t)k * n_max : nullptr;
+  fft_phase<N, false, false>(
+      nc, tw, PitchedScratch<V>{A, N + 1}, [&](int l, int jx) { return src[(size_t)jx * ncols + l]; },
+      [&](int l, int fx, V x, int) {
+        const int id = xm[(size_t)fx * ncols + l];
+        if (id >= 0) {
+          double2 v = cscale(to_d(x), scale);
+          if (kk) {
+            const double2 s = to_d(pin[id]);
+            v.x += kk[id] * s.x;
+            v.y += kk[id] * s.y;
+          }
+          o[id] = cvt<TIO>(v);
+        }
+      });
+  if (blockIdx.x == 0) {
+    for (int i = nk[k] + threadIdx.x; i < n_max; i += blockDim.x) o[i] = cvt<TIO>(make_double2(0.0, 0.0));
+  }
+}
+
+// Shared set-up of the plane kernels: twiddles, row mask, row list and the column map of
+// the rows with columns, copied once per CTA.
+template <typename V, int N>
+__device__ __forceinline__ void plane_setup(V* tw, int* rows, int* yl, int* cm, const V* tw_g,
+                                            const int* rowmask, const int* ylist, const int* cmapy, int ny) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tw[i] = tw_g[i];
+    rows[i] = rowmask[i];
+  }
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) yl[i] = ylist[i];
+  for (int i = threadIdx.x; i < ny * (N + 1); i += blockDim.x) cm[i] = cmapy[i];
+  __syncthreads();
+}
+
+// Plane buffers: B = the plane [jy][jz] (pitch N + 1) and, where two planes fit in shared
+// memory, A = step-1 scratch (ping-pong: one barrier per step).  Otherwise the step-1
+// values stay in B in place and the phases that store into B add a barrier.
+template <typename T, int N>
+struct PlaneCfg {
+  static constexpr bool pingpong = 2 * sizeof(cplx<T>) * N * (N + 1) <= 200 * 1024;
+  static size_t smem_bytes(int ny) {
+    return (pingpong ? 2 : 1) * sizeof(cplx<T>) * (size_t)N * (N + 1) + sizeof(int) * (size_t)ny * (N + 1);
+  }
+};
+
+// Step-1 scratch of the z phases (line l = row ylist[l]) and of the y phases (line = jz).
+template <typename V, int N, bool PING>
+struct ZScratch {
+  V* A;
+  V* B;
+  const int* yl;
+  __device__ __forceinline__ V* operator()(int l, int pos) const {
+    return PING ? A + (size_t)l * (N + 1) + pos : B + (size_t)yl[l] * (N + 1) + pos;
+  }
+};
+template <typename V, int N, bool PING>
+struct YScratch {
+  V* A;
+  V* B;
+  __device__ __forceinline__ V* operator()(int jz, int pos) const {
+    return PING ? A + (size_t)jz * (N + 1) + pos : B + (size_t)pos * (N + 1) + jz;
+  }
+};
+
+// Apply the local potential to one x-plane of one band.  Only rows that hold columns are
+// read before the y pass, so nothing is zeroed.
+template <typename T, int N>
+__global__ void __launch_bounds__(N * LinePlan<N>::N2)
+    k_plane_h(cplx<T>* __restrict__ tbuf, int ncols, const int* __restrict__ cmapy, const int* __restrict__ ylist,
+              const int* __restrict__ rowmask, int ny, const T* __restrict__ v, const cplx<T>* __restrict__ tw_g, int p,
+              const int* __restrict__ kactive) {
+  using V = cplx<T>;
+  constexpr int PP = N + 1;
+  constexpr bool PING = PlaneCfg<T, N>::pingpong;
+  __shared__ V tw[N];
+  __shared__ int rows[N], yl[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* B = reinterpret_cast<V*>(smem_raw);
+  V* A = PING ? B + (size_t)N * PP : B;
+  int* cm = reinterpret_cast<int*>(B + (size_t)(PING ? 2 : 1) * N * PP);
+  const int jx = blockIdx.x, band = blockIdx.y;
+  if (kactive && !kactive[band / p]) return;
+  plane_setup<V, N>(tw, rows, yl, cm, tw_g, rowmask, ylist, cmapy, ny);
+  V* tb = tbuf + ((size_t)band * N + jx) * ncols;
+  const T* vv = v + (size_t)jx * N * N;
+  const ZScratch<V, N, PING> zs{A, B, yl};
+  const YScratch<V, N, PING> ys{A, B};
+  // z inverse over the rows with columns, straight from the column buffer
+  fft_phase<N, true, !PING>(
+      ny, tw, zs,
+      [&](int l, int fz) {
+        const int c = cm[l * PP + fz];
+        return c >= 0 ? tb[c] : mk<V>(0, 0);
+      },
+      [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
+  // y inverse over every jz (rows without columns are zero), times the potential
+  fft_phase<N, true, !PING>(
+      N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
+      [&](int jz, int jy, V x, int) { B[jy * PP + jz] = cscale(x, vv[jy * N + jz]); });
+  // y forward, keeping the rows with columns
+  fft_phase<N, false, !PING>(
+      N, tw, ys, [&](int jz, int jy) { return B[jy * PP + jz]; },
+      [&](int jz, int fy, V x, int) {
+        if (rows[fy]) B[fy * PP + jz] = x;
+      });
+  // z forward, back onto the columns
+  fft_phase<N, false, false>(
+      ny, tw, zs, [&](int l, int jz) { return B[yl[l] * PP + jz]; },
+      [&](int l, int fz, V x, int) {
+        const int c = cm[l * PP + fz];
+        if (c >= 0) tb[c] = x;
+      });
+}
+
+// Density of a group of bands on one x-plane: sum_b w_b |u_b|^2 in FP64 registers (each
+// grid point owned by one thread of the y pass, bands in a fixed order), written as
+// partial[g][jx][jy][jz].
+template <typename T, int N>
+__global__ void __launch_bounds__(N * LinePlan<N>::N2)
+    k_plane_rho(const cplx<T>* __restrict__ tbuf, int ncols, const int* __restrict__ cmapy,
+                const int* __restrict__ ylist, const int* __restrict__ rowmask, int ny,
+                const cplx<T>* __restrict__ tw_g, int nbands, int bands_per_group, const double* __restrict__ bw,
+                double* __restrict__ partial) {
+  using V = cplx<T>;
+  constexpr int PP = N + 1, N1 = LinePlan<N>::N1, N2 = LinePlan<N>::N2;
+  constexpr bool PING = PlaneCfg<T, N>::pingpong;
+  __shared__ V tw[N];
+  __shared__ int rows[N], yl[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* B = reinterpret_cast<V*>(smem_raw);
+  V* A = PING ? B + (size_t)N * PP : B;
+  int* cm = reinterpret_cast<int*>(B + (size_t)(PING ? 2 : 1) * N * PP);
+  const int jx = blockIdx.x, g = blockIdx.y;
+  plane_setup<V, N>(tw, rows, yl, cm, tw_g, rowmask, ylist, cmapy, ny);
+  const ZScratch<V, N, PING> zs{A, B, yl};
+  const YScratch<V, N, PING> ys{A, B};
+  double acc[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) acc[q] = 0.0;
+  const int b0 = g * bands_per_group, b1 = min(nbands, b0 + bands_per_group);
+  for (int band = b0; band < b1; ++band) {
+    const V* tb = tbuf + ((size_t)band * N + jx) * ncols;
+    fft_phase<N, true, !PING>(
+        ny, tw, zs,
+        [&](int l, int fz) {
+          const int c = cm[l * PP + fz];
+          return c >= 0 ? tb[c] : mk<V>(0, 0);
+        },
+        [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
+    const double w = bw[band];
+    fft_phase<N, true, false>(
+        N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
+        [&](int, int, V x, int q) {
+          const double2 u = to_d(x);
+          acc[q] += w * (u.x * u.x + u.y * u.y);
+        });
+  }
+  // thread (jz, t) of the y pass owns jy = (t + N2 j) + N1 k2 at q = j N2 + k2
+  const int L = blockDim.x / N2;
+  const int jz = threadIdx.x % L, t = threadIdx.x / L;
+  if (t < N2 && jz < N) {
+    double* out = partial + ((size_t)g * N + jx) * N * N;
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int jy = (t + N2 * (q / N2)) + N1 * (q % N2);
+      out[(size_t)jy * N + jz] = acc[q];
+    }
+  }
+}
+
+// Lines along one axis of a complex N^3 array a[x][y][z] (axis 2 = z, 1 = y, 0 = x),
+// transformed in place, 256 / N2 lines per CTA.
+template <int N, bool INV>
+__global__ void __launch_bounds__(XPASS_THREADS)
+    k_fft3_axis(double2* __restrict__ a, int axis, const double2* __restrict__ tw_g) {
+  constexpr int N2 = LinePlan<N>::N2;
+  __shared__ double2 tw[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int lpc = blockDim.x / N2;
+  const int l0 = blockIdx.x * lpc;
+  const int nl = min(lpc, N * N - l0);
+  auto addr = [&](int l, int j) -> size_t {
+    const int L = l0 + l, u = L / N, w = L - (L / N) * N;
+    if (axis == 2) return ((size_t)u * N + w) * N + j;
+    if (axis == 1) return ((size_t)u * N + j) * N + w;
+    return ((size_t)j * N + u) * N + w;
+  };
+  fft_phase<N, INV, false>(
+      nl, tw, PitchedScratch<double2>{A, N + 1}, [&](int l, int j) { return a[addr(l, j)]; },
+      [&](int l, int o, double2 x, int) { a[addr(l, o)] = x; });
+}
+
+// Launchers of one grid size; instantiated once per supported N (grid_fft_n*.cu).
+template <int N>
+struct GridFft {
+  static constexpr int N2 = LinePlan<N>::N2;
+
+  template <typename T, typename TIO>
+  static void xinv(const GridCtx& g, const TIO* psi, void* tbuf, const void* tw, int nbands, const int* kactive,
+                   cudaStream_t st) {
+    const int cpc = XPASS_THREADS / N2;
+    dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
+    const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
+    ensure_smem((const void*)k_xpass_inv<T, N, TIO>, sm);
+    k_xpass_inv<T, N, TIO><<<grid, cpc * N2, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf,
+                                                        (const cplx<T>*)tw, kactive);
+    count_launch();
+  }
+
+  template <typename T, typename TIO>
+  static void xfwd(const GridCtx& g, const void* tbuf, const void* tw, const TIO* psi_in, const double* kin,
+                   double scale, TIO* out, int nbands, const int* kactive, cudaStream_t st) {
+    const int cpc = XPASS_THREADS / N2;
+    dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
+    const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
+    ensure_smem((const void*)k_xpass_fwd<T, N, TIO>, sm);
+    k_xpass_fwd<T, N, TIO><<<grid, cpc * N2, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, (const cplx<T>*)tw,
+                                                        g.n_max, g.p, g.nk, psi_in, kin, scale, out, kactive);
+    count_launch();
+  }
+
+  // mode 0: FP64 transforms of FP64 blocks; 1: FP32 transforms of FP64 blocks;
+  // 2: FP32 transforms of FP32 blocks
+  static void xpass_inv(const GridCtx& g, int mode, const void* psi, void* tbuf, int nbands, const int* kactive,
+                        cudaStream_t st) {
+    if (mode == 0)
+      xinv<double>(g, (const double2*)psi, tbuf, g.tw64, nbands, kactive, st);
+    else if (mode == 1)
+      xinv<float>(g, (const double2*)psi, tbuf, g.tw32, nbands, kactive, st);
+    else
+      xinv<float>(g, (const float2*)psi, tbuf, g.tw32, nbands, kactive, st);
+  }
+
+  static void xpass_fwd(const GridCtx& g, int mode, const void* tbuf, const void* psi_in, const double* kin,
+                        double scale, void* out, int nbands, const int* kactive, cudaStream_t st) {
+    if (mode == 0)
+      xfwd<double>(g, tbuf, g.tw64, (const double2*)psi_in, kin, scale, (double2*)out, nbands, kactive, st);
+    else if (mode == 1)
+      xfwd<float>(g, tbuf, g.tw32, (const double2*)psi_in, kin, scale, (double2*)out, nbands, kactive, st);
+    else
+      xfwd<float>(g, tbuf, g.tw32, (const float2*)psi_in, kin, scale, (float2*)out, nbands, kactive, st);
+  }
+
+  template <typename T>
+  static void plane_h_t(const GridCtx& g, void* tbuf, const void* tw, const void* v, int nbands, const int* kactive,
+                        cudaStream_t st) {
+    const size_t sm = PlaneCfg<T, N>::smem_bytes(g.ny);
+    ensure_smem((const void*)k_plane_h<T, N>, sm);
+    k_plane_h<T, N><<<dim3(N, nbands), N * N2, sm, st>>>((cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist, g.rowmask, g.ny,
+                                                         (const T*)v, (const cplx<T>*)tw, g.p, kactive);
+    count_launch();
+  }
+
+  static void plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
+                      cudaStream_t st) {
+    if (prec == 0)
+      plane_h_t<double>(g, tbuf, g.tw64, v, nbands, kactive, st);
+    else
+      plane_h_t<float>(g, tbuf, g.tw32, v, nbands, kactive, st);
+  }
+
+  template <typename T>
+  static void plane_rho_t(const GridCtx& g, const void* tbuf, const void* tw, int nbands, int groups,
+                          const double* bw, double* partial, cudaStream_t st) {
+    const size_t sm = PlaneCfg<T, N>::smem_bytes(g.ny);
+    ensure_smem((const void*)k_plane_rho<T, N>, sm);
+    const int bpg = (nbands + groups - 1) / groups;
+    k_plane_rho<T, N><<<dim3(N, groups), N * N2, sm, st>>>((const cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist,
+                                                           g.rowmask, g.ny, (const cplx<T>*)tw, nbands, bpg, bw,
+                                                           partial);
+    count_launch();
+  }
+
+  static void plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
+                        double* partial, cudaStream_t st) {
+    if (prec == 0)
+      plane_rho_t<double>(g, tbuf, g.tw64, nbands, groups, bw, partial, st);
+    else
+      plane_rho_t<float>(g, tbuf, g.tw32, nbands, groups, bw, partial, st);
+  }
+
+  template <bool INV>
+  static void fft3_axis(const GridCtx& g, double2* a, int axis, cudaStream_t st) {
+    const int lpc = XPASS_THREADS / N2;
+    const size_t sm = sizeof(double2) * (size_t)lpc * (N + 1);
+    ensure_smem((const void*)k_fft3_axis<N, INV>, sm);
+    k_fft3_axis<N, INV><<<(N * N + lpc - 1) / lpc, lpc * N2, sm, st>>>(a, axis, (const double2*)g.tw64);
+    count_launch();
+  }
+
+  static void fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
+    for (int axis = 2; axis >= 0; --axis) {
+      if (inverse)
+        fft3_axis<true>(g, a, axis, st);
+      else
+        fft3_axis<false>(g, a, axis, st);
+    }
+  }
+};
+
+}  // namespace eacg

@@ -1,0 +1,11 @@
+// FFT kernels of the grid sizes 8 to 24 (one instantiation unit per group of sizes keeps
+// the parallel build short).
+#include "grid_fft.cuh"
+
+namespace eacg {
+template struct GridFft<8>;
+template struct GridFft<12>;
+template struct GridFft<16>;
+template struct GridFft<20>;
+template struct GridFft<24>;
+}  // namespace eacg

@@ -1,0 +1,7 @@
+// FFT kernels of the grid sizes 80 and 96.
+#include "grid_fft.cuh"
+
+namespace eacg {
+template struct GridFft<80>;
+template struct GridFft<96>;
+}  // namespace eacg

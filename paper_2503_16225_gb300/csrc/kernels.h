@@ -4,7 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
-#include "fft.cuh"
+#include "common.cuh"
+
 
 namespace eacg {
 
@@ -18,21 +19,22 @@ void ensure_smem(const void* func, size_t bytes);
 
 // Device-side description of the plane-wave grid of one system.
 struct GridCtx {
-  FftPlan plan;
-  int K, p, n_max, ncols, ny, cols_per_cta;
-  const int* nk;      // [K]
-  const int* xmap;    // [K][ncols][N]
-  const int* colfy;   // [ncols]
-  const int* colfz;   // [ncols]
-  const int* ylist;   // [ny]
-  const void* tw64;   // double2[N]
-  const void* tw32;   // float2[N]
+  int N, K, p, n_max, ncols, ny;
+  const int* nk;       // [K]
+  const int* xmap;     // [K][N][ncols]: sphere index of (fx, column) at k, or -1
+  const int* cmapy;    // [ny][N + 1]: column of (ylist[l], fz), or -1
+  const int* rowmask;  // [N]: 1 if row fy holds columns
+  const int* ylist;    // [ny]: the rows fy that hold columns
+  const void* tw64;    // double2[N]
+  const void* tw32;    // float2[N]
 };
 
 // ---- grid_kernels.cu
 void grid_build_sphere(int N, int K, const double* kfrac_d, double thr, double b, int n_max_cap, int* nk, int* row_off,
                        int* m, double* kin, int* colmark, cudaStream_t st);
-void grid_columns(int N, const int* colmark, int* colidx, int* colfy, int* colfz, int* ncols, int* ylist, int* ny,
+// True if N has a compile-time line plan (the grid sizes this library transforms).
+bool grid_supported(int N);
+void grid_columns(int N, const int* colmark, int* colidx, int* cmapy, int* rowmask, int* ncols, int* ylist, int* ny,
                   cudaStream_t st);
 void grid_xmap(int N, int K, int n_max, const int* nk, const int* m, const int* colidx, int ncols, int* xmap,
                cudaStream_t st);
