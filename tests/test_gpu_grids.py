@@ -1,0 +1,76 @@
+"""Every grid size with a compiled FFT plan, against the FP64 CPU oracle.
+
+Each supported N gets a small two-atom crystal (two bands, s/p projectors, a shifted
+k-point) whose cutoff sphere reaches about a quarter of the grid, so that every
+transform phase (x columns, z rows, y lines, the potential multiply, the density) runs
+on several lines with a partial disk.  Density and potential (FP64 transforms, including
+the full 3D FFT of the Hartree term) to relative 1e-11; H psi to 1e-11 with FP64
+transforms and 5e-6 with FP32 transforms (the tolerances of the main parity suite)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.model import Model
+from tests.conftest import ensure_library
+from tests.small_models import small
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+ensure_library()
+import paper_2503_16225_gb300 as E  # noqa: E402
+
+GRID_N = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96)
+
+
+def grid_model(N):
+    a = 8.0
+    b = 2.0 * math.pi / a
+    mmax = 0.23 * N                      # sphere radius in grid units
+    ecut = 0.5 * (b * mmax) ** 2
+    return small(a=a, N=N, ecut=ecut, nb=2, nproj=4, kgrid=(2, 1, 1), seed=40 + N)
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+@pytest.mark.parametrize("N", GRID_N)
+def test_grid_size(N):
+    cfg = grid_model(N)
+    model = Model(cfg)
+    s = E.System(cfg)
+    try:
+        assert s.nk == model.nk
+        rng = np.random.default_rng(N)
+        Phi = [np.linalg.qr(rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2)))[0] for n in model.nk]
+        t = torch.zeros((s.K, s.p, s.n_max), dtype=torch.complex128)
+        for k, P in enumerate(Phi):
+            t[k, :, :P.shape[0]] = torch.from_numpy(np.ascontiguousarray(P.T))
+        phi = t.cuda()
+        rho = s.grid()
+        E.eacg_density(s.h, phi, rho, 0)
+        rho_o = model.density(Phi)
+        assert rel(rho.cpu().numpy(), rho_o) < 1e-11
+        v = s.grid()
+        E.eacg_get_potential(s.h, v)
+        vtot = model.potentials(rho_o)[0]
+        assert rel(v.cpu().numpy(), vtot) < 1e-11
+        C = [rng.standard_normal(P.shape) + 1j * rng.standard_normal(P.shape) for P in Phi]
+        t.zero_()
+        for k, Ck in enumerate(C):
+            t[k, :, :Ck.shape[0]] = torch.from_numpy(np.ascontiguousarray(Ck.T))
+        c = t.cuda()
+        for prec, tol in ((0, 1e-11), (1, 5e-6)):
+            out = s.block()
+            E.eacg_apply_H(s.h, c, out, prec)
+            h = out.cpu().numpy()
+            for k in range(model.K):
+                got = h[k, :, :model.nk[k]].T
+                assert rel(got, model.apply_H(k, C[k], vtot)) < tol, (N, prec, k)
+                assert np.all(h[k, :, model.nk[k]:] == 0)
+    finally:
+        s.close()
