@@ -6,10 +6,13 @@ TEST INFRASTRUCTURE ONLY (see oracle/model.py).
 Readings where the paper is silent or garbled:
   * the new rows of C_{j+1} are V~_{j+1}^* C (the newly added block), which keeps
     C_j = V_j^* C consistent with A_j = V_j^* H V_j;
-  * the rank-revealing orthonormalisation projects out V_j twice, takes the
-    eigen-decomposition of the block Gram matrix, drops eigenvalues below
-    1e-12 * (largest), scales, and repeats the Gram/eigen step once on the
-    kept block to restore orthonormality; rank 0 ends the iteration;
+  * the rank-revealing QR projects out V_j twice, then orthonormalises by a
+    Cholesky factorisation of the block Gram matrix with diagonal pivoting, which
+    is QR with column pivoting (largest remaining column norm first) written on
+    the Gram matrix; it stops when the largest remaining squared column norm is
+    below 1e-12 times the largest squared column norm of the block before the
+    projection, and repeats the pivoted Cholesky step once on the kept block to
+    restore orthonormality; rank 0 ends the iteration;
   * the projected Sylvester equation A_j Y - Y Sigma = C_j is solved by
     diagonalising A_j and Sigma;
   * the TPA preconditioner scales column i by 1 / (1/2 |k+G|^2 + alpha_i),
@@ -24,22 +27,52 @@ from .manifold import herm
 RANK_TOL = 1e-12
 
 
+def pivoted_cholesky(G, ref, tol):
+    """Diagonally pivoted Cholesky of the Hermitian PSD matrix G: returns (piv, L) with
+    G[piv][:, piv] ~ L L^* on the r selected columns (L lower r x r).  Step j takes the
+    largest remaining Schur-complement diagonal (first one on ties) and stops when it is
+    not above tol * ref.  On a Gram matrix R^* R this is QR with column pivoting of R."""
+    S = np.array(G, dtype=np.complex128)
+    n = S.shape[0]
+    piv = list(range(n))
+    L = np.zeros((n, n), dtype=np.complex128)
+    r = 0
+    for j in range(n):
+        d = S.diagonal().real[j:]
+        m = j + int(np.argmax(d))
+        if not d[m - j] > tol * ref:
+            break
+        # symmetric swap of positions j and m
+        S[[j, m], :] = S[[m, j], :]
+        S[:, [j, m]] = S[:, [m, j]]
+        L[[j, m], :] = L[[m, j], :]
+        piv[j], piv[m] = piv[m], piv[j]
+        ljj = np.sqrt(S[j, j].real)
+        L[j, j] = ljj
+        L[j + 1:, j] = S[j + 1:, j] / ljj
+        S[j + 1:, j + 1:] -= np.outer(L[j + 1:, j], L[j + 1:, j].conj())
+        r += 1
+    return piv[:r], L[:r, :r]
+
+
 def orthonormalise(R, V=None, tol=RANK_TOL):
     """Orthonormal basis of range((I - V V^*) R), rank-revealing; returns (n, q~) block."""
     R = R.copy()
-    lref = np.linalg.eigvalsh(herm(R.conj().T @ R)).max() if R.shape[1] else 0.0
+    ref = float((np.abs(R) ** 2).sum(axis=0).max()) if R.shape[1] else 0.0
     if V is not None and V.shape[1]:
         for _ in range(2):
             R = R - V @ (V.conj().T @ R)
-    G = herm(R.conj().T @ R)
-    lam, U = np.linalg.eigh(G)
-    if not lref > 0:
+    if not ref > 0:
         return R[:, :0]
-    keep = lam > tol * lref
-    Q = R @ (U[:, keep] / np.sqrt(lam[keep]))
-    # second pass: the same Gram/eigen scaling on the kept block
-    lam2, U2 = np.linalg.eigh(herm(Q.conj().T @ Q))
-    return Q @ (U2 / np.sqrt(lam2))
+    Q = R
+    for pass_ref in (ref, None):
+        if Q.shape[1] == 0:
+            break
+        G = herm(Q.conj().T @ Q)
+        piv, L = pivoted_cholesky(G, pass_ref if pass_ref is not None else G.diagonal().real.max(), tol)
+        # Q_sel = Q_new L^*  =>  Q_new = Q_sel L^{-*}
+        Q = np.linalg.solve(L, Q[:, piv].conj().T).conj().T if piv else Q[:, :0]
+    return Q
 
 
 def sylvester_projected(A, Sigma, C):

@@ -488,46 +488,6 @@ void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V
                 cudaStream_t st) {
   heig_t<double>(K, p, A, sA, w, V, kactive, st);
 }
-// Largest eigenvalue of K Hermitian positive semidefinite p x p matrices by 24 power
-// iterations from the all-ones vector (Rayleigh quotient of the last iterate), FP64.
-__global__ void k_power_max(int p, const double2* __restrict__ G, double* __restrict__ out) {
-  const int k = blockIdx.x;
-  __shared__ double2 x[64];
-  __shared__ double2 y[64];
-  __shared__ double nrm;
-  const double2* Gk = G + (size_t)k * p * p;
-  for (int i = threadIdx.x; i < p; i += blockDim.x) x[i] = make_double2(1.0, 0.0);
-  __syncthreads();
-  double lam = 0.0;
-  for (int it = 0; it < 24; ++it) {
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-      double2 a = make_double2(0.0, 0.0);
-      for (int j = 0; j < p; ++j) a = cfma(Gk[(size_t)j * p + i], x[j], a);
-      y[i] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double yy = 0.0, xy = 0.0;
-      for (int i = 0; i < p; ++i) {
-        yy += cabs2(y[i]);
-        xy += x[i].x * y[i].x + x[i].y * y[i].y;
-      }
-      double xx = 0.0;
-      for (int i = 0; i < p; ++i) xx += cabs2(x[i]);
-      lam = xx > 0.0 ? xy / xx : 0.0;
-      nrm = yy > 0.0 ? 1.0 / sqrt(yy) : 0.0;
-      out[k] = lam;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < p; i += blockDim.x) x[i] = cscale(y[i], nrm);
-    __syncthreads();
-  }
-}
-void small_power_max(int K, int p, const double2* G, double* out, cudaStream_t st) {
-  k_power_max<<<K, 32, 0, st>>>(p, G, out);
-  count_launch();
-}
-
 // out = V diag(f(w)) V^H, f(x) = x^expo for x > cut_rel * max(w, 0), else 0
 __global__ void k_eig_func(int p, const double2* __restrict__ V, const double* __restrict__ w, double expo,
                            double cut_rel, double2* __restrict__ out, const int* __restrict__ kactive) {
@@ -1043,28 +1003,130 @@ void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const in
 
 // ----------------------------------------------------------------------------- small helpers
 // M[:, i] = U[:, i] w_i^{-1/2} when w_i > tol * lref[k] (and lref[k] > 0), else 0; nzero[k] = dropped count.
-__global__ void k_orth_scale(int p, const double2* __restrict__ U, const double* __restrict__ w,
-                             const double* __restrict__ lref, double tol, double2* __restrict__ M, int* __restrict__ nzero) {
+// Rank-revealing orthonormalisation factor of a block from its Gram matrix G = R^* R (p x p,
+// FP64, one CTA per k): Cholesky with diagonal pivoting, i.e. QR with column pivoting of R
+// written on G.  Step j takes the largest remaining Schur-complement diagonal (first position
+// on ties) and stops when it is not above tol * ref[k] (ref null: the largest diagonal of G).
+// With r selected columns piv[0..r) and G[piv][:, piv] = L L^*, the factor M has zero columns
+// 0..p-r-1 and column p-r+c = sum_a e_{piv[a]} (L^{-*})_{ac}, so R M is orthonormal on its
+// last r columns; nzero[k] = p - r.
+__global__ void k_pivchol(int p, const double2* __restrict__ G, const double* __restrict__ ref, double tol,
+                          double2* __restrict__ M, int* __restrict__ nzero, const int* __restrict__ kactive) {
   const int k = blockIdx.x;
-  const double ref = lref[k];
+  if (kactive && !kactive[k]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* S = reinterpret_cast<double2*>(smem_raw);  // Schur complement, S(i, j) = S[j * p + i]
+  double2* L = S + p * p;                             // factor, then its inverse
+  int* piv = reinterpret_cast<int*>(L + p * p);
+  __shared__ int mstep, rsel;
+  __shared__ double thr;
+  const double2* Gk = G + (size_t)k * p * p;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int j = e / p;
-    const double wj = w[(size_t)k * p + j];
-    const bool keep = ref > 0.0 && wj > tol * ref;
-    M[(size_t)k * p * p + e] = keep ? cscale(U[(size_t)k * p * p + e], 1.0 / sqrt(wj)) : make_double2(0.0, 0.0);
+    const int j = e / p, i = e - j * p;
+    const double2 a = Gk[(size_t)j * p + i], b = Gk[(size_t)i * p + j];
+    S[e] = make_double2(0.5 * (a.x + b.x), i == j ? 0.0 : 0.5 * (a.y - b.y));
+    L[e] = make_double2(0.0, 0.0);
   }
-  if (threadIdx.x == 0 && nzero) {
-    int nz = 0;
-    for (int j = 0; j < p; ++j) {
-      const double wj = w[(size_t)k * p + j];
-      if (!(ref > 0.0 && wj > tol * ref)) ++nz;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) piv[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r0 = ref ? ref[k] : 0.0;
+    if (!ref)
+      for (int i = 0; i < p; ++i) r0 = fmax(r0, S[i * p + i].x);
+    thr = tol * r0;
+    rsel = 0;
+  }
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x == 0) {
+      int m = j;
+      for (int i = j + 1; i < p; ++i)
+        if (S[i * p + i].x > S[m * p + m].x) m = i;
+      mstep = (S[m * p + m].x > thr) ? m : -1;
     }
-    nzero[k] = nz;
+    __syncthreads();
+    const int m = mstep;
+    if (m < 0) break;
+    if (m != j) {  // symmetric swap of positions j and m in S, rows of L, piv
+      for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        const double2 t = S[c * p + j];
+        S[c * p + j] = S[c * p + m];
+        S[c * p + m] = t;
+      }
+      __syncthreads();
+      for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        const double2 t = S[j * p + c];
+        S[j * p + c] = S[m * p + c];
+        S[m * p + c] = t;
+      }
+      for (int c = threadIdx.x; c < j; c += blockDim.x) {
+        const double2 t = L[c * p + j];
+        L[c * p + j] = L[c * p + m];
+        L[c * p + m] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int t = piv[j];
+        piv[j] = piv[m];
+        piv[m] = t;
+      }
+      __syncthreads();
+    }
+    const double ljj = sqrt(S[j * p + j].x);
+    const double inv = 1.0 / ljj;
+    for (int i = j + threadIdx.x; i < p; i += blockDim.x)
+      L[j * p + i] = i == j ? make_double2(ljj, 0.0) : cscale(S[j * p + i], inv);
+    __syncthreads();
+    const int t = p - j - 1;
+    for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+      const int b = j + 1 + e / t, a = j + 1 + e % t;
+      S[b * p + a] = S[b * p + a] - cmul(L[j * p + a], cconj(L[j * p + b]));
+    }
+    if (threadIdx.x == 0) rsel = j + 1;
+    __syncthreads();
   }
+  __syncthreads();
+  const int r = rsel;
+  // X = L^{-1} (lower), column c by forward substitution, one thread per column
+  double2* X = S;
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    for (int i = 0; i < r; ++i) X[c * p + i] = make_double2(0.0, 0.0);
+    X[c * p + c] = make_double2(1.0 / L[c * p + c].x, 0.0);
+    for (int i = c + 1; i < r; ++i) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int a = c; a < i; ++a) acc = acc + cmul(L[a * p + i], X[c * p + a]);
+      X[c * p + i] = cscale(acc, -1.0 / L[i * p + i].x);
+    }
+  }
+  __syncthreads();
+  double2* Mk = M + (size_t)k * p * p;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) Mk[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  // M[piv[a]][p - r + c] = conj(X[c][a]) for a <= c
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int c = e / r, a = e - c * r;
+    if (a <= c) Mk[(size_t)(p - r + c) * p + piv[a]] = cconj(X[a * p + c]);
+  }
+  if (threadIdx.x == 0 && nzero) nzero[k] = p - r;
 }
-void small_orth_scale(int K, int p, const double2* U, const double* w, const double* lref, double tol, double2* M,
-                      int* nzero, cudaStream_t st) {
-  k_orth_scale<<<K, 256, 0, st>>>(p, U, w, lref, tol, M, nzero);
+void small_pivchol(int K, int p, const double2* G, const double* ref, double tol, double2* M, int* nzero,
+                   const int* kactive, cudaStream_t st) {
+  const size_t sm = sizeof(double2) * 2 * p * p + sizeof(int) * p;
+  ensure_smem((const void*)k_pivchol, sm);
+  k_pivchol<<<K, 128, sm, st>>>(p, G, ref, tol, M, nzero, kactive);
+  count_launch();
+}
+
+// Largest diagonal entry (real part) of K p x p matrices: the largest squared column norm
+// when G is a Gram matrix.
+__global__ void k_max_diag(int K, int p, const double2* __restrict__ G, double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const double2* Gk = G + (size_t)k * p * p;
+  double m = Gk[0].x;
+  for (int i = 1; i < p; ++i) m = fmax(m, Gk[(size_t)i * p + i].x);
+  out[k] = m;
+}
+void small_max_diag(int K, int p, const double2* G, double* out, cudaStream_t st) {
+  k_max_diag<<<(K + 127) / 128, 128, 0, st>>>(K, p, G, out);
   count_launch();
 }
 
@@ -1098,17 +1160,6 @@ void small_take_y(int K, int q, int qcap, int p, const double2* Y, double2* Yf, 
   count_launch();
 }
 
-__global__ void k_max_eval(int K, int p, const double* __restrict__ w, double* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double m = w[(size_t)k * p];
-  for (int i = 1; i < p; ++i) m = fmax(m, w[(size_t)k * p + i]);
-  out[k] = m;
-}
-void small_max_eval(int K, int p, const double* w, double* out, cudaStream_t st) {
-  k_max_eval<<<(K + 127) / 128, 128, 0, st>>>(K, p, w, out);
-  count_launch();
-}
 
 __global__ void k_conj_transpose(int p, const double2* __restrict__ A, double2* __restrict__ out) {
   const int k = blockIdx.x;

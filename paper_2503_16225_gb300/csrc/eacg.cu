@@ -35,11 +35,11 @@ struct Status {
 }  // namespace
 
 namespace eacg {
-void small_orth_scale(int K, int p, const double2* U, const double* w, const double* lref, double tol, double2* M,
-                      int* nzero, cudaStream_t st);
+void small_pivchol(int K, int p, const double2* G, const double* ref, double tol, double2* M, int* nzero,
+                   const int* kactive, cudaStream_t st);
+void small_max_diag(int K, int p, const double2* G, double* out, cudaStream_t st);
 void small_put_herm_block(int K, int p, const double2* src, double2* A, int lda, size_t sA, int q0, cudaStream_t st);
 void small_take_y(int K, int q, int qcap, int p, const double2* Y, double2* Yf, const int* take, cudaStream_t st);
-void small_max_eval(int K, int p, const double* w, double* out, cudaStream_t st);
 void small_conj_transpose(int K, int p, const double2* A, double2* out, cudaStream_t st);
 void small_add_herm(int K, int p, const double2* A, double s, double2* out, cudaStream_t st);
 void small_sqrt_vals(int K, int p, const double* w, double* out, cudaStream_t st);
@@ -80,7 +80,7 @@ struct eacg_system {
   // small [K][p][p]
   double2 *lam = nullptr, *lam_t = nullptr, *sm1 = nullptr, *sm2 = nullptr, *sm3 = nullptr, *evec = nullptr,
           *evec_t = nullptr, *sinv_t = nullptr, *sig = nullptr, *sigv = nullptr, *sigvh = nullptr;
-  double *eval = nullptr, *eval_t = nullptr, *sval = nullptr, *alpha = nullptr, *sqd = nullptr, *lref = nullptr;
+  double *eval = nullptr, *eval_t = nullptr, *alpha = nullptr, *sqd = nullptr, *lref = nullptr;
   double2* cn_work = nullptr;
   size_t cn_elems = 0;
   double* d_red = nullptr;    // reduction scratch
@@ -415,7 +415,7 @@ static eacg_status alloc_work(eacg_system* s) {
   double2** smalls[] = {&s->lam, &s->lam_t, &s->sm1, &s->sm2, &s->sm3, &s->evec, &s->evec_t, &s->sinv_t,
                         &s->sig, &s->sigv, &s->sigvh};
   for (auto m : smalls) TRY(dalloc(s, m, sp));
-  double** vecs[] = {&s->eval, &s->eval_t, &s->sval, &s->alpha, &s->sqd, &s->lref};
+  double** vecs[] = {&s->eval, &s->eval_t, &s->alpha, &s->sqd, &s->lref};
   for (auto v : vecs) TRY(dalloc(s, v, sizeof(double) * (size_t)K * p));
   // tbuf: one FP64 complex value per (band, jx, column)
   TRY(dalloc(s, &s->d_tbuf, sizeof(double2) * (size_t)K * p * N * s->ncols));
@@ -782,18 +782,20 @@ static eacg_status apply_H_t(eacg_system* s, const float2* in, float2* out, cons
 }
 
 // Rank-revealing orthonormalisation of R (n x p per k) against the first q columns of V
-// (Algorithm 4, reading: two projections, eigen-decomposition of the Gram matrix with a
-// relative drop tolerance against the Gram of R before projection, second pass).
-// Result into out (n x p per k, dropped directions as leading zero columns), nzero[k].
+// (Algorithm 4's rank-revealing QR, reading: two projections, then QR with column pivoting
+// written as a diagonally pivoted Cholesky of the Gram matrix, stopped below a relative
+// tolerance of the largest squared column norm of R before projection; a second pivoted
+// Cholesky pass on the kept block).  Result into out (n x p per k, dropped directions as
+// leading zero columns), nzero[k].
 template <typename T>
 static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, int q, size_t sV, cplx<T>* out,
                                   cplx<T>* scratch, const int* kactive) {
   using O = FomOps<T>;
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
-  // reference: largest Gram eigenvalue before projection (power iteration)
+  // reference: largest squared column norm before projection
   O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
-  small_power_max(K, p, s->sm1, s->lref, s->st);
+  small_max_diag(K, p, s->sm1, s->lref, s->st);
   if (q > 0) {
     for (int pass = 0; pass < 2; ++pass) {
       O::cn(K, nm, q, p, V, sV, nm, R, sb, nm, s->fYt, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work, kactive,
@@ -803,15 +805,12 @@ static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, 
   }
   // first (rank-revealing) pass
   O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
-  dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
-  small_orth_scale(K, p, s->sm2, s->sval, s->lref, O::drop_tol, s->sm3, s->d_nzero, s->st);
+  small_pivchol(K, p, s->sm1, s->lref, O::drop_tol, s->sm3, s->d_nzero, kactive, s->st);
   O::nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, scratch, sb, nm, ONE, ZERO, kactive, s->st);
-  // second pass on the kept block
+  // second pass on the kept block (reference: its own largest column norm)
   O::cn(K, nm, p, p, scratch, sb, nm, scratch, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive,
         s->st);
-  dense_heig(K, p, s->sm1, (size_t)p * p, s->sval, s->sm2, kactive, s->st);
-  small_max_eval(K, p, s->sval, s->lref, s->st);
-  small_orth_scale(K, p, s->sm2, s->sval, s->lref, O::drop_tol, s->sm3, s->d_info, s->st);
+  small_pivchol(K, p, s->sm1, nullptr, O::drop_tol, s->sm3, s->d_info, kactive, s->st);
   O::nn(K, nm, p, p, scratch, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st);
   CKL(s);
   return EACG_OK;

@@ -93,8 +93,6 @@ void dense_tpa32(int K, int p, int n_max, const double* kin, const double* alpha
 // Hermitian eigen-decomposition of K matrices p x p (ld p): ascending eigenvalues and
 // unit eigenvectors (columns).  p <= 64.
 void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive, cudaStream_t st);
-// Largest eigenvalue of K Hermitian positive semidefinite p x p matrices (power iteration), p <= 64.
-void small_power_max(int K, int p, const double2* G, double* out, cudaStream_t st);
 // out[k] = V diag(f(w)) V^H with f(x) = x^e (e = -0.5, 0.5) restricted to w > cut; else 0.
 void dense_eig_func(int K, int p, const double2* V, const double* w, double expo, double cut_rel, double2* out,
                     const int* kactive, cudaStream_t st);

@@ -104,6 +104,32 @@ def test_orthonormalise_is_rank_revealing():
     assert np.abs(V.conj().T @ Q).max() < 1e-13
 
 
+def test_pivoted_cholesky_is_qr_with_column_pivoting():
+    """On a Gram matrix the pivoted Cholesky is Householder QR with column pivoting (LAPACK
+    geqp3): the same pivot order and |L| = |R^*|, so the orthonormalisation is an RRQR."""
+    rng = np.random.default_rng(17)
+    R = _rand(rng, 40, 7) * np.array([0.3, 2.0, 1.0, 5.0, 0.7, 1.5, 3.0])
+    G = R.conj().T @ R
+    piv, L = fom.pivoted_cholesky(G, 1.0, 1e-12)
+    Qr, Rr, P = sla.qr(R, mode="economic", pivoting=True)
+    assert list(P) == piv
+    np.testing.assert_allclose(np.abs(L), np.abs(Rr.conj().T), atol=1e-12)
+    np.testing.assert_allclose(L @ L.conj().T, G[np.ix_(piv, piv)], atol=1e-11)
+
+
+def test_pivoted_cholesky_stops_at_the_numerical_rank():
+    rng = np.random.default_rng(18)
+    B = _rand(rng, 30, 3)
+    R = np.hstack([B, B @ _rand(rng, 3, 2)])          # rank 3, five columns
+    G = R.conj().T @ R
+    piv, L = fom.pivoted_cholesky(G, np.abs(np.diag(G)).max(), 1e-12)
+    assert len(piv) == 3
+    # the kept columns span range(R)
+    Q = np.linalg.solve(L, R[:, piv].conj().T).conj().T
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(3), atol=1e-12)
+    np.testing.assert_allclose(Q @ (Q.conj().T @ R), R, atol=1e-11)
+
+
 def test_fom_with_tight_tolerance_solves_the_sylvester_equation_exactly():
     """Algorithm 4 with rtol -> 0 reproduces the dense Sylvester solution."""
     m = Model(small(nproj=4, nb=3, ecut=2.0))
