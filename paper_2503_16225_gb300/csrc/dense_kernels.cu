@@ -828,149 +828,295 @@ void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStre
 }
 
 // ----------------------------------------------------------------------------- FOM projected solves
-// One CTA per (m, k): Gaussian elimination with partial pivoting of [A - s_m I | c_m] (q x (q+1),
-// column-major) in the working precision T, then back substitution; y is written (in FP64) to
-// column m of Y (ld ldc).  The pivot search of column c + 1 is fused into the elimination of
-// column c: each thread keeps the largest packed (|w|^2, row) key it produced, a warp shuffle
-// reduces the keys and one shared atomic per warp combines them.  Ties go to the smaller row.
-// Two barriers per column (row swap, elimination) and one per back-substitution row.  The
-// working matrix lives in shared memory when it fits, else in the global work buffer.
-__device__ __forceinline__ unsigned long long piv_key(float v, int row) {
-  return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - (unsigned)row);
+// Shifted solves (A - s_m I) y_m = c_m, m < p, for one k per CTA; A is Hermitian q x q (FP64,
+// column-major, ld lda), arithmetic in the working precision T.
+//   1. Householder reduction A = Q T Q^*, Q = H_0 ... H_{q-2}, H_j = I - tau_j v_j v_j^* acting
+//      on rows j+1.., chosen so that H_j^* maps column j below the diagonal onto beta_j e_1 with
+//      beta_j real: T is real symmetric tridiagonal (diagonal d, off-diagonal e = beta).
+//      Step j: x = tau A22 v, w = x - (tau/2) conj(v^* x) v, A22 <- A22 - v w^* - w v^*.
+//   2. z_m = Q^* c_m (reflectors in order), (T - s_m I) z_m = Q^* c_m by Gaussian elimination
+//      with partial pivoting (one thread per shift), y_m = Q z_m (reflectors in reverse order).
+// One reduction of (16/3) q^3 flops replaces p dense factorisations of (8/3) q^3 each.  The
+// packed lower triangle (column j holds rows j..q-1) stays in shared memory during the
+// reduction when it fits, else in the global work area; the reflectors are kept in the work
+// area for the two transforms.  Every reduction runs in a fixed order (deterministic).
+constexpr int HS_THREADS = 1024;
+
+__host__ __device__ __forceinline__ size_t poff(int j, int q) {  // start of packed column j
+  return (size_t)j * q - (size_t)j * (j - 1) / 2;
 }
-__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
-    v = u > v ? u : v;
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
   }
   return v;
 }
 
+// Sum over the CTA of one value per thread in a fixed order; every thread gets the result.
+template <typename V>
+__device__ __forceinline__ V block_sum(V v, V* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    V t = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = t + red[i];
+    red[32] = t;
+  }
+  __syncthreads();
+  const V r = red[32];
+  __syncthreads();
+  return r;
+}
+
 template <typename T>
-__global__ void k_shifted_solve(int p, int q, const double2* __restrict__ A, int lda, size_t sA,
-                                const double* __restrict__ s, const double2* __restrict__ C, int ldc, size_t sC,
-                                double2* __restrict__ Y, cplx<T>* __restrict__ work, const int* __restrict__ kactive,
-                                int* __restrict__ info, int in_smem) {
+__global__ void __launch_bounds__(HS_THREADS)
+    k_hshift(int p, int q, const double2* __restrict__ A, int lda, size_t sA, const double* __restrict__ sh,
+             const double2* __restrict__ C, int ldc, size_t sC, double2* __restrict__ Y, unsigned char* work,
+             size_t work_stride, const int* __restrict__ kactive, int* __restrict__ info, int pack_in_smem,
+             int z_in_smem) {
   using V = cplx<T>;
-  const int m = blockIdx.x, k = blockIdx.y;
+  const int k = blockIdx.x;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ unsigned long long key[2];
-  V* W = in_smem ? reinterpret_cast<V*>(smem_raw) : work + ((size_t)k * p + m) * (size_t)q * (q + 1);
+  V* tau = reinterpret_cast<V*>(smem_raw);
+  V* red = tau + q;  // [34]
+  T* dg = reinterpret_cast<T*>(red + 34);
+  T* eg = dg + q;
+  unsigned char* area = reinterpret_cast<unsigned char*>(eg + q + 2);
+  area = reinterpret_cast<unsigned char*>(((uintptr_t)area + 15) & ~(uintptr_t)15);
+  // work area of this k: packed reflectors, then z (q x p), then the bands (3 q per shift)
+  unsigned char* wk = work + (size_t)k * work_stride;
+  V* Pg = reinterpret_cast<V*>(wk);
+  V* Zg = Pg + poff(q, q);
+  T* Bg = reinterpret_cast<T*>(Zg + (size_t)q * p);
+  // phase-1 layout of the area: packed matrix (if in shared memory), v, w
+  V* P = pack_in_smem ? reinterpret_cast<V*>(area) : Pg;
+  V* vv = pack_in_smem ? P + poff(q, q) : reinterpret_cast<V*>(area);
+  V* xv = vv + q;
+  __shared__ V s_tau, s_a2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const double2* Ak = A + k * sA;
-  const double sm = s[(size_t)k * p + m];
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    key[0] = 0ull;
-    key[1] = 0ull;
-  }
+  for (int j = 0; j < q; ++j)
+    for (int i = j + tid; i < q; i += blockDim.x) P[poff(j, q) + (i - j)] = to_c<T>(Ak[(size_t)j * lda + i]);
   __syncthreads();
-  unsigned long long mine = 0ull;
-  for (size_t e = threadIdx.x; e < (size_t)q * (q + 1); e += blockDim.x) {
-    const int j = (int)(e / q), i = (int)(e - (size_t)j * q);
-    double2 v;
-    if (j < q) {
-      v = Ak[(size_t)j * lda + i];
-      if (i == j) v.x -= sm;
-    } else {
-      v = C[k * sC + (size_t)m * ldc + i];
+  V zero;
+  zero.x = 0;
+  zero.y = 0;
+  // ---- 1. reduction to tridiagonal form
+  for (int j = 0; j + 1 < q; ++j) {
+    const size_t cj = poff(j, q) - j;  // P(i, j) = P[cj + i]
+    V part = zero;
+    for (int i = j + 2 + tid; i < q; i += blockDim.x) {
+      const V x = P[cj + i];
+      part.x += x.x * x.x + x.y * x.y;
     }
-    const V w = to_c<T>(v);
-    W[e] = w;
-    if (j == 0) {
-      const unsigned long long kk = piv_key((float)(w.x * w.x + w.y * w.y), i);
-      mine = kk > mine ? kk : mine;
+    const T ss = block_sum(part, red).x;
+    if (tid == 0) {
+      const V alpha = P[cj + j + 1];
+      V t = zero;
+      T beta = alpha.x;
+      if (ss > (T)0 || alpha.y != (T)0) {
+        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + ss), alpha.x);
+        t.x = (beta - alpha.x) / beta;
+        t.y = -alpha.y / beta;
+        // scale = 1 / (alpha - beta)
+        const V am = mk<V>(alpha.x - beta, alpha.y);
+        const T den = am.x * am.x + am.y * am.y;
+        s_a2 = mk<V>(am.x / den, -am.y / den);
+      } else {
+        s_a2 = mk<V>((T)1, (T)0);
+      }
+      s_tau = t;
+      tau[j] = t;
+      eg[j] = beta;
+      dg[j] = P[cj + j].x;
     }
-  }
-  mine = warp_max_key(mine);
-  if (lane == 0 && mine) atomicMax(&key[0], mine);
-  __syncthreads();
-  for (int c = 0; c < q; ++c) {
-    const unsigned long long kc = key[c & 1];
-    int r = (int)(0xffffffffu - (unsigned)(kc & 0xffffffffull));
-    r = min(max(r, c), q - 1);  // rows c..q-1 each posted a key, so r is in range; keep it there
-    if (threadIdx.x == 0) {
-      key[(c + 1) & 1] = 0ull;
-      if ((kc >> 32) == 0ull && info) info[k * p + m] = c + 1;
+    __syncthreads();
+    const V t = s_tau, scale = s_a2;
+    for (int i = j + 1 + tid; i < q; i += blockDim.x) {
+      const V v = (i == j + 1) ? mk<V>((T)1, (T)0) : cmul(P[cj + i], scale);
+      vv[i] = v;
+      P[cj + i] = v;
     }
-    if (r != c) {
-      for (int j = c + threadIdx.x; j <= q; j += blockDim.x) {
-        const V t = W[(size_t)j * q + c];
-        W[(size_t)j * q + c] = W[(size_t)j * q + r];
-        W[(size_t)j * q + r] = t;
+    __syncthreads();
+    if (t.x == (T)0 && t.y == (T)0) continue;
+    // x = A22 v: the lower part by rows (thread per row), the upper part by columns (warp per column)
+    for (int i = j + 1 + tid; i < q; i += blockDim.x) {
+      V acc = zero;
+      for (int l = j + 1; l <= i; ++l) acc = acc + cmul(P[poff(l, q) + (i - l)], vv[l]);
+      xv[i] = acc;
+    }
+    __syncthreads();
+    for (int i = j + 1 + warp; i < q; i += nw) {
+      const size_t ci = poff(i, q) - i;
+      V acc = zero;
+      for (int l = i + 1 + lane; l < q; l += 32) acc = acc + cmulc(P[ci + l], vv[l]);
+      acc = warp_sum(acc);
+      if (lane == 0) xv[i] = cmul(t, xv[i] + acc);  // x = tau A22 v
+    }
+    __syncthreads();
+    V dp = zero;
+    for (int i = j + 1 + tid; i < q; i += blockDim.x) dp = dp + cmulc(vv[i], xv[i]);
+    const V dot = block_sum(dp, red);  // v^* x
+    if (tid == 0) s_a2 = cscale(cmul(t, cconj(dot)), (T)-0.5);
+    __syncthreads();
+    const V a2 = s_a2;
+    for (int i = j + 1 + tid; i < q; i += blockDim.x) xv[i] = xv[i] + cmul(a2, vv[i]);  // w
+    __syncthreads();
+    // A22 -= v w^* + w v^* on the lower triangle: warp per column, lanes down the rows
+    for (int l = j + 1 + warp; l < q; l += nw) {
+      const size_t cl = poff(l, q) - l;
+      const V vl = vv[l], wl = xv[l];
+      for (int i = l + lane; i < q; i += 32) {
+        const V d = cmul(vv[i], cconj(wl)) + cmul(xv[i], cconj(vl));
+        P[cl + i] = P[cl + i] - d;
       }
     }
     __syncthreads();
-    const V d = W[(size_t)c * q + c];
-    const T dd = d.x * d.x + d.y * d.y;
-    V dinv;
-    dinv.x = dd > (T)0 ? d.x / dd : (T)0;
-    dinv.y = dd > (T)0 ? -d.y / dd : (T)0;
-    const int rows = q - c - 1;
-    mine = 0ull;
-    for (size_t e = threadIdx.x; e < (size_t)rows * (q - c); e += blockDim.x) {
-      const int jj = (int)(e / rows), ii = (int)(e - (size_t)jj * rows);
-      const int i = c + 1 + ii, j = c + 1 + jj;
-      const V f = cmul(W[(size_t)c * q + i], dinv);
-      const V nw = W[(size_t)j * q + i] - cmul(f, W[(size_t)j * q + c]);
-      W[(size_t)j * q + i] = nw;
-      if (jj == 0) {
-        const unsigned long long kk = piv_key((float)(nw.x * nw.x + nw.y * nw.y), i);
-        mine = kk > mine ? kk : mine;
-      }
-    }
-    mine = warp_max_key(mine);
-    if (lane == 0 && mine) atomicMax(&key[(c + 1) & 1], mine);
-    __syncthreads();
   }
-  // back substitution on the upper triangle, column oriented; every thread computes y_c itself
-  // (nobody writes rhs[c] in step c), then updates its share of rhs[0..c)
-  V* rhs = W + (size_t)q * q;
-  for (int c = q - 1; c >= 0; --c) {
-    const V d = W[(size_t)c * q + c];
-    const T dd = d.x * d.x + d.y * d.y;
-    V yc;
-    if (dd > (T)0) {
-      V di;
-      di.x = d.x / dd;
-      di.y = -d.y / dd;
-      yc = cmul(rhs[c], di);
-    } else {
-      yc.x = 0;
-      yc.y = 0;
-    }
-    for (int i = threadIdx.x; i < c; i += blockDim.x) rhs[i] = rhs[i] - cmul(W[(size_t)c * q + i], yc);
-    __syncthreads();
-    if (threadIdx.x == 0) rhs[c] = yc;
+  if (tid == 0) {
+    dg[q - 1] = P[poff(q - 1, q)].x;
+    eg[q - 1] = 0;
+  }
+  if (pack_in_smem)
+    for (size_t e = tid; e < poff(q, q); e += blockDim.x) Pg[e] = P[e];
+  __syncthreads();
+  // ---- 2. z = Q^* c per shift (warp per shift, reflectors from the work area)
+  V* Z = z_in_smem ? reinterpret_cast<V*>(area) : Zg;
+  T* Bd = z_in_smem ? reinterpret_cast<T*>(Z + (size_t)q * p) : Bg;
+  for (int e = tid; e < q * p; e += blockDim.x) {
+    const int m = e / q, i = e - m * q;
+    Z[e] = to_c<T>(C[k * sC + (size_t)m * ldc + i]);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < q; i += blockDim.x) Y[k * sC + (size_t)m * ldc + i] = to_d(rhs[i]);
+  for (int m = warp; m < p; m += nw) {
+    V* z = Z + (size_t)m * q;
+    for (int j = 0; j + 1 < q; ++j) {
+      const V tj = tau[j];
+      if (tj.x == (T)0 && tj.y == (T)0) continue;
+      const V* v = Pg + poff(j, q) - j;
+      V acc = zero;
+      for (int i = j + 1 + lane; i < q; i += 32) acc = acc + cmulc(v[i], z[i]);
+      const V f = cmul(cconj(tj), warp_sum(acc));
+      __syncwarp();
+      for (int i = j + 1 + lane; i < q; i += 32) z[i] = z[i] - cmul(v[i], f);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // ---- 3. (T - s_m I) z = z by Gaussian elimination with partial pivoting, thread per shift
+  for (int m = tid; m < p; m += blockDim.x) {
+    V* b = Z + (size_t)m * q;
+    T* dd = Bd + (size_t)m * 3 * q;
+    T* du = dd + q;
+    T* du2 = du + q;
+    const T sm = (T)sh[(size_t)k * p + m];
+    for (int i = 0; i < q; ++i) {
+      dd[i] = dg[i] - sm;
+      du[i] = eg[i];
+      du2[i] = 0;
+    }
+    int bad = 0;
+    for (int i = 0; i + 1 < q; ++i) {
+      const T sub = eg[i];
+      if (fabs(dd[i]) >= fabs(sub)) {
+        if (dd[i] == (T)0) {
+          bad = 1;
+          continue;
+        }
+        const T f = sub / dd[i];
+        dd[i + 1] -= f * du[i];
+        b[i + 1] = b[i + 1] - cscale(b[i], f);
+        du2[i] = 0;
+      } else {
+        const T f = dd[i] / sub;
+        dd[i] = sub;
+        const T tmp = dd[i + 1];
+        dd[i + 1] = du[i] - f * tmp;
+        if (i + 2 < q) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du2[i];
+        }
+        du[i] = tmp;
+        const V bi = b[i];
+        b[i] = b[i + 1];
+        b[i + 1] = bi - cscale(b[i], f);
+      }
+    }
+    if (dd[q - 1] == (T)0) bad = 1;
+    if (bad) {
+      if (info) info[k * p + m] = 1;
+      for (int i = 0; i < q; ++i) b[i] = zero;
+      continue;
+    }
+    b[q - 1] = cscale(b[q - 1], (T)1 / dd[q - 1]);
+    if (q > 1) b[q - 2] = cscale(b[q - 2] - cscale(b[q - 1], du[q - 2]), (T)1 / dd[q - 2]);
+    for (int i = q - 3; i >= 0; --i)
+      b[i] = cscale(b[i] - cscale(b[i + 1], du[i]) - cscale(b[i + 2], du2[i]), (T)1 / dd[i]);
+  }
+  __syncthreads();
+  // ---- 4. y = Q z (reflectors in reverse order), written in FP64
+  for (int m = warp; m < p; m += nw) {
+    V* z = Z + (size_t)m * q;
+    for (int j = q - 2; j >= 0; --j) {
+      const V tj = tau[j];
+      if (tj.x == (T)0 && tj.y == (T)0) continue;
+      const V* v = Pg + poff(j, q) - j;
+      V acc = zero;
+      for (int i = j + 1 + lane; i < q; i += 32) acc = acc + cmulc(v[i], z[i]);
+      const V f = cmul(tj, warp_sum(acc));
+      __syncwarp();
+      for (int i = j + 1 + lane; i < q; i += 32) z[i] = z[i] - cmul(v[i], f);
+      __syncwarp();
+    }
+    for (int i = lane; i < q; i += 32) Y[k * sC + (size_t)m * ldc + i] = to_d(z[i]);
+  }
+}
+
+// Work bytes per k of the shifted solve.
+static size_t hs_work_stride(int p, int q, size_t es, size_t ts) {
+  const size_t b = poff(q, q) * es + (size_t)q * p * es + (size_t)3 * p * q * ts;
+  return (b + 255) & ~(size_t)255;
 }
 
 size_t fom_shifted_work(int K, int p, int q, int prec) {
-  return (size_t)K * p * q * (q + 1) * (prec ? sizeof(float2) : sizeof(double2));
+  const size_t es = prec ? sizeof(float2) : sizeof(double2), ts = prec ? sizeof(float) : sizeof(double);
+  return (size_t)K * hs_work_stride(p, q, es, ts);
+}
+
+template <typename T>
+static void hshift_launch(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s,
+                          const double2* C, int ldc, size_t sC, double2* Y, void* work, const int* kactive,
+                          int* info, cudaStream_t st) {
+  using V = cplx<T>;
+  constexpr size_t LIMIT = 227 * 1024;
+  const size_t persist = (size_t)q * sizeof(V) + 34 * sizeof(V) + (size_t)(2 * q + 2) * sizeof(T) + 16;
+  const size_t pack = poff(q, q) * sizeof(V) + 2 * (size_t)q * sizeof(V);
+  const size_t vecs = 2 * (size_t)q * sizeof(V);
+  const size_t zb = (size_t)q * p * sizeof(V) + (size_t)3 * p * q * sizeof(T);
+  const int pack_in = persist + pack <= LIMIT;
+  const int z_in = persist + zb <= LIMIT;
+  const size_t sm = persist + std::max(pack_in ? pack : vecs, z_in ? zb : (size_t)0);
+  ensure_smem((const void*)k_hshift<T>, sm);
+  k_hshift<T><<<K, HS_THREADS, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (unsigned char*)work,
+                                         hs_work_stride(p, q, sizeof(V), sizeof(T)), kactive, info, pack_in, z_in);
+  count_launch();
 }
 
 void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s, const double2* C,
                        int ldc, size_t sC, double2* Y, void* work, const int* kactive, int* info, int prec,
                        cudaStream_t st) {
-  dim3 g(p, K);
-  const size_t es = prec ? sizeof(float2) : sizeof(double2);
-  const size_t need = (size_t)q * (q + 1) * es;
-  const bool in_smem = need <= 200 * 1024;
-  const size_t sm = in_smem ? need : 0;
-  const int threads = q <= 64 ? 128 : 256;
-  if (prec) {
-    if (in_smem) ensure_smem((const void*)k_shifted_solve<float>, sm);
-    k_shifted_solve<float><<<g, threads, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (float2*)work, kactive, info,
-                                                   in_smem ? 1 : 0);
-  } else {
-    if (in_smem) ensure_smem((const void*)k_shifted_solve<double>, sm);
-    k_shifted_solve<double><<<g, threads, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (double2*)work, kactive,
-                                                    info, in_smem ? 1 : 0);
-  }
-  count_launch();
+  if (q <= 0) return;
+  if (prec)
+    hshift_launch<float>(K, p, q, A, lda, sA, s, C, ldc, sC, Y, work, kactive, info, st);
+  else
+    hshift_launch<double>(K, p, q, A, lda, sA, s, C, ldc, sC, Y, work, kactive, info, st);
 }
 
 __global__ void k_mirror(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ kactive) {
@@ -989,20 +1135,27 @@ void fom_mirror(int K, int q0, int p, double2* A, int lda, size_t sA, const int*
   }
 }
 
-__global__ void k_pad_diag(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ nzero, double big) {
+// Diagonal of the rows that belong to dropped (zero) Krylov columns: those rows and columns of
+// A and of the projected right-hand side are zero, so any diagonal value d other than every
+// shift gives them y = 0.  d = 1 + max_m |s_m| keeps A - s_m I nonsingular there and of the
+// scale of the shifts (a huge d would overflow the FP32 Householder norms).
+__global__ void k_pad_diag(int q0, int p, double2* A, int lda, size_t sA, const int* __restrict__ nzero,
+                           const double* __restrict__ shifts) {
   const int k = blockIdx.x;
   double2* Ak = A + k * sA;
   const int nz = nzero[k];
-  for (int i = threadIdx.x; i < nz && i < p; i += blockDim.x)
-    Ak[(size_t)(q0 + i) * lda + q0 + i] = make_double2(big, 0.0);
+  double d = 0.0;
+  for (int m = 0; m < p; ++m) d = fmax(d, fabs(shifts[(size_t)k * p + m]));
+  d += 1.0;
+  for (int i = threadIdx.x; i < nz && i < p; i += blockDim.x) Ak[(size_t)(q0 + i) * lda + q0 + i] = make_double2(d, 0.0);
 }
-void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, double big, cudaStream_t st) {
-  k_pad_diag<<<K, 64, 0, st>>>(q0, p, A, lda, sA, nzero, big);
+void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, const double* shifts,
+                  cudaStream_t st) {
+  k_pad_diag<<<K, 64, 0, st>>>(q0, p, A, lda, sA, nzero, shifts);
   count_launch();
 }
 
 // ----------------------------------------------------------------------------- small helpers
-// M[:, i] = U[:, i] w_i^{-1/2} when w_i > tol * lref[k] (and lref[k] > 0), else 0; nzero[k] = dropped count.
 // Rank-revealing orthonormalisation factor of a block from its Gram matrix G = R^* R (p x p,
 // FP64, one CTA per k): Cholesky with diagonal pivoting, i.e. QR with column pivoting of R
 // written on G.  Step j takes the largest remaining Schur-complement diagonal (first position

@@ -504,7 +504,7 @@ static eacg_status fom_reserve(eacg_system* s, int qneed) {
   s->fYt = nYt;
   s->fYf = nYf;
   s->qcap = qc;
-  const size_t fw = (size_t)K * p * qc * (qc + 1);
+  const size_t fw = (fom_shifted_work(K, p, qc, 0) + sizeof(double2) - 1) / sizeof(double2);
   if (fw > s->fwork_elems) {
     dfree(s, s->fwork);
     s->fwork = nullptr;
@@ -900,7 +900,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     }
     O::cn(K, nm, p, p, Vn, sV, nm, Wn, sV, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, s->d_kactive, s->st);
     small_put_herm_block(K, p, s->sm1, s->fA, s->qcap, sA, q0, s->st);
-    fom_pad_diag(K, q0, p, s->fA, s->qcap, sA, s->d_nzero, 1e30, s->st);
+    fom_pad_diag(K, q0, p, s->fA, s->qcap, sA, s->d_nzero, s->eval, s->st);
     O::cn(K, nm, p, p, Vn, sV, nm, C, sb, nm, s->fC + q0, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work,
           s->d_kactive, s->st);
     CKL(s);
@@ -925,8 +925,10 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     // Y = solve(A Y - Y Sigma = C_j) via C~ = C Q, (A - s_m) y~_m = c~_m, Y = Y~ Q^H
     dense_gemm_nn(K, q, p, p, s->fC, sC, s->qcap, s->sigv, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
                   s->d_kactive, s->st);
-    PROF_RUN(P_FOMSOLVE + (f32 ? P_F32 : 0), (double)K * p * q * (q + 1) * (f32 ? 8.0 : 16.0) * 2,
-             (double)K * p * (8.0 / 3.0) * q * q * q, 0,
+    // algorithmic: A, C read and Y written once per k; (16/3) q^3 for the Householder reduction
+    // plus two reflector transforms of 8 q^2 per shift
+    PROF_RUN(P_FOMSOLVE + (f32 ? P_F32 : 0), (double)K * ((double)q * q + 2.0 * q * p) * 16.0,
+             (double)K * ((16.0 / 3.0) * q * q * q + 16.0 * q * q * p), 0,
              fom_shifted_solve(K, p, q, s->fA, s->qcap, sA, s->eval, s->fYt, s->qcap, sC, s->fY, s->fwork,
                                s->d_kactive, nullptr, f32 ? 1 : 0, s->st));
     PROF_RUN(P_FOM_RES, 2.0 * K * q * nm * sizeof(V) + 2.0 * s->blk * sizeof(V), 16.0 * K * nm * q * p, 0, {

@@ -125,18 +125,20 @@ void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStre
 void dense_kin_energy(int K, int p, int n_max, const double* kin, const double2* phi, const double* kw, double occ,
                       double* partials, cudaStream_t st);
 
-// ---- fom_kernels.cu
-// Solve (A[k] - s[k][m] I) y = c for every (k, m): A q x q (lda), c/y columns of q x p (ldc).
-// prec 0: FP64 elimination, 1: FP32 elimination (FP64 in and out).  work: fom_shifted_work bytes
-// (used only when q x (q+1) does not fit in shared memory).
+// ---- FOM projected solves (dense_kernels.cu)
+// Solve (A[k] - s[k][m] I) y = c for every (k, m): A Hermitian q x q (lda), c/y columns of q x p
+// (ldc), by one Householder tridiagonalisation per k and p tridiagonal solves.
+// prec 0: FP64 arithmetic, 1: FP32 arithmetic (FP64 in and out).  work: fom_shifted_work bytes
+// (reflectors, right-hand sides and tridiagonal factors of every k).  info[k * p + m] = 1 when a
+// shifted tridiagonal matrix is exactly singular (that y is set to zero); may be null.
 size_t fom_shifted_work(int K, int p, int q, int prec);
 void fom_shifted_solve(int K, int p, int q, const double2* A, int lda, size_t sA, const double* s,
                        const double2* C, int ldc, size_t sC, double2* Y, void* work, const int* kactive,
                        int* info, int prec, cudaStream_t st);
 // A[k][i][j] for i in [q0, q0 + p) and j < q0: conj of A[k][j][i] (Hermitian mirror).
 void fom_mirror(int K, int q0, int p, double2* A, int lda, size_t sA, const int* kactive, cudaStream_t st);
-// Rows of A with zero new columns: A[k][q0 + i][q0 + i] = big for i < nzero[k].
-void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, double big,
+// Rows of A with zero new columns: A[k][q0 + i][q0 + i] = 1 + max_m |shifts[k][m]| for i < nzero[k].
+void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const int* nzero, const double* shifts,
                   cudaStream_t st);
 
 }  // namespace eacg
