@@ -45,6 +45,9 @@ def parse():
                     help="serve a stream of this many synthetic crystals instead (Poisson arrivals)")
     ap.add_argument("--rate", type=float, default=2.0, help="arrival rate of the serving stream (requests/s)")
     ap.add_argument("--resident", type=int, default=8, help="maximum resident requests while serving")
+    ap.add_argument("--op", default="solve", choices=["solve", "apply_h", "density", "ea_gradient"],
+                    help="apply_h / density / ea_gradient: time a few calls of one operation on the "
+                         "workload's start point instead of solves (short runs under a profiler)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the host-buffer (e2e) solves and the CPU baseline (short runs under a profiler)")
     return ap.parse_args()
@@ -360,12 +363,52 @@ def hpsi_bytes_per_band(sysm, prec_bytes=8):
     return 2 * sysm.n_max * 16 + 4 * sysm.N * sysm.ncols * 2 * prec_bytes
 
 
+def run_op(args):
+    """A few calls of one hot-path operation (H application, density or energy-adaptive
+    gradient) on the workload's start point, timed with CUDA events: a short program for
+    profiler captures."""
+    import torch
+    import synth
+    import paper_2503_16225_gb300 as E
+
+    cfg = workload(args.workload)
+    prec = 1 if args.precision == "mixed" else 0
+    sysm = E.System(cfg, E.eacg_default_params(precision=prec))
+    raw = synth.raw_coefficients(cfg["seed"], sysm.nk, sysm.p, sysm.n_max)
+    E.eacg_set_psi(sysm.h, torch.from_numpy(raw).cuda())
+    phi = sysm.block()
+    E.eacg_get_psi(sysm.h, phi)
+    E.eacg_density(sysm.h, phi, None, 0)
+    out = sysm.block()
+    if args.op == "apply_h":
+        call = lambda: E.eacg_apply_H(sysm.h, phi, out, prec)  # noqa: E731
+    elif args.op == "density":
+        call = lambda: E.eacg_density(sysm.h, phi, None, prec)  # noqa: E731
+    else:
+        call = lambda: E.eacg_ea_gradient(sysm.h, phi, out, sysm.K, prec)  # noqa: E731
+    for _ in range(args.warmup):
+        call()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    e1.synchronize()
+    print(json.dumps({"op": args.op, "workload": cfg["name"], "precision": args.precision, "calls": args.steps,
+                      "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps), "bands": sysm.K * sysm.p}))
+    sysm.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.serve > 0:
         run_serve(args)
+    elif args.op != "solve":
+        run_op(args)
     else:
         run_gpu(args)
 
