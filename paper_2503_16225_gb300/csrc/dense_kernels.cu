@@ -22,6 +22,36 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // 
 }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// FP64 reciprocal square root and reciprocal by Newton-Raphson from an FP32 seed: two steps
+// take the seed's ~1e-7 relative error to FP64 rounding (quadratic convergence), using only
+// multiply-adds, which GB300 executes far faster than its FP64 divide and square-root
+// sequences.  The argument (positive, normal) is first scaled by an exact power of two into
+// [1, 4) so that the FP32 seed never under- or overflows.
+//   y <- y (3 - x y^2) / 2          for 1 / sqrt(x)
+//   y <- y (2 - x y)                for 1 / x
+__device__ __forceinline__ double pow2(int e) {  // 2^e for -1022 <= e <= 1023
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+__device__ __forceinline__ int exponent_of(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int half = exponent_of(x) >> 1;  // floor(e / 2)
+  const double xs = x * pow2(-2 * half);  // in [1, 4)
+  double y = (double)rsqrtf((float)xs);
+  y = y * fma(-0.5 * xs * y, y, 1.5);
+  y = y * fma(-0.5 * xs * y, y, 1.5);
+  return y * pow2(-half);
+}
+__device__ __forceinline__ double rcp_nr(double x) {
+  const int e = exponent_of(x);
+  const double xs = x * pow2(-e);  // in [1, 2)
+  double y = (double)(1.0f / (float)xs);
+  y = y * fma(-xs, y, 2.0);
+  y = y * fma(-xs, y, 2.0);
+  return y * pow2(-e);
+}
+
 // ----------------------------------------------------------------------------- A^H B
 // Templated on the block precision T (double or float): A and B are cplx<T>, the products
 // are accumulated in T within a chunk of rows, the chunk partials and the result are FP64.
@@ -280,193 +310,199 @@ void dense_tpa32(int K, int p, int n_max, const double* kin, const double* alpha
 }
 
 // ----------------------------------------------------------------------------- Hermitian eig
-// One p x p Hermitian matrix per CTA (p <= 64), FP64.  Householder reduction to a real
-// symmetric tridiagonal T = Q^* A Q (the reflector of column j maps it onto a real multiple of
-// e_{j+1}), Q formed explicitly, then implicit QL iterations with a Wilkinson shift on T whose
-// plane rotations are accumulated into Z = Q, so A = Z diag(d) Z^*.  The sequential parts
-// (reflector coefficients, the rotation chase) run on one thread, the O(p^2) updates on all.
-// Eigenvalues ascending (ties by index), eigenvectors as columns.
-constexpr int HEIG_THREADS = 64;
-__global__ void __launch_bounds__(HEIG_THREADS)
-    k_heig(int p, const double2* __restrict__ Ag, size_t sA, double* __restrict__ w, double2* __restrict__ Vg,
-           const int* __restrict__ kactive) {
+// Parallel cyclic Jacobi (round-robin pairs) on one p x p Hermitian matrix per CTA, FP64.
+// The rotation parameters use multiply-add refinements of FP32 reciprocal / rsqrt seeds in
+// FP64 (no FP64 divide or square root).  Converged when the off-diagonal norm is below
+// 1e-14 of the matrix norm.
+template <typename T>
+struct JacobiMath;
+template <>
+struct JacobiMath<double> {
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt_nr(x); }
+  static __device__ __forceinline__ double rcp(double x) { return rcp_nr(x); }
+  static constexpr double tol2 = 1e-28, neg = 1e-16, tiny = 1e-280;
+};
+template <typename T>
+__global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double* __restrict__ w,
+                       double2* __restrict__ Vg, const int* __restrict__ kactive) {
+  using V2 = cplx<T>;
+  using M = JacobiMath<T>;
   const int k = blockIdx.x;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ld = p + 1;  // odd pitch: column walks by different threads avoid bank conflicts
-  double2* A = reinterpret_cast<double2*>(smem_raw);  // A(i, j) = A[j * ld + i]
-  double2* Z = A + (size_t)p * ld;
-  __shared__ double d[64], e[64], rc[64], rs[64];
-  __shared__ double2 tau[64], vv[64], xv[64];
-  __shared__ double2 s_scale, s_a2;
-  __shared__ int s_m, s_lo, s_go, s_iters;
-  const int tid = threadIdx.x;
+  const int pe = p + (p & 1);  // even number of slots (a dummy index when p is odd)
+  V2* A = reinterpret_cast<V2*>(smem_raw);
+  V2* V = A + p * p;
+  T* rot = reinterpret_cast<T*>(V + p * p);  // [pe/2][4]: c, s, cos phi, sin phi
+  T* red = rot + 2 * pe;                     // [2 + 2 * warps]
   const double2* Ak = Ag + k * sA;
-  for (int e2 = tid; e2 < p * p; e2 += blockDim.x) {
-    const int j = e2 / p, i = e2 - j * p;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int j = e / p, i = e - j * p;
+    // symmetrise exactly while loading: upper from (A_ij + conj A_ji) / 2
     const double2 a = Ak[(size_t)j * p + i], b = Ak[(size_t)i * p + j];
-    A[j * ld + i] = make_double2(0.5 * (a.x + b.x), i == j ? 0.0 : 0.5 * (a.y - b.y));
+    double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    if (i == j) h.y = 0.0;
+    A[e] = to_c<T>(h);
+    V[e].x = (T)(i == j ? 1 : 0);
+    V[e].y = (T)0;
   }
   __syncthreads();
-  // ---- Householder reduction
-  for (int j = 0; j + 1 < p; ++j) {
-    if (tid == 0) {
-      const double2 alpha = A[j * ld + j + 1];
-      double ss = 0.0;
-      for (int i = j + 2; i < p; ++i) ss += A[j * ld + i].x * A[j * ld + i].x + A[j * ld + i].y * A[j * ld + i].y;
-      double2 t = make_double2(0.0, 0.0);
-      double beta = alpha.x;
-      double2 scale = make_double2(1.0, 0.0);
-      if (ss > 0.0 || alpha.y != 0.0) {
-        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + ss), alpha.x);
-        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-        const double2 am = make_double2(alpha.x - beta, alpha.y);
-        const double den = am.x * am.x + am.y * am.y;
-        scale = make_double2(am.x / den, -am.y / den);
+  const int npair = pe / 2;
+  // round-robin pairing (circle method): slot 0 fixed, slots 1..pe-1 rotate by one per round
+  auto slot = [pe](int pos, int round) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (pe - 1); };
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    {
+      // off-diagonal and diagonal squared norms: fixed per-thread strides, then a fixed
+      // shuffle tree per warp and a fixed warp order (deterministic)
+      T off = 0, dia = 0;
+      for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int j = e / p, i = e - j * p;
+        const T a2 = A[e].x * A[e].x + A[e].y * A[e].y;
+        if (i == j)
+          dia += a2;
+        else
+          off += a2;
       }
-      d[j] = A[j * ld + j].x;
-      e[j] = beta;
-      tau[j] = t;
-      s_scale = scale;
-    }
-    __syncthreads();
-    const double2 t = tau[j], scale = s_scale;
-    for (int i = j + 1 + tid; i < p; i += blockDim.x) {
-      const double2 v = (i == j + 1) ? make_double2(1.0, 0.0) : cmul(A[j * ld + i], scale);
-      vv[i] = v;
-      A[j * ld + i] = v;
-    }
-    __syncthreads();
-    if (t.x == 0.0 && t.y == 0.0) continue;
-    for (int i = j + 1 + tid; i < p; i += blockDim.x) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int l = j + 1; l < p; ++l) acc = cfma(A[l * ld + i], vv[l], acc);
-      xv[i] = cmul(t, acc);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double2 dot = make_double2(0.0, 0.0);
-      for (int i = j + 1; i < p; ++i) dot = cfmac(vv[i], xv[i], dot);
-      s_a2 = cscale(cmul(t, cconj(dot)), -0.5);
-    }
-    __syncthreads();
-    const double2 a2 = s_a2;
-    for (int i = j + 1 + tid; i < p; i += blockDim.x) xv[i] = cfma(a2, vv[i], xv[i]);
-    __syncthreads();
-    for (int i = j + 1 + tid; i < p; i += blockDim.x) {
-      const double2 vi = vv[i], wi = xv[i];
-      for (int l = j + 1; l < p; ++l) {
-        const double2 dl = cmul(vi, cconj(xv[l])) + cmul(wi, cconj(vv[l]));
-        A[l * ld + i] = A[l * ld + i] - dl;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_down_sync(0xffffffffu, off, o);
+        dia += __shfl_down_sync(0xffffffffu, dia, o);
       }
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    d[p - 1] = A[(p - 1) * ld + p - 1].x;
-    e[p - 1] = 0.0;
-  }
-  // ---- Q = H_0 ... H_{p-2}, accumulated backwards into Z
-  for (int e2 = tid; e2 < p * p; e2 += blockDim.x) {
-    const int j = e2 / p, i = e2 - j * p;
-    Z[j * ld + i] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  for (int j = p - 2; j >= 0; --j) {
-    const double2 t = tau[j];
-    if (t.x == 0.0 && t.y == 0.0) continue;
-    for (int c = j + 1 + tid; c < p; c += blockDim.x) {
-      double2 dot = make_double2(0.0, 0.0);
-      for (int i = j + 1; i < p; ++i) dot = cfmac(A[j * ld + i], Z[c * ld + i], dot);
-      const double2 f = cmul(t, dot);
-      for (int i = j + 1; i < p; ++i) Z[c * ld + i] = Z[c * ld + i] - cmul(A[j * ld + i], f);
-    }
-    __syncthreads();
-  }
-  // ---- implicit QL with a Wilkinson shift; thread 0 chases, all threads rotate rows of Z
-  if (tid == 0) s_iters = 0;
-  __syncthreads();
-  int l = 0;
-  while (l < p) {
-    if (tid == 0) {
-      int m = l;
-      for (; m + 1 < p; ++m)
-        if (fabs(e[m]) <= 2.220446049250313e-16 * (fabs(d[m]) + fabs(d[m + 1]))) break;
-      if (m == l || s_iters >= 60) {
-        s_go = 0;
-        s_iters = 0;
-      } else {
-        ++s_iters;
-        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-        double r = hypot(g, 1.0);
-        g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-        double sn = 1.0, cs = 1.0, pp = 0.0;
-        int i = m - 1;
-        bool under = false;
-        for (; i >= l; --i) {
-          const double f = sn * e[i], bb = cs * e[i];
-          r = hypot(f, g);
-          e[i + 1] = r;
-          if (r == 0.0) {
-            d[i + 1] -= pp;
-            e[m] = 0.0;
-            under = true;
-            break;
-          }
-          sn = f / r;
-          cs = g / r;
-          g = d[i + 1] - pp;
-          r = (d[i] - g) * sn + 2.0 * cs * bb;
-          pp = sn * r;
-          d[i + 1] = g + pp;
-          g = cs * r - bb;
-          rc[i] = cs;
-          rs[i] = sn;
-        }
-        if (!under) {
-          d[l] -= pp;
-          e[l] = g;
-          e[m] = 0.0;
-        }
-        s_m = m;
-        s_lo = under ? i + 1 : l;
-        s_go = 1;
+      if ((threadIdx.x & 31) == 0) {
+        red[2 + 2 * (threadIdx.x >> 5)] = off;
+        red[3 + 2 * (threadIdx.x >> 5)] = dia;
       }
-    }
-    __syncthreads();
-    if (!s_go) {
-      ++l;
       __syncthreads();
-      continue;
-    }
-    const int m = s_m, lo = s_lo;
-    for (int r = tid; r < p; r += blockDim.x) {
-      for (int i = m - 1; i >= lo; --i) {
-        const double c = rc[i], sn = rs[i];
-        const double2 zi = Z[i * ld + r], zj = Z[(i + 1) * ld + r];
-        Z[(i + 1) * ld + r] = make_double2(sn * zi.x + c * zj.x, sn * zi.y + c * zj.y);
-        Z[i * ld + r] = make_double2(c * zi.x - sn * zj.x, c * zi.y - sn * zj.y);
+      if (threadIdx.x == 0) {
+        T so = 0, sd = 0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+          so += red[2 + 2 * wi];
+          sd += red[3 + 2 * wi];
+        }
+        red[0] = so;
+        red[1] = sd;
       }
     }
     __syncthreads();
+    const T fro2 = red[0] + red[1];
+    const bool done = !(red[0] > M::tol2 * fro2);
+    __syncthreads();
+    if (done) break;
+    const T negligible = M::neg * sqrt(fro2) / p;
+    for (int round = 0; round < pe - 1; ++round) {
+      // rotation parameters for each pair
+      for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+        int i = slot(t, round), j = slot(pe - 1 - t, round);
+        if (i > j) {
+          const int q = i;
+          i = j;
+          j = q;
+        }
+        T c = 1, s = 0, cf = 1, sf = 0;
+        if (j < p) {
+          const V2 b = A[j * p + i];
+          const T r2 = b.x * b.x + b.y * b.y;
+          if (r2 > M::tiny && r2 > negligible * negligible) {
+            const T a = A[i * p + i].x, d = A[j * p + j].x;
+            const T ir = M::rsq(r2);                       // 1 / |b|
+            const T zeta = (T)0.5 * (d - a) * ir;
+            const T h = (T)1 + zeta * zeta;
+            const T den = fabs(zeta) + h * M::rsq(h);      // |zeta| + sqrt(1 + zeta^2)
+            const T tt = (zeta >= 0 ? (T)1 : (T)-1) * M::rcp(den);
+            c = M::rsq((T)1 + tt * tt);
+            s = tt * c;
+            cf = b.x * ir;  // e^{i phi} = b / |b|
+            sf = b.y * ir;
+          }
+        }
+        rot[4 * t + 0] = c;
+        rot[4 * t + 1] = s;
+        rot[4 * t + 2] = cf;
+        rot[4 * t + 3] = sf;
+      }
+      __syncthreads();
+      // columns: (A_ki, A_kj) <- (c A_ki - s e^{-i phi} A_kj, s A_ki + c e^{-i phi} A_kj); same for V
+      for (int e = threadIdx.x; e < npair * p; e += blockDim.x) {
+        const int t = e / p, r = e - t * p;
+        int i = slot(t, round), j = slot(pe - 1 - t, round);
+        if (i > j) {
+          const int q = i;
+          i = j;
+          j = q;
+        }
+        if (j >= p) continue;
+        const T c = rot[4 * t], s = rot[4 * t + 1];
+        V2 em;
+        em.x = rot[4 * t + 2];
+        em.y = -rot[4 * t + 3];  // e^{-i phi}
+        {
+          const V2 ai = A[i * p + r], aj = cmul(em, A[j * p + r]);
+          A[i * p + r] = cscale(ai, c) - cscale(aj, s);
+          A[j * p + r] = cscale(ai, s) + cscale(aj, c);
+        }
+        {
+          const V2 vi = V[i * p + r], vj = cmul(em, V[j * p + r]);
+          V[i * p + r] = cscale(vi, c) - cscale(vj, s);
+          V[j * p + r] = cscale(vi, s) + cscale(vj, c);
+        }
+      }
+      __syncthreads();
+      // rows: (A_ik, A_jk) <- (c A_ik - s e^{i phi} A_jk, s A_ik + c e^{i phi} A_jk); the annihilated
+      // pair is set to exactly zero and the diagonal kept real
+      for (int e = threadIdx.x; e < npair * p; e += blockDim.x) {
+        const int t = e / p, col = e - t * p;
+        int i = slot(t, round), j = slot(pe - 1 - t, round);
+        if (i > j) {
+          const int q = i;
+          i = j;
+          j = q;
+        }
+        if (j >= p) continue;
+        const T c = rot[4 * t], s = rot[4 * t + 1];
+        V2 ep;
+        ep.x = rot[4 * t + 2];
+        ep.y = rot[4 * t + 3];
+        const V2 ai = A[col * p + i], aj = cmul(ep, A[col * p + j]);
+        V2 ni = cscale(ai, c) - cscale(aj, s);
+        V2 nj = cscale(ai, s) + cscale(aj, c);
+        if (s != (T)0 && col == j) ni.x = ni.y = (T)0;  // (i, j)
+        if (s != (T)0 && col == i) nj.x = nj.y = (T)0;  // (j, i)
+        if (col == i) ni.y = (T)0;
+        if (col == j) nj.y = (T)0;
+        A[col * p + i] = ni;
+        A[col * p + j] = nj;
+      }
+      __syncthreads();
+    }
   }
-  // ---- ascending order (ties by index) and write out
-  for (int i = tid; i < p; i += blockDim.x) {
-    const double wi = d[i];
+  __syncthreads();
+  // sort ascending by rank (ties by index) and write out
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const T wi = A[i * p + i].x;
     int rank = 0;
-    for (int j = 0; j < p; ++j)
-      if (d[j] < wi || (d[j] == wi && j < i)) ++rank;
-    w[(size_t)k * p + rank] = wi;
-    for (int r = 0; r < p; ++r) Vg[(size_t)k * p * p + (size_t)rank * p + r] = Z[i * ld + r];
+    for (int j = 0; j < p; ++j) {
+      const T wj = A[j * p + j].x;
+      if (wj < wi || (wj == wi && j < i)) ++rank;
+    }
+    w[(size_t)k * p + rank] = (double)wi;
+    for (int r = 0; r < p; ++r) Vg[(size_t)k * p * p + (size_t)rank * p + r] = to_d(V[i * p + r]);
   }
+}
+
+template <typename T>
+static void heig_t(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
+                   cudaStream_t st) {
+  const int pe = p + (p & 1);
+  const size_t sm = sizeof(cplx<T>) * 2 * p * p + sizeof(T) * (2 * pe + 2 + 16) + 16;
+  ensure_smem((const void*)k_heig<T>, sm);
+  const int threads = p <= 16 ? 64 : 256;
+  k_heig<T><<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
+  count_launch();
 }
 
 void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
                 cudaStream_t st) {
-  const size_t sm = sizeof(double2) * 2 * (size_t)p * (p + 1);
-  ensure_smem((const void*)k_heig, sm);
-  k_heig<<<K, HEIG_THREADS, sm, st>>>(p, A, sA, w, V, kactive);
-  count_launch();
+  heig_t<double>(K, p, A, sA, w, V, kactive, st);
 }
 // out = V diag(f(w)) V^H, f(x) = x^expo for x > cut_rel * max(w, 0), else 0
 __global__ void k_eig_func(int p, const double2* __restrict__ V, const double* __restrict__ w, double expo,
