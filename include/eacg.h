@@ -86,6 +86,13 @@ typedef struct {
   int max_fom;        /* 50  */
   int max_ls;         /* 30  */
   int precision;      /* 0 FP64, 1 mixed */
+  int graphs;         /* 1: the FOM's block H application is replayed as a CUDA graph per system
+                       * (captured on its second call with the same buffers); 0: direct launches.
+                       * Results are identical either way.  Default 1 */
+  int fft_plan;       /* line-FFT plan of the transforms: -1 picks the faster of the compiled
+                       * plans for this grid by timing both on the system at set-up (autotune);
+                       * 0 or 1 forces a plan (one that does not exist for N falls back to 0).
+                       * Default -1 */
 } eacg_params;
 
 typedef struct {

@@ -112,6 +112,27 @@ struct eacg_system {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> evpool;
   size_t evused = 0;
+  struct ProfMs {  // profile records already read back (graph replays)
+    int slot;
+    double ms, bytes, flops, units;
+  };
+  std::vector<ProfMs> prof_ms;
+  // ---- CUDA graph of the FOM's block H application, one per block precision
+  struct HGraph {
+    const void* in = nullptr;
+    const void* out = nullptr;
+    const void* ka = nullptr;
+    const void* cnw = nullptr;
+    int direct = 0;                   // direct calls with this key (capture on the second)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;            // kernel nodes of the graph
+    std::vector<ProfRec> recs;        // capture-time profile records; events owned by the graph
+    bool pending = false;             // a replay whose events were recorded but not yet read
+  };
+  HGraph hg[2];
+  HGraph* cap = nullptr;              // graph being captured (profile events go to it)
+  bool graphs_off = false;            // set when capture is not possible on this system
 };
 
 namespace {
@@ -139,6 +160,9 @@ cudaEvent_t prof_event(eacg_system* s) {
 }  // namespace
 
 void eacg::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+namespace {
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace
 
 namespace {
 std::mutex g_smem_mu;
@@ -156,19 +180,30 @@ void eacg::ensure_smem(const void* func, size_t bytes) {
   }
 }
 
-// Records CUDA events around a kernel (group) when profiling is on.
+// Records CUDA events around a kernel (group) when profiling is on.  While a graph is being
+// captured the events always go into the graph (they become event-record nodes whose times
+// are read back after each profiled replay).
+namespace {
+cudaEvent_t cap_event(eacg_system* s) {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
 #define PROF_RUN(slot, bytes_, flops_, units_, ...)                                       \
   do {                                                                            \
     cudaEvent_t a_ = nullptr;                                                     \
-    if (s->prof_on) {                                                             \
-      a_ = prof_event(s);                                                         \
+    const bool rec_ = s->prof_on || s->cap;                                       \
+    if (rec_) {                                                                   \
+      a_ = s->cap ? cap_event(s) : prof_event(s);                                 \
       cudaEventRecord(a_, s->st);                                                 \
     }                                                                             \
     __VA_ARGS__;                                                                  \
-    if (s->prof_on) {                                                             \
-      cudaEvent_t b_ = prof_event(s);                                             \
+    if (rec_) {                                                                   \
+      cudaEvent_t b_ = s->cap ? cap_event(s) : prof_event(s);                     \
       cudaEventRecord(b_, s->st);                                                 \
-      s->prof.push_back({(slot), a_, b_, (double)(bytes_), (double)(flops_), (double)(units_)}); \
+      (s->cap ? s->cap->recs : s->prof)                                           \
+          .push_back({(slot), a_, b_, (double)(bytes_), (double)(flops_), (double)(units_)}); \
     }                                                                             \
   } while (0)
 
@@ -283,6 +318,8 @@ extern "C" void eacg_default_params(eacg_params* prm) {
   prm->max_fom = 50;
   prm->max_ls = 30;
   prm->precision = 0;
+  prm->graphs = 1;
+  prm->fft_plan = -1;
 }
 
 static double sphere_volume_estimate(const eacg_model* m) {
@@ -781,6 +818,92 @@ static eacg_status apply_H_t(eacg_system* s, const float2* in, float2* out, cons
   return apply_H_block32(s, in, out, ka);
 }
 
+// ---- CUDA graph of the FOM's block H application
+// The FOM applies H to the same device blocks every iteration, so the whole launch sequence
+// (x pass, plane, x pass back, projector GEMMs) is captured once per system and block
+// precision and replayed.  The first call with a given set of buffers runs directly (it sets
+// the kernels' shared-memory limits), the second is captured (thread-local mode, so other
+// systems' host threads are unaffected) and every later call replays it.  The graph holds
+// event-record nodes at the profile slots; after a profiled replay their times are read back
+// before the next replay.  Any capture error turns graphs off for the system.
+static void hg_release(eacg_system::HGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  for (auto& r : g.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g = eacg_system::HGraph();
+}
+
+static void hg_resolve(eacg_system* s, eacg_system::HGraph& g) {
+  if (!g.pending) return;
+  for (const auto& r : g.recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) s->prof_ms.push_back({r.slot, ms, r.bytes, r.flops, r.units});
+  }
+  g.pending = false;
+}
+
+template <typename V>
+static eacg_status apply_H_fom(eacg_system* s, const V* in, V* out, const int* ka) {
+  auto& g = s->hg[sizeof(V) == sizeof(float2) ? 1 : 0];
+  if (!s->prm.graphs || s->graphs_off) return apply_H_t(s, in, out, ka);
+  const bool same = g.in == in && g.out == out && g.ka == ka && g.cnw == s->cn_work;
+  if (!same) {
+    hg_release(g);
+    g.in = in;
+    g.out = out;
+    g.ka = ka;
+    g.cnw = s->cn_work;
+  }
+  if (!g.exec) {
+    if (g.direct++ == 0) return apply_H_t(s, in, out, ka);
+    // capture
+    cudaGetLastError();
+    if (cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      s->graphs_off = true;
+      return apply_H_t(s, in, out, ka);
+    }
+    const long long h0 = s->h_apps;
+    s->cap = &g;
+    const eacg_status st = apply_H_t(s, in, out, ka);
+    s->cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(s->st, &graph);
+    s->h_apps = h0;
+    cudaGraphExec_t exec = nullptr;
+    if (st != EACG_OK || e1 != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      hg_release(g);
+      s->graphs_off = true;
+      return st != EACG_OK ? st : apply_H_t(s, in, out, ka);
+    }
+    g.graph = graph;
+    g.exec = exec;
+    // kernel nodes of the graph: the capture counted them as launches, the replays launch them
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    g.kernels = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++g.kernels;
+    }
+    count_launches(-g.kernels);
+  }
+  hg_resolve(s, g);
+  CK(cudaGraphLaunch(g.exec, s->st));
+  count_launches(g.kernels);
+  s->h_apps += (long long)s->K * s->p;
+  if (s->prof_on) g.pending = true;
+  return EACG_OK;
+}
+
 // Rank-revealing orthonormalisation of R (n x p per k) against the first q columns of V
 // (Algorithm 4's rank-revealing QR, reading: two projections, then QR with column pivoting
 // written as a diagonally pivoted Cholesky of the Gram matrix, stopped below a relative
@@ -883,7 +1006,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
   cudaMemsetAsync(vt, 0, sizeof(V) * s->blk, s->st);
   cudaMemsetAsync(wt, 0, sizeof(V) * s->blk, s->st);
   TRY(orthonormalise<T>(s, t2, nullptr, 0, 0, vt, t3, s->d_kactive));
-  TRY(apply_H_t(s, vt, wt, s->d_kactive));
+  TRY(apply_H_fom(s, vt, wt, s->d_kactive));
   TRY(put_cols(s, vt, wt, 0));
   int q = 0;
   auto add_block = [&](int q0) -> eacg_status {
@@ -992,7 +1115,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     small_take_y(K, q, s->qcap, p, s->fYt, s->fYf, s->d_take, s->st);
     if (!any2) break;
     TRY(upload_active());
-    TRY(apply_H_t(s, vt, wt, s->d_kactive));
+    TRY(apply_H_fom(s, vt, wt, s->d_kactive));
     TRY(put_cols(s, vt, wt, q));
     // the H application above advanced h_apps by all K; keep the per-k count honest
     {
@@ -1432,6 +1555,7 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
 extern "C" void eacg_destroy(eacg_system* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
+  for (auto& g : s->hg) hg_release(g);
   for (cudaEvent_t e : s->evpool) cudaEventDestroy(e);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_out) cudaFreeHost(s->h_out);
@@ -1628,6 +1752,8 @@ extern "C" eacg_status eacg_profile_enable(eacg_system* s, int on) {
   SYS_CHECK(s);
   CK(cudaStreamSynchronize(s->st));
   s->prof.clear();
+  s->prof_ms.clear();
+  for (auto& g : s->hg) g.pending = false;
   s->evused = 0;
   s->prof_on = on != 0;
   return EACG_OK;
@@ -1648,7 +1774,16 @@ extern "C" int eacg_profile_read(eacg_system* s, eacg_kernel_stat* out, int max)
     acc[r.slot].flops += r.flops;
     acc[r.slot].units += r.units;
   }
+  for (auto& g : s->hg) hg_resolve(s, g);
+  for (const auto& r : s->prof_ms) {
+    acc[r.slot].launches += 1;
+    acc[r.slot].ms += r.ms;
+    acc[r.slot].bytes += r.bytes;
+    acc[r.slot].flops += r.flops;
+    acc[r.slot].units += r.units;
+  }
   s->prof.clear();
+  s->prof_ms.clear();
   s->evused = 0;
   int n = 0;
   for (int i = 0; i < P_NSLOTS && n < max; ++i)
