@@ -134,6 +134,11 @@ const char* eacg_last_error(const eacg_system* sys);
 
 /* n_k per k-point (nk_host: K ints, may be NULL), n_max = max n_k, union column count. */
 eacg_status eacg_get_dims(const eacg_system* sys, int* nk_host, int* n_max, int* ncols);
+/* Line-FFT plan variant (0 or 1) the system uses for its FP64 and its FP32 transforms: the
+ * one eacg_params.fft_plan forced, else the one the set-up timing found faster (variant 0
+ * where the grid size has a single plan).  Implementation detail of the transforms; the
+ * paper has no counterpart. */
+eacg_status eacg_get_plans(const eacg_system* sys, int* plan64, int* plan32);
 /* Integer triples m (G = 2 pi m / a) of the basis: m_dev int32 [K][n_max][3]
  * (rows >= n_k unspecified).  Canonical order: (mx, my, mz) lexicographic, mz fastest. */
 eacg_status eacg_get_basis(const eacg_system* sys, int* m_dev);

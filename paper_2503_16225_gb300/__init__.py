@@ -16,7 +16,7 @@ from .build import LIB
 __all__ = [
     "EacgModel", "EacgParams", "EacgStepInfo", "EacgResult", "EacgError", "lib", "model_from_config",
     "eacg_default_params", "eacg_bytes_required", "eacg_create_system", "eacg_destroy", "eacg_last_error",
-    "eacg_get_dims", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
+    "eacg_get_dims", "eacg_get_plans", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
     "System", "STATUS",
@@ -83,6 +83,7 @@ def _load():
         "eacg_destroy": (None, [vp]),
         "eacg_last_error": (ctypes.c_char_p, [vp]),
         "eacg_get_dims": (ctypes.c_int, [vp, _ip, _ip, _ip]),
+        "eacg_get_plans": (ctypes.c_int, [vp, _ip, _ip]),
         "eacg_get_basis": (ctypes.c_int, [vp, vp]),
         "eacg_set_psi": (ctypes.c_int, [vp, vp]),
         "eacg_get_psi": (ctypes.c_int, [vp, vp]),
@@ -203,6 +204,13 @@ def eacg_get_basis(sys, m_dev):
 
 def eacg_set_psi(sys, psi):
     _check(sys, lib.eacg_set_psi(sys, _ptr(psi)))
+
+
+def eacg_get_plans(sys):
+    """(plan of the FP64 transforms, plan of the FP32 transforms)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(sys, lib.eacg_get_plans(sys, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def eacg_get_psi(sys, out):

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <map>
@@ -1452,6 +1453,76 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
     if (!(sys)) return EACG_EINVAL;         \
   } while (0)
 
+// ---- autotune of the line-FFT plan
+// For grid sizes with two compiled line plans, time both on this system's transform pipeline
+// (inverse x pass, plane, forward x pass over all bands) in each precision and keep the faster.
+// The transforms' time does not depend on the values, so zeroed buffers are used.  Choices are
+// cached per (device, N, columns, rows, bands, n_max) for the whole process.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, std::pair<int, int>> g_tune;
+}  // namespace
+
+static eacg_status autotune_plans(eacg_system* s) {
+  s->g.plan64 = s->g.plan32 = 0;
+  if (!grid_has_plan1(s->N)) return EACG_OK;
+  if (s->prm.fft_plan == 0 || s->prm.fft_plan == 1) {
+    s->g.plan64 = s->g.plan32 = s->prm.fft_plan;
+    return EACG_OK;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::array<int, 6> key = {dev, s->N, s->ncols, s->ny, s->K * s->p, s->n_max};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      s->g.plan64 = it->second.first;
+      s->g.plan32 = it->second.second;
+      return EACG_OK;
+    }
+  }
+  const int nb = s->K * s->p;
+  CK(cudaMemsetAsync(s->phi, 0, sizeof(double2) * s->blk, s->st));
+  CK(cudaMemsetAsync(s->d_tbuf, 0, sizeof(double2) * (size_t)nb * s->N * s->ncols, s->st));
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  int choice[2] = {0, 0};
+  for (int prec = 0; prec < 2; ++prec) {
+    const void* v = prec == 0 ? (const void*)s->d_vtot : (const void*)s->d_vtot32;
+    const int reps = prec == 0 ? 1 : 4;
+    float best = 0.f;
+    for (int plan = 0; plan < 2; ++plan) {
+      (prec == 0 ? s->g.plan64 : s->g.plan32) = plan;
+      auto run = [&]() {
+        grid_xpass_inv(s->g, prec, s->phi, s->d_tbuf, nb, nullptr, s->st);
+        grid_plane_h(s->g, prec, s->d_tbuf, v, nb, nullptr, s->st);
+        grid_xpass_fwd(s->g, prec, s->d_tbuf, s->phi, nullptr, 1.0, s->tmp1, nb, nullptr, s->st);
+      };
+      run();  // first launch of each kernel outside the timing
+      CK(cudaEventRecord(a, s->st));
+      for (int r = 0; r < reps; ++r) run();
+      CK(cudaEventRecord(b, s->st));
+      CK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, a, b));
+      if (plan == 0 || ms < best) {
+        best = ms;
+        choice[prec] = plan;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CKL(s);
+  s->g.plan64 = choice[0];
+  s->g.plan32 = choice[1];
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = {choice[0], choice[1]};
+  return EACG_OK;
+}
+
 extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params* prm, void* stream,
                                           eacg_system** out) {
   if (!out) return EACG_EINVAL;
@@ -1544,6 +1615,7 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   s->g.tw32 = s->d_tw32;
   if ((st = build_potential_and_projectors(s)) != EACG_OK) return fail(st);
   if ((st = alloc_work(s)) != EACG_OK) return fail(st);
+  if ((st = autotune_plans(s)) != EACG_OK) return fail(st);
   if (cudaStreamSynchronize(s->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     s->err = "set-up kernels failed";
     return fail(EACG_ECUDA);
@@ -1561,6 +1633,13 @@ extern "C" void eacg_destroy(eacg_system* s) {
   if (s->h_out) cudaFreeHost(s->h_out);
   if (s->h_int) cudaFreeHost(s->h_int);
   delete s;
+}
+
+extern "C" eacg_status eacg_get_plans(const eacg_system* s, int* plan64, int* plan32) {
+  SYS_CHECK(s);
+  if (plan64) *plan64 = s->g.plan64;
+  if (plan32) *plan32 = s->g.plan32;
+  return EACG_OK;
 }
 
 extern "C" const char* eacg_last_error(const eacg_system* s) { return s ? s->err.c_str() : "null system"; }

@@ -24,30 +24,40 @@
 
 namespace eacg {
 
-template <int N>
+// Plan variant 0 exists for every supported N; variant 1 (a second split N1 x N2) where one
+// is worth trying.  The autotuner picks between them per system and precision.
+template <int N, int PV = 0>
 struct LinePlan;
-#define EACG_LINE_PLAN(N_, A_, B_)             \
+#define EACG_LINE_PLAN(N_, PV_, A_, B_)        \
   template <>                                  \
-  struct LinePlan<N_> {                        \
+  struct LinePlan<N_, PV_> {                   \
     static constexpr int N1 = A_, N2 = B_;     \
   };
-EACG_LINE_PLAN(8, 4, 2)
-EACG_LINE_PLAN(12, 6, 2)
-EACG_LINE_PLAN(16, 4, 4)
-EACG_LINE_PLAN(20, 10, 2)
-EACG_LINE_PLAN(24, 12, 2)
-EACG_LINE_PLAN(32, 8, 4)
-EACG_LINE_PLAN(36, 12, 3)
-EACG_LINE_PLAN(40, 20, 2)
-EACG_LINE_PLAN(48, 12, 4)
-EACG_LINE_PLAN(64, 16, 4)
-EACG_LINE_PLAN(72, 12, 6)
-EACG_LINE_PLAN(80, 20, 4)
-EACG_LINE_PLAN(96, 24, 4)
+EACG_LINE_PLAN(8, 0, 4, 2)
+EACG_LINE_PLAN(12, 0, 6, 2)
+EACG_LINE_PLAN(16, 0, 4, 4)
+EACG_LINE_PLAN(20, 0, 10, 2)
+EACG_LINE_PLAN(24, 0, 12, 2)
+EACG_LINE_PLAN(32, 0, 8, 4)
+EACG_LINE_PLAN(36, 0, 12, 3)
+EACG_LINE_PLAN(40, 0, 20, 2)
+EACG_LINE_PLAN(48, 0, 12, 4)
+EACG_LINE_PLAN(64, 0, 16, 4)
+EACG_LINE_PLAN(72, 0, 12, 6)
+EACG_LINE_PLAN(80, 0, 20, 4)
+EACG_LINE_PLAN(96, 0, 24, 4)
+EACG_LINE_PLAN(16, 1, 8, 2)
+EACG_LINE_PLAN(32, 1, 16, 2)
+EACG_LINE_PLAN(36, 1, 6, 6)
+EACG_LINE_PLAN(48, 1, 24, 2)
+EACG_LINE_PLAN(64, 1, 8, 8)
+EACG_LINE_PLAN(72, 1, 24, 3)
 #undef EACG_LINE_PLAN
 
-// The supported line lengths (every N with a LinePlan), for host-side checks and dispatch.
+// The supported line lengths (every N with a LinePlan), for host-side checks and dispatch,
+// and those with a second plan variant.
 #define EACG_FOR_EACH_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(64) X(72) X(80) X(96)
+#define EACG_FOR_EACH_N_PLAN1(X) X(16) X(32) X(36) X(48) X(64) X(72)
 
 template <int R, bool INV, typename V>
 __device__ __forceinline__ void dft_small(V* v) {
@@ -140,9 +150,9 @@ __device__ __forceinline__ void reg_dft(V* a, const V* tw) {
 }
 
 // Step 1 of slot t: a[m] = x[t + N2 m] in; a[k1] = w_N^{t k1} sum_m x[t + N2 m] w_N1^{m k1} out.
-template <int N, bool INV, typename V>
+template <int N, int PV, bool INV, typename V>
 __device__ __forceinline__ void line_step1(V* a, int t, const V* tw) {
-  constexpr int N1 = LinePlan<N>::N1;
+  constexpr int N1 = LinePlan<N, PV>::N1;
   reg_dft<N1, N, INV>(a, tw);
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) a[k1] = twiddle<N, INV>(a[k1], t * k1, tw);  // t k1 < N
@@ -150,9 +160,9 @@ __device__ __forceinline__ void line_step1(V* a, int t, const V* tw) {
 
 // Step 2 of slot t: a[j N2 + tt] = step-1 value of slot tt at k1 = t + N2 j in;
 // a[j N2 + k2] = X[(t + N2 j) + N1 k2] out.
-template <int N, bool INV, typename V>
+template <int N, int PV, bool INV, typename V>
 __device__ __forceinline__ void line_step2(V* a, const V* tw) {
-  constexpr int N1 = LinePlan<N>::N1, N2 = LinePlan<N>::N2;
+  constexpr int N1 = LinePlan<N, PV>::N1, N2 = LinePlan<N, PV>::N2;
 #pragma unroll
   for (int j = 0; j < N1 / N2; ++j) reg_dft<N2, N, INV>(a + j * N2, tw);
 }
@@ -164,10 +174,10 @@ __device__ __forceinline__ void line_step2(V* a, const V* tw) {
 // phase, and with MIDSYNC also between the step-2 loads and the stores (needed when the
 // scratch slots of a line are the places its outputs are stored to).  Every thread must
 // call it.
-template <int N, bool INV, bool MIDSYNC, typename V, typename Scratch, typename Load, typename Store>
+template <int N, int PV, bool INV, bool MIDSYNC, typename V, typename Scratch, typename Load, typename Store>
 __device__ __forceinline__ void fft_phase(int nlines, const V* tw, const Scratch& scratch, const Load& load,
                                           const Store& store) {
-  constexpr int N1 = LinePlan<N>::N1, N2 = LinePlan<N>::N2;
+  constexpr int N1 = LinePlan<N, PV>::N1, N2 = LinePlan<N, PV>::N2;
   const int L = blockDim.x / N2;
   const int l = threadIdx.x % L, t = threadIdx.x / L;
   const bool act = t < N2 && l < nlines;
@@ -175,7 +185,7 @@ __device__ __forceinline__ void fft_phase(int nlines, const V* tw, const Scratch
   if (act) {
 #pragma unroll
     for (int m = 0; m < N1; ++m) a[m] = load(l, t + N2 * m);
-    line_step1<N, INV>(a, t, tw);
+    line_step1<N, PV, INV>(a, t, tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) *scratch(l, t + N2 * k1) = a[k1];
   }
@@ -185,7 +195,7 @@ __device__ __forceinline__ void fft_phase(int nlines, const V* tw, const Scratch
     for (int j = 0; j < N1 / N2; ++j)
 #pragma unroll
       for (int tt = 0; tt < N2; ++tt) a[j * N2 + tt] = *scratch(l, tt + N2 * (t + N2 * j));
-    line_step2<N, INV>(a, tw);
+    line_step2<N, PV, INV>(a, tw);
   }
   if (MIDSYNC) __syncthreads();
   if (act) {

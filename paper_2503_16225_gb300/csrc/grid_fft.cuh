@@ -24,12 +24,12 @@ constexpr int XPASS_THREADS = 256;  // x-pass CTA: 256 / N2 columns of one band
 
 // Inverse x pass: sphere coefficients gathered straight into the step-1 registers; the
 // transformed columns are written to tbuf[band][jx][col] (coalesced over columns).
-template <typename T, int N, typename TIO>
+template <typename T, int N, int PV, typename TIO>
 __global__ void __launch_bounds__(XPASS_THREADS)
     k_xpass_inv(const TIO* __restrict__ psi, int n_max, int p, const int* __restrict__ xmap, int ncols,
                 cplx<T>* __restrict__ tbuf, const cplx<T>* __restrict__ tw_g, const int* __restrict__ kactive) {
   using V = cplx<T>;
-  constexpr int N2 = LinePlan<N>::N2;
+  constexpr int N2 = LinePlan<N, PV>::N2;
   __shared__ V tw[N];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(XPASS_THREADS)
   const int* xm = xmap + (size_t)k * N * ncols + c0;
   const TIO* src = psi + (size_t)band * n_max;
   V* dst = tbuf + (size_t)band * N * ncols + c0;
-  fft_phase<N, true, false>(
+  fft_phase<N, PV, true, false>(
       nc, tw, PitchedScratch<V>{A, N + 1},
       [&](int l, int fx) {
         const int id = xm[(size_t)fx * ncols + l];
@@ -54,14 +54,14 @@ __global__ void __launch_bounds__(XPASS_THREADS)
 
 // Forward x pass and gather: out = scale * FFT + kin * psi_in (kin may be null); the padding
 // beyond n_k is zeroed.
-template <typename T, int N, typename TIO>
+template <typename T, int N, int PV, typename TIO>
 __global__ void __launch_bounds__(XPASS_THREADS)
     k_xpass_fwd(const cplx<T>* __restrict__ tbuf, const int* __restrict__ xmap, int ncols,
                 const cplx<T>* __restrict__ tw_g, int n_max, int p, const int* __restrict__ nk,
                 const TIO* __restrict__ psi_in, const double* __restrict__ kin, double scale, TIO* __restrict__ out,
                 const int* __restrict__ kactive) {
   using V = cplx<T>;
-  constexpr int N2 = LinePlan<N>::N2;
+  constexpr int N2 = LinePlan<N, PV>::N2;
   __shared__ V tw[N];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(XPASS_THREADS)
   TIO* o = out + (size_t)band * n_max;
   const TIO* pin = psi_in + (size_t)band * n_max;
   const double* kk = kin ? kin + (size_t)k * n_max : nullptr;
-  fft_phase<N, false, false>(
+  fft_phase<N, PV, false, false>(
       nc, tw, PitchedScratch<V>{A, N + 1}, [&](int l, int jx) { return src[(size_t)jx * ncols + l]; },
       [&](int l, int fx, V x, int) {
         const int id = xm[(size_t)fx * ncols + l];
@@ -142,8 +142,8 @@ struct YScratch {
 
 // Apply the local potential to one x-plane of one band.  Only rows that hold columns are
 // read before the y pass, so nothing is zeroed.
-template <typename T, int N>
-__global__ void __launch_bounds__(N * LinePlan<N>::N2)
+template <typename T, int N, int PV>
+__global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
     k_plane_h(cplx<T>* __restrict__ tbuf, int ncols, const int* __restrict__ cmapy, const int* __restrict__ ylist,
               const int* __restrict__ rowmask, int ny, const T* __restrict__ v, const cplx<T>* __restrict__ tw_g, int p,
               const int* __restrict__ kactive) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(N * LinePlan<N>::N2)
   const ZScratch<V, N, PING> zs{A, B, yl};
   const YScratch<V, N, PING> ys{A, B};
   // z inverse over the rows with columns, straight from the column buffer
-  fft_phase<N, true, !PING>(
+  fft_phase<N, PV, true, !PING>(
       ny, tw, zs,
       [&](int l, int fz) {
         const int c = cm[l * PP + fz];
@@ -172,17 +172,17 @@ __global__ void __launch_bounds__(N * LinePlan<N>::N2)
       },
       [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
   // y inverse over every jz (rows without columns are zero), times the potential
-  fft_phase<N, true, !PING>(
+  fft_phase<N, PV, true, !PING>(
       N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
       [&](int jz, int jy, V x, int) { B[jy * PP + jz] = cscale(x, vv[jy * N + jz]); });
   // y forward, keeping the rows with columns
-  fft_phase<N, false, !PING>(
+  fft_phase<N, PV, false, !PING>(
       N, tw, ys, [&](int jz, int jy) { return B[jy * PP + jz]; },
       [&](int jz, int fy, V x, int) {
         if (rows[fy]) B[fy * PP + jz] = x;
       });
   // z forward, back onto the columns
-  fft_phase<N, false, false>(
+  fft_phase<N, PV, false, false>(
       ny, tw, zs, [&](int l, int jz) { return B[yl[l] * PP + jz]; },
       [&](int l, int fz, V x, int) {
         const int c = cm[l * PP + fz];
@@ -193,14 +193,14 @@ __global__ void __launch_bounds__(N * LinePlan<N>::N2)
 // Density of a group of bands on one x-plane: sum_b w_b |u_b|^2 in FP64 registers (each
 // grid point owned by one thread of the y pass, bands in a fixed order), written as
 // partial[g][jx][jy][jz].
-template <typename T, int N>
-__global__ void __launch_bounds__(N * LinePlan<N>::N2)
+template <typename T, int N, int PV>
+__global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
     k_plane_rho(const cplx<T>* __restrict__ tbuf, int ncols, const int* __restrict__ cmapy,
                 const int* __restrict__ ylist, const int* __restrict__ rowmask, int ny,
                 const cplx<T>* __restrict__ tw_g, int nbands, int bands_per_group, const double* __restrict__ bw,
                 double* __restrict__ partial) {
   using V = cplx<T>;
-  constexpr int PP = N + 1, N1 = LinePlan<N>::N1, N2 = LinePlan<N>::N2;
+  constexpr int PP = N + 1, N1 = LinePlan<N, PV>::N1, N2 = LinePlan<N, PV>::N2;
   constexpr bool PING = PlaneCfg<T, N>::pingpong;
   __shared__ V tw[N];
   __shared__ int rows[N], yl[N];
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(N * LinePlan<N>::N2)
   const int b0 = g * bands_per_group, b1 = min(nbands, b0 + bands_per_group);
   for (int band = b0; band < b1; ++band) {
     const V* tb = tbuf + ((size_t)band * N + jx) * ncols;
-    fft_phase<N, true, !PING>(
+    fft_phase<N, PV, true, !PING>(
         ny, tw, zs,
         [&](int l, int fz) {
           const int c = cm[l * PP + fz];
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(N * LinePlan<N>::N2)
         },
         [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
     const double w = bw[band];
-    fft_phase<N, true, false>(
+    fft_phase<N, PV, true, false>(
         N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
         [&](int, int, V x, int q) {
           const double2 u = to_d(x);
@@ -248,10 +248,10 @@ __global__ void __launch_bounds__(N * LinePlan<N>::N2)
 
 // Lines along one axis of a complex N^3 array a[x][y][z] (axis 2 = z, 1 = y, 0 = x),
 // transformed in place, 256 / N2 lines per CTA.
-template <int N, bool INV>
+template <int N, int PV, bool INV>
 __global__ void __launch_bounds__(XPASS_THREADS)
     k_fft3_axis(double2* __restrict__ a, int axis, const double2* __restrict__ tw_g) {
-  constexpr int N2 = LinePlan<N>::N2;
+  constexpr int N2 = LinePlan<N, PV>::N2;
   __shared__ double2 tw[N];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -266,15 +266,16 @@ __global__ void __launch_bounds__(XPASS_THREADS)
     if (axis == 1) return ((size_t)u * N + j) * N + w;
     return ((size_t)j * N + u) * N + w;
   };
-  fft_phase<N, INV, false>(
+  fft_phase<N, PV, INV, false>(
       nl, tw, PitchedScratch<double2>{A, N + 1}, [&](int l, int j) { return a[addr(l, j)]; },
       [&](int l, int o, double2 x, int) { a[addr(l, o)] = x; });
 }
 
-// Launchers of one grid size; instantiated once per supported N (grid_fft_n*.cu).
-template <int N>
+// Launchers of one grid size and line-plan variant; instantiated per supported (N, variant)
+// in the grid_fft_*.cu units.
+template <int N, int PV>
 struct GridFft {
-  static constexpr int N2 = LinePlan<N>::N2;
+  static constexpr int N2 = LinePlan<N, PV>::N2;
 
   template <typename T, typename TIO>
   static void xinv(const GridCtx& g, const TIO* psi, void* tbuf, const void* tw, int nbands, const int* kactive,
@@ -282,8 +283,8 @@ struct GridFft {
     const int cpc = XPASS_THREADS / N2;
     dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
     const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
-    ensure_smem((const void*)k_xpass_inv<T, N, TIO>, sm);
-    k_xpass_inv<T, N, TIO><<<grid, cpc * N2, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf,
+    ensure_smem((const void*)k_xpass_inv<T, N, PV, TIO>, sm);
+    k_xpass_inv<T, N, PV, TIO><<<grid, cpc * N2, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf,
                                                         (const cplx<T>*)tw, kactive);
     count_launch();
   }
@@ -294,8 +295,8 @@ struct GridFft {
     const int cpc = XPASS_THREADS / N2;
     dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
     const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
-    ensure_smem((const void*)k_xpass_fwd<T, N, TIO>, sm);
-    k_xpass_fwd<T, N, TIO><<<grid, cpc * N2, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, (const cplx<T>*)tw,
+    ensure_smem((const void*)k_xpass_fwd<T, N, PV, TIO>, sm);
+    k_xpass_fwd<T, N, PV, TIO><<<grid, cpc * N2, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, (const cplx<T>*)tw,
                                                         g.n_max, g.p, g.nk, psi_in, kin, scale, out, kactive);
     count_launch();
   }
@@ -326,8 +327,8 @@ struct GridFft {
   static void plane_h_t(const GridCtx& g, void* tbuf, const void* tw, const void* v, int nbands, const int* kactive,
                         cudaStream_t st) {
     const size_t sm = PlaneCfg<T, N>::smem_bytes(g.ny);
-    ensure_smem((const void*)k_plane_h<T, N>, sm);
-    k_plane_h<T, N><<<dim3(N, nbands), N * N2, sm, st>>>((cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist, g.rowmask, g.ny,
+    ensure_smem((const void*)k_plane_h<T, N, PV>, sm);
+    k_plane_h<T, N, PV><<<dim3(N, nbands), N * N2, sm, st>>>((cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist, g.rowmask, g.ny,
                                                          (const T*)v, (const cplx<T>*)tw, g.p, kactive);
     count_launch();
   }
@@ -344,9 +345,9 @@ struct GridFft {
   static void plane_rho_t(const GridCtx& g, const void* tbuf, const void* tw, int nbands, int groups,
                           const double* bw, double* partial, cudaStream_t st) {
     const size_t sm = PlaneCfg<T, N>::smem_bytes(g.ny);
-    ensure_smem((const void*)k_plane_rho<T, N>, sm);
+    ensure_smem((const void*)k_plane_rho<T, N, PV>, sm);
     const int bpg = (nbands + groups - 1) / groups;
-    k_plane_rho<T, N><<<dim3(N, groups), N * N2, sm, st>>>((const cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist,
+    k_plane_rho<T, N, PV><<<dim3(N, groups), N * N2, sm, st>>>((const cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist,
                                                            g.rowmask, g.ny, (const cplx<T>*)tw, nbands, bpg, bw,
                                                            partial);
     count_launch();
@@ -364,8 +365,8 @@ struct GridFft {
   static void fft3_axis(const GridCtx& g, double2* a, int axis, cudaStream_t st) {
     const int lpc = XPASS_THREADS / N2;
     const size_t sm = sizeof(double2) * (size_t)lpc * (N + 1);
-    ensure_smem((const void*)k_fft3_axis<N, INV>, sm);
-    k_fft3_axis<N, INV><<<(N * N + lpc - 1) / lpc, lpc * N2, sm, st>>>(a, axis, (const double2*)g.tw64);
+    ensure_smem((const void*)k_fft3_axis<N, PV, INV>, sm);
+    k_fft3_axis<N, PV, INV><<<(N * N + lpc - 1) / lpc, lpc * N2, sm, st>>>(a, axis, (const double2*)g.tw64);
     count_launch();
   }
 

@@ -2,7 +2,9 @@
 #include "grid_fft.cuh"
 
 namespace eacg {
-template struct GridFft<32>;
-template struct GridFft<36>;
-template struct GridFft<40>;
+template struct GridFft<32, 0>;
+template struct GridFft<32, 1>;
+template struct GridFft<36, 0>;
+template struct GridFft<36, 1>;
+template struct GridFft<40, 0>;
 }  // namespace eacg

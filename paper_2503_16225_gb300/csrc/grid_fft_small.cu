@@ -3,9 +3,10 @@
 #include "grid_fft.cuh"
 
 namespace eacg {
-template struct GridFft<8>;
-template struct GridFft<12>;
-template struct GridFft<16>;
-template struct GridFft<20>;
-template struct GridFft<24>;
+template struct GridFft<8, 0>;
+template struct GridFft<12, 0>;
+template struct GridFft<16, 0>;
+template struct GridFft<16, 1>;
+template struct GridFft<20, 0>;
+template struct GridFft<24, 0>;
 }  // namespace eacg

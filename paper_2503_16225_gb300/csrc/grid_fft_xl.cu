@@ -2,6 +2,6 @@
 #include "grid_fft.cuh"
 
 namespace eacg {
-template struct GridFft<80>;
-template struct GridFft<96>;
+template struct GridFft<80, 0>;
+template struct GridFft<96, 0>;
 }  // namespace eacg

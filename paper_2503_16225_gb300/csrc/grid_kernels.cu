@@ -263,9 +263,12 @@ __global__ void k_projectors(int K, int n_max, const int* __restrict__ nk, const
 }
 
 // ----------------------------------------------------------------------------- launchers
-#define EACG_EXTERN_N(N_) extern template struct GridFft<N_>;
+#define EACG_EXTERN_N(N_) extern template struct GridFft<N_, 0>;
 EACG_FOR_EACH_N(EACG_EXTERN_N)
 #undef EACG_EXTERN_N
+#define EACG_EXTERN_N1(N_) extern template struct GridFft<N_, 1>;
+EACG_FOR_EACH_N_PLAN1(EACG_EXTERN_N1)
+#undef EACG_EXTERN_N1
 
 #define EACG_CASE_N(N_) \
   case N_:              \
@@ -277,15 +280,35 @@ bool grid_supported(int N) {
       return false;
   }
 }
+bool grid_has_plan1(int N) {
+  switch (N) {
+    EACG_FOR_EACH_N_PLAN1(EACG_CASE_N)
+    default:
+      return false;
+  }
+}
 #undef EACG_CASE_N
 
-// Calls f(GridFft<N>()) for the grid size N (grid_supported(N) is checked at set-up).
+// Calls f(GridFft<N, plan>()) for the grid size N (grid_supported(N) is checked at set-up);
+// plan 1 falls back to 0 where N has no second plan.
 template <typename F>
-static void dispatch_n(int N, const F& f) {
+static void dispatch_n(int N, int plan, const F& f) {
+  if (plan == 1) {
+    switch (N) {
+#define EACG_CASE_N1(N_)  \
+  case N_:                \
+    f(GridFft<N_, 1>());  \
+    return;
+      EACG_FOR_EACH_N_PLAN1(EACG_CASE_N1)
+#undef EACG_CASE_N1
+      default:
+        break;
+    }
+  }
   switch (N) {
-#define EACG_CASE_N(N_) \
-  case N_:              \
-    f(GridFft<N_>());   \
+#define EACG_CASE_N(N_)   \
+  case N_:                \
+    f(GridFft<N_, 0>());  \
     break;
     EACG_FOR_EACH_N(EACG_CASE_N)
 #undef EACG_CASE_N
@@ -294,40 +317,49 @@ static void dispatch_n(int N, const F& f) {
   }
 }
 
+// line-plan variant of the transforms in this precision (0: FP64, else FP32)
+static int plan_of(const GridCtx& g, int prec) { return prec == 0 ? g.plan64 : g.plan32; }
+
 void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, int nbands, const int* kactive,
                     cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) { decltype(G)::xpass_inv(g, prec == 0 ? 0 : 1, psi, tbuf, nbands, kactive, st); });
+  dispatch_n(g.N, plan_of(g, prec), [&](auto G) {
+    decltype(G)::xpass_inv(g, prec == 0 ? 0 : 1, psi, tbuf, nbands, kactive, st);
+  });
 }
 
 void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
                     double scale, double2* out, int nbands, const int* kactive, cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) {
+  dispatch_n(g.N, plan_of(g, prec), [&](auto G) {
     decltype(G)::xpass_fwd(g, prec == 0 ? 0 : 1, tbuf, psi_in, kin, scale, out, nbands, kactive, st);
   });
 }
 
 void grid_xpass_inv32(const GridCtx& g, const float2* psi, void* tbuf, int nbands, const int* kactive,
                       cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) { decltype(G)::xpass_inv(g, 2, psi, tbuf, nbands, kactive, st); });
+  dispatch_n(g.N, g.plan32, [&](auto G) { decltype(G)::xpass_inv(g, 2, psi, tbuf, nbands, kactive, st); });
 }
 
 void grid_xpass_fwd32(const GridCtx& g, const void* tbuf, const float2* psi_in, const double* kin, double scale,
                       float2* out, int nbands, const int* kactive, cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) { decltype(G)::xpass_fwd(g, 2, tbuf, psi_in, kin, scale, out, nbands, kactive, st); });
+  dispatch_n(g.N, g.plan32, [&](auto G) {
+    decltype(G)::xpass_fwd(g, 2, tbuf, psi_in, kin, scale, out, nbands, kactive, st);
+  });
 }
 
 void grid_plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
                   cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) { decltype(G)::plane_h(g, prec, tbuf, v, nbands, kactive, st); });
+  dispatch_n(g.N, plan_of(g, prec), [&](auto G) { decltype(G)::plane_h(g, prec, tbuf, v, nbands, kactive, st); });
 }
 
 void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
                     double* partial, cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) { decltype(G)::plane_rho(g, prec, tbuf, nbands, groups, bw, partial, st); });
+  dispatch_n(g.N, plan_of(g, prec), [&](auto G) {
+    decltype(G)::plane_rho(g, prec, tbuf, nbands, groups, bw, partial, st);
+  });
 }
 
 void grid_fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
-  dispatch_n(g.N, [&](auto G) { decltype(G)::fft3(g, a, inverse, st); });
+  dispatch_n(g.N, g.plan64, [&](auto G) { decltype(G)::fft3(g, a, inverse, st); });
 }
 
 void grid_reduce_groups(const double* partial, int G, size_t n, double* out, cudaStream_t st) {

@@ -20,6 +20,7 @@ void ensure_smem(const void* func, size_t bytes);
 // Device-side description of the plane-wave grid of one system.
 struct GridCtx {
   int N, K, p, n_max, ncols, ny;
+  int plan64, plan32;  // line-plan variant of the FP64 and the FP32 transforms (0 or 1)
   const int* nk;       // [K]
   const int* xmap;     // [K][N][ncols]: sphere index of (fx, column) at k, or -1
   const int* cmapy;    // [ny][N + 1]: column of (ylist[l], fz), or -1
@@ -32,8 +33,10 @@ struct GridCtx {
 // ---- grid_kernels.cu
 void grid_build_sphere(int N, int K, const double* kfrac_d, double thr, double b, int n_max_cap, int* nk, int* row_off,
                        int* m, double* kin, int* colmark, cudaStream_t st);
-// True if N has a compile-time line plan (the grid sizes this library transforms).
+// True if N has a compile-time line plan (the grid sizes this library transforms), and if it
+// has a second plan variant for the autotuner to try.
 bool grid_supported(int N);
+bool grid_has_plan1(int N);
 void grid_columns(int N, const int* colmark, int* colidx, int* cmapy, int* rowmask, int* ncols, int* ylist, int* ny,
                   cudaStream_t st);
 void grid_xmap(int N, int K, int n_max, const int* nk, const int* m, const int* colidx, int ncols, int* xmap,

@@ -1,4 +1,4 @@
-"""Every grid size with a compiled FFT plan, against the FP64 CPU oracle.
+"""Every grid size and line-FFT plan variant with compiled kernels, against the FP64 CPU oracle.
 
 Each supported N gets a small two-atom crystal (two bands, s/p projectors, a shifted
 k-point) whose cutoff sphere reaches about a quarter of the grid, so that every
@@ -24,6 +24,8 @@ ensure_library()
 import paper_2503_16225_gb300 as E  # noqa: E402
 
 GRID_N = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96)
+PLAN1_N = (16, 32, 36, 48, 64, 72)   # sizes with a second line plan
+CASES = [(n, 0) for n in GRID_N] + [(n, 1) for n in PLAN1_N]
 
 
 def grid_model(N):
@@ -38,12 +40,13 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
 
 
-@pytest.mark.parametrize("N", GRID_N)
-def test_grid_size(N):
+@pytest.mark.parametrize("N,plan", CASES)
+def test_grid_size(N, plan):
     cfg = grid_model(N)
     model = Model(cfg)
-    s = E.System(cfg)
+    s = E.System(cfg, E.eacg_default_params(fft_plan=plan))
     try:
+        assert E.eacg_get_plans(s.h) == (plan, plan)
         assert s.nk == model.nk
         rng = np.random.default_rng(N)
         Phi = [np.linalg.qr(rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2)))[0] for n in model.nk]
@@ -74,3 +77,19 @@ def test_grid_size(N):
                 assert np.all(h[k, :, model.nk[k]:] == 0)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("N", [24, 48])
+def test_autotune_picks_a_compiled_plan(N):
+    """fft_plan = -1 (default) times the plans at set-up: the choice is a compiled variant (0 where
+    the size has one plan), and a second system of the same shape reuses the cached choice."""
+    cfg = grid_model(N)
+    a = E.System(cfg)
+    b = E.System(cfg)
+    try:
+        pa, pb = E.eacg_get_plans(a.h), E.eacg_get_plans(b.h)
+        assert pa == pb
+        assert all(x in ((0, 1) if N in PLAN1_N else (0,)) for x in pa)
+    finally:
+        a.close()
+        b.close()
