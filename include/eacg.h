@@ -139,6 +139,15 @@ eacg_status eacg_get_dims(const eacg_system* sys, int* nk_host, int* n_max, int*
  * where the grid size has a single plan).  Implementation detail of the transforms; the
  * paper has no counterpart. */
 eacg_status eacg_get_plans(const eacg_system* sys, int* plan64, int* plan32);
+/* Tile variant (row groups per CTA: 1, 2 or 4) of the block-overlap kernel A^H B for an m x n
+ * result over L rows in the given block precision (0 complex128, 1 complex64): the fastest one
+ * timed when a system using that shape was set up, 4 for shapes never tuned.  Process-wide;
+ * the paper has no counterpart. */
+int eacg_gemm_tile(int m, int n, int L, int precision);
+/* Forces tile variant 1, 2 or 4 for every shape of every system in the process (results change
+ * only by rounding order); 0 returns to the tuned choices.  EACG_EINVAL for other values.  For
+ * tests and tuning experiments; the paper has no counterpart. */
+eacg_status eacg_force_gemm_tile(int groups);
 /* Integer triples m (G = 2 pi m / a) of the basis: m_dev int32 [K][n_max][3]
  * (rows >= n_k unspecified).  Canonical order: (mx, my, mz) lexicographic, mz fastest. */
 eacg_status eacg_get_basis(const eacg_system* sys, int* m_dev);

@@ -8,6 +8,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -55,13 +58,14 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // ----------------------------------------------------------------------------- A^H B
 // Templated on the block precision T (double or float): A and B are cplx<T>, the products
 // are accumulated in T within a chunk of rows, the chunk partials and the result are FP64.
-// A CTA computes one 16 x 16 tile of C over one chunk of CN_CHUNK rows with CN_GROUPS groups
-// of 256 threads, each group taking every CN_GROUPS-th stage of CN_SUB rows; the groups' tiles
-// are summed in a fixed order in shared memory (one partial per chunk, deterministic).
+// A CTA computes one 16 x 16 tile of C over one chunk of CN_CHUNK rows with G = 1, 2 or 4 groups
+// of 256 threads, each group taking every G-th stage of CN_SUB rows; the groups' tiles are
+// summed in a fixed order in shared memory (one partial per chunk, deterministic).  G is picked
+// per shape by dense_tune_cn (timed at system set-up, cached for the process); untuned shapes
+// use 4.
 constexpr int CN_TILE = 16;
 constexpr int CN_CHUNK = 1024;  // rows per partial
 constexpr int CN_SUB = 16;      // rows staged per step and group
-constexpr int CN_GROUPS = 4;
 
 size_t dense_cn_work(int K, int L, int m, int n) {
   const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
@@ -75,7 +79,7 @@ __device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
 }
 
-template <typename T>
+template <typename T, int CN_GROUPS>
 __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
     k_gemm_cn_partial(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
                       const cplx<T>* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
     __syncthreads();
   }
   // fixed-order sum of the groups' tiles
-  V* red = &sa[0][0][0];  // CN_GROUPS * 256 values fit in sa
+  V* red = &sa[0][0][0];  // CN_GROUPS * 256 values fit in sa (CN_SUB * (CN_TILE + 1) >= 256)
   red[g * CN_TILE * CN_TILE + t] = acc;
   __syncthreads();
   if (g == 0 && i0 + ti < m && j0 + tj < n) {
@@ -137,22 +141,112 @@ __global__ void k_gemm_cn_reduce(int m, int n, int nch, const double2* __restric
   }
 }
 
+namespace {
+std::mutex g_cn_mu;
+std::map<std::array<int, 5>, int> g_cn_groups;  // (device, element bytes, m, n, row chunks) buckets -> G
+
+int pow2_bucket(int x) {
+  int b = 16;
+  while (b < x && b < 4096) b <<= 1;
+  return b;
+}
+std::array<int, 5> cn_key(size_t es, int m, int n, int L) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return {dev, (int)es, pow2_bucket(m), pow2_bucket(n), std::min(8, (L + CN_CHUNK - 1) / CN_CHUNK)};
+}
+int g_cn_force = 0;  // 1, 2 or 4 overrides the tuned choice for every shape
+int cn_groups_for(size_t es, int m, int n, int L) {
+  std::lock_guard<std::mutex> lock(g_cn_mu);
+  if (g_cn_force) return g_cn_force;
+  auto it = g_cn_groups.find(cn_key(es, m, n, L));
+  return it == g_cn_groups.end() ? 4 : it->second;
+}
+}  // namespace
+
+template <typename T>
+static void gemm_cn_partial_launch(int G, dim3 g1, int L, int m, int n, const cplx<T>* A, size_t sA, int lda,
+                                   const cplx<T>* B, size_t sB, int ldb, double2* work, const int* kactive,
+                                   cudaStream_t st) {
+  if (G == 1)
+    k_gemm_cn_partial<T, 1><<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+  else if (G == 2)
+    k_gemm_cn_partial<T, 2><<<g1, CN_TILE * CN_TILE * 2, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+  else
+    k_gemm_cn_partial<T, 4><<<g1, CN_TILE * CN_TILE * 4, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+  count_launch();
+}
+
 template <typename T>
 static void gemm_cn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const cplx<T>* B, size_t sB,
                       int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
-                      const int* kactive, cudaStream_t st) {
+                      const int* kactive, cudaStream_t st, int G = 0) {
   if (K <= 0 || m <= 0 || n <= 0) return;
   const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
   const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
   dim3 g1(tiles, nch > 0 ? nch : 1, K);
-  if (nch > 0) {
-    k_gemm_cn_partial<T><<<g1, CN_TILE * CN_TILE * CN_GROUPS, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work,
-                                                                        kactive);
-    count_launch();
-  }
+  if (nch > 0)
+    gemm_cn_partial_launch<T>(G > 0 ? G : cn_groups_for(sizeof(cplx<T>), m, n, L), g1, L, m, n, A, sA, lda, B, sB,
+                              ldb, work, kactive, st);
   dim3 g2((m * n + 255) / 256, K);
   k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
   count_launch();
+}
+
+// Times G = 1, 2, 4 on the given operands (Kt k-points) and records the fastest for the shape
+// bucket of (element size, m, n, L); a bucket already tuned is kept.
+template <typename T>
+static void tune_cn_t(int Kt, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const cplx<T>* B,
+                      size_t sB, int ldb, double2* C, double2* work, cudaStream_t st) {
+  const auto key = cn_key(sizeof(cplx<T>), m, n, L);
+  {
+    std::lock_guard<std::mutex> lock(g_cn_mu);
+    if (g_cn_groups.count(key)) return;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  int best_g = 4;
+  float best = 0.f;
+  for (int G : {4, 2, 1}) {
+    gemm_cn_t<T>(Kt, L, m, n, A, sA, lda, B, sB, ldb, C, (size_t)m * n, m, one, zero, work, nullptr, st, G);
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 3; ++r)
+      gemm_cn_t<T>(Kt, L, m, n, A, sA, lda, B, sB, ldb, C, (size_t)m * n, m, one, zero, work, nullptr, st, G);
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (G == 4 || ms < best) {
+      best = ms;
+      best_g = G;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::lock_guard<std::mutex> lock(g_cn_mu);
+  g_cn_groups.emplace(key, best_g);
+}
+
+void dense_tune_cn(int Kt, int L, int m, int n, int prec, const void* A, size_t sA, int lda, const void* B,
+                   size_t sB, int ldb, double2* C, double2* work, cudaStream_t st) {
+  if (Kt <= 0 || m <= 0 || n <= 0 || L <= 0) return;
+  if (prec)
+    tune_cn_t<float>(Kt, L, m, n, (const float2*)A, sA, lda, (const float2*)B, sB, ldb, C, work, st);
+  else
+    tune_cn_t<double>(Kt, L, m, n, (const double2*)A, sA, lda, (const double2*)B, sB, ldb, C, work, st);
+}
+
+int dense_cn_groups(int m, int n, int L, int prec) {
+  return cn_groups_for(prec ? sizeof(float2) : sizeof(double2), m, n, L);
+}
+
+int dense_cn_force(int groups) {
+  if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return -1;
+  std::lock_guard<std::mutex> lock(g_cn_mu);
+  g_cn_force = groups;
+  return 0;
 }
 
 void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,

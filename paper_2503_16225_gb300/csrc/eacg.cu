@@ -1523,6 +1523,42 @@ static eacg_status autotune_plans(eacg_system* s) {
   return EACG_OK;
 }
 
+// ---- autotune of the A^H B tiles: the shapes this system uses (Gram p x p, projector overlaps
+// nproj x p, the FOM's q x p for q up to 16 p), both block precisions, on temporary operands
+// of at most 8 k-points (the choice is recorded per shape bucket for the whole process).
+static eacg_status autotune_gemm(eacg_system* s) {
+  const int p = s->p, nm = s->n_max, Kt = std::min(s->K, 8);
+  const int mmax = std::min(16 * p, 1024);
+  std::vector<int> ms = {p, 2 * p, 4 * p, 8 * p, 16 * p};
+  if (s->nproj > 0) ms.push_back(s->nproj);
+  double2 *A = nullptr, *C = nullptr, *W = nullptr;
+  const size_t na = (size_t)Kt * std::max(mmax, s->nproj) * nm;
+  if (cudaMalloc(&A, sizeof(double2) * na) != cudaSuccess) {
+    cudaGetLastError();
+    return EACG_OK;  // tuning is optional: untuned shapes use the default tile
+  }
+  const int mm = std::max(mmax, s->nproj);
+  const size_t nc = (size_t)Kt * mm * p, nw = dense_cn_work(Kt, nm, mm, p);
+  if (cudaMalloc(&C, sizeof(double2) * nc) != cudaSuccess || cudaMalloc(&W, sizeof(double2) * nw) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(A);
+    if (C) cudaFree(C);
+    return EACG_OK;
+  }
+  CK(cudaMemsetAsync(A, 0, sizeof(double2) * na, s->st));
+  for (int prec = 0; prec < 2; ++prec)
+    for (int m : ms) {
+      if (m > mm) continue;
+      dense_tune_cn(Kt, nm, m, p, prec, A, (size_t)m * nm, nm, A, (size_t)m * nm, nm, C, W, s->st);
+    }
+  cudaStreamSynchronize(s->st);
+  cudaFree(A);
+  cudaFree(C);
+  cudaFree(W);
+  CKL(s);
+  return EACG_OK;
+}
+
 extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params* prm, void* stream,
                                           eacg_system** out) {
   if (!out) return EACG_EINVAL;
@@ -1616,6 +1652,7 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   if ((st = build_potential_and_projectors(s)) != EACG_OK) return fail(st);
   if ((st = alloc_work(s)) != EACG_OK) return fail(st);
   if ((st = autotune_plans(s)) != EACG_OK) return fail(st);
+  if ((st = autotune_gemm(s)) != EACG_OK) return fail(st);
   if (cudaStreamSynchronize(s->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     s->err = "set-up kernels failed";
     return fail(EACG_ECUDA);
@@ -1640,6 +1677,14 @@ extern "C" eacg_status eacg_get_plans(const eacg_system* s, int* plan64, int* pl
   if (plan64) *plan64 = s->g.plan64;
   if (plan32) *plan32 = s->g.plan32;
   return EACG_OK;
+}
+
+extern "C" int eacg_gemm_tile(int m, int n, int L, int precision) {
+  return dense_cn_groups(m, n, L, precision ? 1 : 0);
+}
+
+extern "C" eacg_status eacg_force_gemm_tile(int groups) {
+  return dense_cn_force(groups) == 0 ? EACG_OK : EACG_EINVAL;
 }
 
 extern "C" const char* eacg_last_error(const eacg_system* s) { return s ? s->err.c_str() : "null system"; }

@@ -79,6 +79,14 @@ void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int 
 void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                    cudaStream_t st);
+// Tile autotune of the A^H B kernel: times its row-group variants on these operands (Kt
+// k-points, prec 0 complex128 / 1 complex64 A and B) and records the fastest for the shape bucket
+// of (m, n, L) for the whole process (kept if already tuned).  C: Kt * m * n, work:
+// dense_cn_work(Kt, L, m, n).  dense_cn_groups: the variant in use for a shape (4 if untuned).
+void dense_tune_cn(int Kt, int L, int m, int n, int prec, const void* A, size_t sA, int lda, const void* B,
+                   size_t sB, int ldb, double2* C, double2* work, cudaStream_t st);
+int dense_cn_groups(int m, int n, int L, int prec);
+int dense_cn_force(int groups);  // 1, 2, 4 forces that variant for every shape; 0 back to tuned
 // FP32-block variants: A, B (cn) / A, C (nn) complex64, FP32 accumulation; small factors and
 // the cn result stay FP64.
 void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const float2* B, size_t sB,
