@@ -30,6 +30,10 @@ L2_BYTES = 129 * 2 ** 20
 # 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (a probe measured 1.196 TFLOP/s at ~2.0 GHz)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of single-kernel
+# slots, from the ncu captures summarised in profiles/ (diamond 4x4x4 workload, 1024 bands per
+# launch); a kernel changed since its capture must be removed from this table.
+NCU_TRAFFIC_BYTES = {"plane_h_f64": 394.4e6, "plane_h_f32": 169.7e6}
 # profile slots that time exactly one kernel (the roofline is reported for the top one)
 SINGLE_KERNEL_SLOTS = ("plane_h", "plane_rho", "xpass_inv", "xpass_fwd", "xpass_rho", "fom_solve")
 
@@ -392,7 +396,9 @@ def run_gpu(args):
         else:
             peak, pk = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
         roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "peak_kind": pk,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC_BYTES.get(top) if args.workload == "diamond_k444" else None,
+                "traffic_unit": "bytes per launch (ncu)", "avg_launch_ms": avg_ms,
                 "launches": n, "hbm_GBps_algorithmic": (st["bytes"] / n) / (avg_ms / 1e3) / 1e9,
                 "hbm_peak_GBps": hbm, "hbm_peak_kind": peak_kind}
     apps = sum(r.h_band_apps for r in results)

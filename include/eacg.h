@@ -87,7 +87,8 @@ typedef struct {
   int max_ls;         /* 30  */
   int precision;      /* 0 FP64, 1 mixed */
   int graphs;         /* 1: the FOM's block H application is replayed as a CUDA graph per system
-                       * (captured on its second call with the same buffers); 0: direct launches.
+                       * (captured on its second call with the same buffers; needs a stream of
+                       * the system's own, not the legacy default stream); 0: direct launches.
                        * Results are identical either way.  Default 1 */
   int fft_plan;       /* line-FFT plan of the transforms: -1 picks the faster of the compiled
                        * plans for this grid by timing both on the system at set-up (autotune);
@@ -139,6 +140,11 @@ eacg_status eacg_get_dims(const eacg_system* sys, int* nk_host, int* n_max, int*
  * where the grid size has a single plan).  Implementation detail of the transforms; the
  * paper has no counterpart. */
 eacg_status eacg_get_plans(const eacg_system* sys, int* plan64, int* plan32);
+/* Number of CUDA-graph replays of the FOM's block H application on this system so far (see
+ * eacg_params.graphs).  Graphs need a stream of the system's own: on the legacy default stream
+ * (stream NULL) capture is impossible and the system launches directly.  The paper has no
+ * counterpart. */
+long long eacg_graph_launches(const eacg_system* sys);
 /* Tile variant (row groups per CTA: 1, 2 or 4) of the block-overlap kernel A^H B for an m x n
  * result over L rows in the given block precision (0 complex128, 1 complex64): the fastest one
  * timed when a system using that shape was set up, 4 for shapes never tuned.  Process-wide;

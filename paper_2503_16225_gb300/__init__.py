@@ -16,7 +16,7 @@ from .build import LIB
 __all__ = [
     "EacgModel", "EacgParams", "EacgStepInfo", "EacgResult", "EacgError", "lib", "model_from_config",
     "eacg_default_params", "eacg_bytes_required", "eacg_create_system", "eacg_destroy", "eacg_last_error",
-    "eacg_get_dims", "eacg_get_plans", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
+    "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
     "System", "STATUS",
@@ -84,6 +84,7 @@ def _load():
         "eacg_last_error": (ctypes.c_char_p, [vp]),
         "eacg_get_dims": (ctypes.c_int, [vp, _ip, _ip, _ip]),
         "eacg_get_plans": (ctypes.c_int, [vp, _ip, _ip]),
+        "eacg_graph_launches": (ctypes.c_longlong, [vp]),
         "eacg_gemm_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "eacg_force_gemm_tile": (ctypes.c_int, [ctypes.c_int]),
         "eacg_get_basis": (ctypes.c_int, [vp, vp]),
@@ -213,6 +214,10 @@ def eacg_get_plans(sys):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(sys, lib.eacg_get_plans(sys, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def eacg_graph_launches(sys):
+    return int(lib.eacg_graph_launches(sys))
 
 
 def eacg_gemm_tile(m, n, L, precision):

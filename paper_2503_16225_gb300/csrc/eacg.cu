@@ -133,6 +133,7 @@ struct eacg_system {
   };
   HGraph hg[2];
   HGraph* cap = nullptr;              // graph being captured (profile events go to it)
+  long long graph_launches = 0;       // replays of captured graphs
   bool graphs_off = false;            // set when capture is not possible on this system
 };
 
@@ -185,10 +186,18 @@ void eacg::ensure_smem(const void* func, size_t bytes) {
 // captured the events always go into the graph (they become event-record nodes whose times
 // are read back after each profiled replay).
 namespace {
-cudaEvent_t cap_event(eacg_system* s) {
+cudaEvent_t cap_event(eacg_system*) {
   cudaEvent_t e = nullptr;
   cudaEventCreate(&e);
   return e;
+}
+// While capturing, an event record must be marked external to become a node whose time can be
+// read after each replay (a plain record would only order captured work).
+void record_event(eacg_system* s, cudaEvent_t e) {
+  if (s->cap)
+    cudaEventRecordWithFlags(e, s->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s->st);
 }
 }  // namespace
 #define PROF_RUN(slot, bytes_, flops_, units_, ...)                                       \
@@ -197,12 +206,12 @@ cudaEvent_t cap_event(eacg_system* s) {
     const bool rec_ = s->prof_on || s->cap;                                       \
     if (rec_) {                                                                   \
       a_ = s->cap ? cap_event(s) : prof_event(s);                                 \
-      cudaEventRecord(a_, s->st);                                                 \
+      record_event(s, a_);                                                        \
     }                                                                             \
     __VA_ARGS__;                                                                  \
     if (rec_) {                                                                   \
       cudaEvent_t b_ = s->cap ? cap_event(s) : prof_event(s);                     \
-      cudaEventRecord(b_, s->st);                                                 \
+      record_event(s, b_);                                                        \
       (s->cap ? s->cap->recs : s->prof)                                           \
           .push_back({(slot), a_, b_, (double)(bytes_), (double)(flops_), (double)(units_)}); \
     }                                                                             \
@@ -842,7 +851,10 @@ static void hg_resolve(eacg_system* s, eacg_system::HGraph& g) {
   for (const auto& r : g.recs) {
     float ms = 0.f;
     cudaEventSynchronize(r.b);
-    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) s->prof_ms.push_back({r.slot, ms, r.bytes, r.flops, r.units});
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+      s->prof_ms.push_back({r.slot, ms, r.bytes, r.flops, r.units});
+    else
+      cudaGetLastError();  // a time that cannot be read is dropped, not reported as a launch error
   }
   g.pending = false;
 }
@@ -853,6 +865,7 @@ static eacg_status apply_H_fom(eacg_system* s, const V* in, V* out, const int* k
   if (!s->prm.graphs || s->graphs_off) return apply_H_t(s, in, out, ka);
   const bool same = g.in == in && g.out == out && g.ka == ka && g.cnw == s->cn_work;
   if (!same) {
+    hg_resolve(s, g);  // keep the last replay's profile records
     hg_release(g);
     g.in = in;
     g.out = out;
@@ -899,6 +912,7 @@ static eacg_status apply_H_fom(eacg_system* s, const V* in, V* out, const int* k
   }
   hg_resolve(s, g);
   CK(cudaGraphLaunch(g.exec, s->st));
+  ++s->graph_launches;
   count_launches(g.kernels);
   s->h_apps += (long long)s->K * s->p;
   if (s->prof_on) g.pending = true;
@@ -1678,6 +1692,8 @@ extern "C" eacg_status eacg_get_plans(const eacg_system* s, int* plan64, int* pl
   if (plan32) *plan32 = s->g.plan32;
   return EACG_OK;
 }
+
+extern "C" long long eacg_graph_launches(const eacg_system* s) { return s ? s->graph_launches : -1; }
 
 extern "C" int eacg_gemm_tile(int m, int n, int L, int precision) {
   return dense_cn_groups(m, n, L, precision ? 1 : 0);

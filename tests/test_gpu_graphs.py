@@ -1,6 +1,8 @@
-"""CUDA-graph replay of the FOM's block H application: results, per-slot profile counts and
-the launch counter must be the same as with direct launches (the kernels and their order are
-identical; every reduction has a fixed order, so the comparison is bitwise)."""
+"""CUDA-graph replay of the FOM's block H application: results, per-slot profile counts (with
+profiling on, so the captured event records are read back) and the launch counter must be the
+same as with direct launches (the kernels and their order are identical; every reduction has a
+fixed order, so the comparison is bitwise).  Graphs need a stream of the system's own, so each
+system here gets one."""
 import numpy as np
 import pytest
 
@@ -18,23 +20,31 @@ import paper_2503_16225_gb300 as E  # noqa: E402
 
 
 def _gradient(cfg, precision, graphs):
-    s = E.System(cfg, E.eacg_default_params(precision=precision, graphs=graphs))
+    st = torch.cuda.Stream()
+    s = E.System(cfg, E.eacg_default_params(precision=precision, graphs=graphs), stream=st.cuda_stream)
+    torch.cuda.synchronize()
     try:
         raw = synth.raw_coefficients(cfg["seed"], s.nk, s.p, s.n_max)
-        E.eacg_set_psi(s.h, torch.from_numpy(raw).cuda())
+        psi = torch.from_numpy(raw).cuda()
         phi = s.block()
+        torch.cuda.synchronize()  # tensors made on torch's stream, used on the system's
+        E.eacg_set_psi(s.h, psi)
         E.eacg_get_psi(s.h, phi)
         E.eacg_density(s.h, phi, None, 0)
         outs, its, profs = [], [], []
         for _ in range(2):  # the second call replays graphs captured during the first
             g = s.block()
+            torch.cuda.synchronize()
             E.eacg_profile_enable(s.h, 1)
             n0 = E.eacg_launch_count()
             its.append(E.eacg_ea_gradient(s.h, phi, g, s.K, precision))
-            torch.cuda.synchronize()
+            st.synchronize()
             profs.append((E.eacg_launch_count() - n0,
                           {k: v["launches"] for k, v in E.eacg_profile_read(s.h).items()}))
+            st.synchronize()
             outs.append(g.cpu().numpy())
+        replays = E.eacg_graph_launches(s.h)
+        assert (replays > 0) if graphs else (replays == 0)
         return outs, its, profs
     finally:
         s.close()
