@@ -26,6 +26,15 @@ Readings where the paper is silent, ambiguous or inconsistent:
     energy-adaptive gradient for that iteration; if <r_new, eta_new> >= 0 the
     direction restarts from -g_new;
   * per-k FOM solves stop independently; transport scaling is omitted (Sec. 5.2).
+
+EARGD (the paper's comparison method, Sec. 5.2 list of methods, which points to another
+paper for its details) is read as: the same warm-up, then eta = -g_EA with the alternating
+Barzilai-Borwein step (odd energy-adaptive steps <s,s>/|<s,y>|, even ones |<s,y>|/<y,y>,
+s = tau T(eta), y = g_new - T(g), clamped to [1e-10, 1e10], 1 at the first step) and
+Zhang-Hager non-monotone backtracking: tau <- gamma tau until
+f(tau) <= C + nm_delta tau f'(0), with C_0 = E_0, Q_0 = 1,
+Q_{k+1} = nm_rho Q_k + 1, C_{k+1} = (nm_rho Q_k C_k + E_{k+1}) / Q_{k+1}
+(nm_rho = 0.85, nm_delta = 1e-4).
 """
 from __future__ import annotations
 
@@ -53,6 +62,9 @@ class Params:
     max_warm: int = 100
     max_fom: int = 50
     max_ls: int = 30
+    method: int = 0          # 0: EARCG (Algorithm 3); 1: EARGD (gradient descent, BB step)
+    nm_rho: float = 0.85     # EARGD non-monotone averaging
+    nm_delta: float = 1e-4   # EARGD sufficient decrease against the reference value
 
 
 @dataclass
@@ -211,6 +223,30 @@ def secant_step(model, base: Point, eta, tau0, prm: Params, counter):
     return modified_secant(Trial(model, base, eta, counter), f0, df0, tau0, prm)
 
 
+def nonmonotone_step(model, base: Point, eta, tau0, C, prm: Params, counter):
+    """EARGD backtracking: tau0 gamma^j for the first j with f(tau) <= C + nm_delta tau f'(0)."""
+    df0 = 2.0 * model.occ * pairing(model, base.R, eta)
+    trial = Trial(model, base, eta, counter)
+    t = tau0
+    for n in range(1, prm.max_ls + 1):
+        pt, f, _ = trial(t)
+        if f <= C + prm.nm_delta * t * df0:
+            return t, pt, n
+        t *= prm.gamma
+    raise LineSearchError(f"non-monotone backtracking: no acceptable step in {prm.max_ls} trials")
+
+
+def bb_step(model, s, y, odd: bool) -> float:
+    """Alternating Barzilai-Borwein step in the pairing <.,.> (odd: BB1, even: BB2), clamped."""
+    ss = pairing(model, s, s)
+    sy = abs(pairing(model, s, y))
+    yy = pairing(model, y, y)
+    t = ss / sy if odd else sy / yy
+    if not math.isfinite(t) or t <= 0:
+        return 1.0
+    return min(max(t, 1e-10), 1e10)
+
+
 def beta_fr_prp(r_new_g_new: float, r_old_g_old: float, r_new_Tg_old: float) -> float:
     """Hybrid FR-PRP parameter max{0, min{beta_FR, beta_PRP}} in residual pairings (Sec. 3.4)."""
     bfr = r_new_g_new / r_old_g_old
@@ -271,12 +307,21 @@ def solve(model: Model, Psi0, prm: Params | None = None, warm=True, callback=Non
     rg = pairing(model, pt.R, g)
     hist.append(dict(it=0, E=pt.E, rnorm=pt.rnorm, tau=0.0, beta=0.0, phase=phase, gkind=gkind))
     status = "converged" if pt.rnorm <= prm.res_tol else "maxiter"
+    gd = prm.method == 1
+    C, Q, ea_it = pt.E, 1.0, 0     # EARGD non-monotone reference and energy-adaptive step count
     while pt.rnorm > prm.res_tol:
         if it >= prm.max_outer:
             status = "maxiter"
             break
         try:
-            tau, new, trials = secant_step(model, pt, eta, tau, prm, counter)
+            if gd and phase == "ea":
+                tau, new, trials = nonmonotone_step(model, pt, eta, tau, C, prm, counter)
+                Qn = prm.nm_rho * Q + 1.0
+                C = (prm.nm_rho * Q * C + new.E) / Qn
+                Q = Qn
+                ea_it += 1
+            else:
+                tau, new, trials = secant_step(model, pt, eta, tau, prm, counter)
         except LineSearchError:
             status = "linesearch"
             break
@@ -298,6 +343,12 @@ def solve(model: Model, Psi0, prm: Params | None = None, warm=True, callback=Non
         if switch:
             beta = 0.0
             tau = 1.0
+            C, Q, ea_it = pt.E, 1.0, 0
+        elif gd and phase == "ea":
+            beta = 0.0
+            s_k = [tau * x for x in Teta]
+            y_k = [gn[k] - Tg[k] for k in range(model.K)]
+            tau = bb_step(model, s_k, y_k, ea_it % 2 == 1)
         else:
             beta = beta_fr_prp(rgn, rg, pairing(model, pt.R, Tg))
         eta = [-gn[k] + beta * Teta[k] for k in range(model.K)]

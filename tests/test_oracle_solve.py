@@ -110,3 +110,42 @@ def test_remark4_shifted_inverse_overlap_is_quadratic_in_the_residual(small_nonl
     (r1, d1), (r2, d2) = out
     ratio = math.log(d1 / d2) / math.log(r1 / r2)
     assert 1.7 < ratio < 2.3
+
+
+# ----------------------------------------------------------------------------- EARGD
+def test_bb_step_closed_form():
+    """y = c s: both Barzilai-Borwein quotients equal 1/c (the secant of a c-scaled identity)."""
+    m = Model(small(nb=2))
+    rng = np.random.default_rng(2)
+    s = [rng.standard_normal((n, m.p)) + 1j * rng.standard_normal((n, m.p)) for n in m.nk]
+    for c in (0.5, 3.0):
+        y = [c * x for x in s]
+        assert abs(earcg.bb_step(m, s, y, True) - 1.0 / c) < 1e-12
+        assert abs(earcg.bb_step(m, s, y, False) - 1.0 / c) < 1e-12
+
+
+def test_eargd_linear_model_matches_dense_diagonalisation():
+    """EARGD reaches the same minimiser as the explicit eigenvalue problem."""
+    cfg = small(a=7.0, N=16, ecut=3.0, nb=2, nproj=4, hartree=0, xc=0, kgrid=(2, 1, 1))
+    m = Model(cfg)
+    res = earcg.solve(m, start(m), earcg.Params(method=1))
+    assert res.status == "converged"
+    want = sum(m.kw[k] * m.occ * np.linalg.eigvalsh(m.dense_H(k, m.vloc))[:m.p].sum() for k in range(m.K))
+    assert abs(res.E - want) < 1e-10 * max(1.0, abs(want))
+
+
+def test_eargd_monotone_limit_and_agreement_with_earcg(two_atom_solution):
+    """nm_rho = 0 makes the reference value the current energy: the energy-adaptive phase then
+    decreases monotonically; either way EARGD ends at EARCG's energy (unique minimiser)."""
+    m, ref = two_atom_solution
+    cfg = synth.config_two_atom(1)
+    raw = synth.raw_coefficients(cfg["seed"], m.nk, m.p)
+    psi0 = [raw[k, :, :m.nk[k]].T.copy() for k in range(m.K)]
+    for rho in (0.85, 0.0):
+        res = earcg.solve(m, psi0, earcg.Params(method=1, nm_rho=rho))
+        assert res.status == "converged"
+        assert abs(res.E - ref.E) < 1e-9
+        if rho == 0.0:
+            E = [h["E"] for h in res.history if h["phase"] == "ea"]
+            for e0, e1 in zip(E, E[1:]):
+                assert e1 <= e0 + 1e-12 * abs(e0)
