@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--op", default="solve", choices=["solve", "apply_h", "density", "ea_gradient"],
                     help="apply_h / density / ea_gradient: time a few calls of one operation on the "
                          "workload's start point instead of solves (short runs under a profiler)")
+    ap.add_argument("--method", default="earcg", choices=["earcg", "eargd"],
+                    help="eargd: the paper's gradient-descent comparator (BB step, non-monotone backtracking)")
     ap.add_argument("--concurrent", type=int, default=4,
                     help="resident systems solved concurrently (own stream and host thread each); "
                          "value = whole-job served solves/s")
@@ -235,7 +237,8 @@ def run_gpu(args):
 
     cfg = workload(args.workload)
     prec = 1 if args.precision == "mixed" else 0
-    params = E.eacg_default_params(precision=prec)
+    method = 1 if args.method == "eargd" else 0
+    params = E.eacg_default_params(precision=prec, method=method)
     C = max(1, args.concurrent)
     # C resident systems of the workload, each with its own stream and host thread (served)
     systems = []
@@ -356,7 +359,7 @@ def run_gpu(args):
     # ---- plain FP64, one system at a time (the comparison the served number is quoted against)
     fp64_ref = None
     if prec == 1 and not args.no_extras and not args.no_fp64_ref:
-        p64 = E.eacg_default_params(precision=0)
+        p64 = E.eacg_default_params(precision=0, method=method)
         s64 = E.System(cfg, p64)
         for it in range(2):  # one untimed solve, then one timed
             E.eacg_set_psi(s64.h, psi0)
@@ -405,12 +408,13 @@ def run_gpu(args):
     hpsi_gbs = (apps * bytes_per_band) / (total_ms / 1e3) / 1e9
 
     line = {
-        "metric": "served eARCG solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)",
+        "metric": ("served eARCG solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)" if method == 0 else
+                   "served EARGD solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)"),
         "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if prec else "f64", "data": "synthetic",
         "config": {"workload": cfg["name"], "kpoints": len(cfg["kweight"]), "bands": cfg["nbands"],
-                   "grid": cfg["N"], "ecut": cfg["ecut"], "precision": args.precision,
+                   "grid": cfg["N"], "ecut": cfg["ecut"], "precision": args.precision, "method": args.method,
                    "parallelism": f"replicas{world}", "concurrent_systems": C,
                    "l2": "flushed between rounds of concurrent solves (256 MiB write)"},
         "time_to_1e8_ms": {"p50": statistics.median(latencies), "p99": max(latencies), "all": latencies},

@@ -94,6 +94,10 @@ typedef struct {
                        * plans for this grid by timing both on the system at set-up (autotune);
                        * 0 or 1 forces a plan (one that does not exist for N falls back to 0).
                        * Default -1 */
+  int method;         /* 0: EARCG (Algorithm 3); 1: EARGD, the paper's gradient-descent comparator
+                       * (same warm-up; then eta = -G with an alternating Barzilai-Borwein step
+                       * and Zhang-Hager non-monotone backtracking, rho 0.85, delta 1e-4).
+                       * Default 0 */
 } eacg_params;
 
 typedef struct {

@@ -328,13 +328,14 @@ def solve(model: Model, Psi0, prm: Params | None = None, warm=True, callback=Non
         it += 1
         if phase == "warm":
             warm_it += 1
+        tau_acc = tau  # the accepted step ("tau" in the history is the next step's start)
         Teta, Tg = transports(pt, new, eta, g, tau, model)
         switch = phase == "warm" and (new.rnorm <= prm.warm_res or warm_it >= prm.max_warm)
         if switch:
             phase = "ea"
         pt = new
         if pt.rnorm <= prm.res_tol:
-            hist.append(dict(it=it, E=pt.E, rnorm=pt.rnorm, tau=tau, beta=0.0, phase=phase,
+            hist.append(dict(it=it, E=pt.E, rnorm=pt.rnorm, tau=tau, tau_acc=tau_acc, beta=0.0, phase=phase,
                              gkind=gkind, trials=trials))
             status = "converged"
             break
@@ -356,7 +357,7 @@ def solve(model: Model, Psi0, prm: Params | None = None, warm=True, callback=Non
             eta = [-x for x in gn]
             beta = 0.0
         g, rg = gn, rgn
-        hist.append(dict(it=it, E=pt.E, rnorm=pt.rnorm, tau=tau, beta=beta, phase=phase,
+        hist.append(dict(it=it, E=pt.E, rnorm=pt.rnorm, tau=tau, tau_acc=tau_acc, beta=beta, phase=phase,
                          gkind=gkind, trials=trials))
         if callback is not None:
             callback(hist[-1])

@@ -824,15 +824,22 @@ int dense_dot(int K, size_t len, const double2* V, const double2* W, const doubl
   count_launch();
   return K * DOT_BLOCKS_PER_K;
 }
-__global__ void k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += p[i];
-    *out = s;
+// Sum of n partials by one CTA of 256 threads: thread t adds p[t], p[t + 256], ... in order,
+// then a fixed shared-memory tree (deterministic).
+__global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+    if (threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = sh[0];
 }
 void dense_sum_partials(const double* partials, int n, double* out, cudaStream_t st) {
-  k_sum_partials<<<1, 32, 0, st>>>(partials, n, out);
+  k_sum_partials<<<1, 256, 0, st>>>(partials, n, out);
   count_launch();
 }
 

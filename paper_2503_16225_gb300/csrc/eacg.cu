@@ -99,6 +99,8 @@ struct eacg_system {
   // ---- iteration state
   int fresh = 1, have_psi = 0, phase = 0, iter = 0, warm_iter = 0, cur_prec = 0;
   double E = 0, rnorm = 0, tau = 1, rg = 0;
+  double nm_C = 0, nm_Q = 1;  // EARGD: non-monotone reference value and its weight
+  int ea_steps = 0;           // EARGD: energy-adaptive steps taken (alternates the BB formula)
   double eterms[5] = {0, 0, 0, 0, 0};
   long long h_apps = 0;
   int last_fom_max = 0;
@@ -305,7 +307,7 @@ static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::st
     *why = "grid size N must be one of 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96";
     return EACG_EUNSUPPORTED;
   }
-  if (prm && (!(prm->mu > 0) || prm->max_ls < 1 || prm->max_fom < 1)) {
+  if (prm && (!(prm->mu > 0) || prm->max_ls < 1 || prm->max_fom < 1 || prm->method < 0 || prm->method > 1)) {
     *why = "invalid parameters";
     return EACG_EINVAL;
   }
@@ -330,6 +332,7 @@ extern "C" void eacg_default_params(eacg_params* prm) {
   prm->precision = 0;
   prm->graphs = 1;
   prm->fft_plan = -1;
+  prm->method = 0;
 }
 
 static double sphere_volume_estimate(const eacg_model* m) {
@@ -1207,6 +1210,27 @@ static eacg_status trial(eacg_system* s, double t, int prec, TrialOut* out) {
   return EACG_OK;
 }
 
+// EARGD (the paper's gradient-descent comparator; details are the readings listed with the
+// library): tau0 gamma^j for the first j with f(tau) <= C + NM_DELTA tau f'(0), C the
+// Zhang-Hager reference value.  The accepted point is the last trial evaluated.
+constexpr double NM_RHO = 0.85, NM_DELTA = 1e-4;
+static eacg_status trial(eacg_system* s, double t, int prec, TrialOut* out);
+static eacg_status nonmonotone(eacg_system* s, double df0, double tau0, int prec, double* tau_out, TrialOut* acc,
+                               int* trials_out) {
+  double t = tau0;
+  for (int n = 1; n <= s->prm.max_ls; ++n) {
+    TRY(trial(s, t, prec, acc));
+    if (acc->ev.E <= s->nm_C + NM_DELTA * t * df0) {
+      *tau_out = t;
+      *trials_out = n;
+      return EACG_OK;
+    }
+    t *= s->prm.gamma;
+  }
+  s->err = "non-monotone backtracking: no acceptable step within max_ls trials";
+  return EACG_ELINESEARCH;
+}
+
 // Algorithm 2 (with the readings stated in the header): returns the accepted step in *tau;
 // the accepted point is the last trial evaluated.
 static eacg_status modified_secant(eacg_system* s, double f0, double df0, double tau0, int prec, double* tau_out,
@@ -1360,6 +1384,9 @@ static eacg_status start_iteration(eacg_system* s) {
   s->iter = 0;
   s->warm_iter = 0;
   s->tau = 1.0;
+  s->nm_C = s->E;
+  s->nm_Q = 1.0;
+  s->ea_steps = 0;
   s->fresh = 0;
   if (s->rnorm <= s->prm.res_tol) return EACG_OK;
   int kind;
@@ -1399,14 +1426,25 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
   double tau = 0;
   TrialOut acc;
   int trials = 0;
-  eacg_status st = modified_secant(s, s->E, df0, s->tau, prec, &tau, &acc, &trials);
+  const bool gd = s->prm.method == 1 && s->phase == 1;  // EARGD step
+  auto search = [&]() {
+    return gd ? nonmonotone(s, df0, s->tau, prec, &tau, &acc, &trials)
+              : modified_secant(s, s->E, df0, s->tau, prec, &tau, &acc, &trials);
+  };
+  eacg_status st = search();
   if (st == EACG_ELINESEARCH && prec == 1) {
     // FP32 transforms can no longer resolve the energy decrease: continue in FP64
     s->prm.switch_res = std::max(s->prm.switch_res, 2.0 * s->rnorm);
     prec = 0;
-    st = modified_secant(s, s->E, df0, s->tau, prec, &tau, &acc, &trials);
+    st = search();
   }
   if (st != EACG_OK) return st;
+  if (gd) {
+    const double Qn = NM_RHO * s->nm_Q + 1.0;
+    s->nm_C = (NM_RHO * s->nm_Q * s->nm_C + acc.ev.E) / Qn;
+    s->nm_Q = Qn;
+    s->ea_steps += 1;
+  }
   s->iter += 1;
   if (s->phase == 0) s->warm_iter += 1;
   // transport of the old g (needs old Phi, eta, g and the accepted trial's S)
@@ -1428,6 +1466,21 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
     if (sw) {
       beta = 0.0;
       s->tau = 1.0;
+      s->nm_C = s->E;
+      s->nm_Q = 1.0;
+      s->ea_steps = 0;
+    } else if (gd) {
+      // alternating Barzilai-Borwein step from s = tau T(eta), y = g_new - T(g_old)
+      beta = 0.0;
+      dense_axpby(s->blk, ONE, s->gv, MONE, s->tg, s->tmp2, s->st);
+      pairing_dev(s, s->teta, s->teta, 0, true);
+      pairing_dev(s, s->teta, s->tmp2, 1, true);
+      pairing_dev(s, s->tmp2, s->tmp2, 2, true);
+      TRY(sync_read(s, 3));
+      const double ss = tau * tau * s->h_out[0], sy = std::fabs(tau * s->h_out[1]), yy = s->h_out[2];
+      double t = (s->ea_steps % 2 == 1) ? ss / sy : sy / yy;
+      if (!std::isfinite(t) || t <= 0.0) t = 1.0;
+      s->tau = std::min(std::max(t, 1e-10), 1e10);
     } else {
       pairing_dev(s, s->res, s->tg, 0, true);
       TRY(sync_read(s, 1));
