@@ -107,44 +107,97 @@ __device__ __forceinline__ V twiddle(V x, int e, const V* tw) {
   return cmul(x, w);
 }
 
+// First factor R of a register DFT of length M = R Q: a base radix coprime to Q when one
+// exists (prime-factor split, no twiddles), else 4 or 2 (Cooley-Tukey split).
+template <int A, int B>
+struct Gcd {
+  static constexpr int value = Gcd<B, A % B>::value;
+};
+template <int A>
+struct Gcd<A, 0> {
+  static constexpr int value = A;
+};
 template <int M>
 struct FirstRadix {
-  static constexpr int R = (M % 4 == 0) ? 4 : (M % 2 == 0) ? 2 : (M % 3 == 0) ? 3 : 5;
+  static constexpr int R = (M % 4 == 0 && Gcd<4, M / 4>::value == 1)   ? 4
+                           : (M % 3 == 0 && Gcd<3, M / 3>::value == 1) ? 3
+                           : (M % 5 == 0 && Gcd<5, M / 5>::value == 1) ? 5
+                           : (M % 4 == 0)                               ? 4
+                           : (M % 2 == 0)                               ? 2
+                           : (M % 3 == 0)                               ? 3
+                                                                        : 5;
+};
+// X^{-1} mod Mod for gcd(X, Mod) = 1 (Mod <= 8 here)
+template <int X, int Mod, int T = 1>
+struct ModInv {
+  static constexpr int value = ((X % Mod) * T) % Mod == 1 % Mod ? T : ModInv<X, Mod, T + 1>::value;
+};
+template <int X, int Mod>
+struct ModInv<X, Mod, 9> {
+  static constexpr int value = 0;
 };
 
 // In-register DFT of length M (M divides N) on a[0..M), natural order in and out.
-// M = R Q with m = r + R q, k = u + Q s: A[u + Q s] = sum_r w_R^{r s} w_M^{r u} (DFT_Q a[r + R .])[u].
+// Coprime M = R Q (prime-factor algorithm): with n = (Q r + R q) mod M and
+// k = (Q (Q^-1 mod R) k_r + R (R^-1 mod Q) k_q) mod M the DFT is an R x Q two-dimensional DFT
+// without twiddles.  Otherwise M = R Q with m = r + R q, k = u + Q s (Cooley-Tukey):
+// A[u + Q s] = sum_r w_R^{r s} w_M^{r u} (DFT_Q a[r + R .])[u].
 template <int M, int N, bool INV, typename V>
 __device__ __forceinline__ void reg_dft(V* a, const V* tw) {
   if constexpr (M == 2 || M == 3 || M == 4 || M == 5) {
     dft_small<M, INV>(a);
   } else if constexpr (M > 1) {
     constexpr int R = FirstRadix<M>::R, Q = M / R;
-    V c[R][Q];
+    if constexpr (Gcd<R, Q>::value == 1) {
+      constexpr int QI = ModInv<Q, R>::value, RI = ModInv<R, Q>::value;
+      V c[R][Q];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+      for (int q = 0; q < Q; ++q) {
+        V t[R];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) c[r][q] = a[r + R * q];
-      reg_dft<Q, N, INV>(c[r], tw);
+        for (int r = 0; r < R; ++r) t[r] = a[(Q * r + R * q) % M];
+        dft_small<R, INV>(t);
 #pragma unroll
-      for (int u = 1; u < Q; ++u) {
-        const int e = (r * u) % M;
-        if (e == 0) continue;
-        if (4 * e == M) {
-          c[r][u] = mul_mi<INV>(c[r][u]);
-        } else {
-          c[r][u] = twiddle<N, INV>(c[r][u], e * (N / M), tw);
+        for (int r = 0; r < R; ++r) c[r][q] = t[r];
+      }
+#pragma unroll
+      for (int kr = 0; kr < R; ++kr) reg_dft<Q, N, INV>(c[kr], tw);
+#pragma unroll
+      for (int kr = 0; kr < R; ++kr)
+#pragma unroll
+        for (int kq = 0; kq < Q; ++kq) a[(Q * QI * kr + R * RI * kq) % M] = c[kr][kq];
+    } else {
+      V c[R][Q];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) c[r][q] = a[r + R * q];
+        reg_dft<Q, N, INV>(c[r], tw);
+#pragma unroll
+        for (int u = 1; u < Q; ++u) {
+          const int e = (r * u) % M;
+          if (e == 0) continue;
+          if (4 * e == M) {
+            c[r][u] = mul_mi<INV>(c[r][u]);
+          } else if (2 * e == M) {
+            c[r][u].x = -c[r][u].x;
+            c[r][u].y = -c[r][u].y;
+          } else if (4 * e == 3 * M) {
+            c[r][u] = mul_mi<!INV>(c[r][u]);
+          } else {
+            c[r][u] = twiddle<N, INV>(c[r][u], e * (N / M), tw);
+          }
         }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < Q; ++u) {
-      V d[R];
+      for (int u = 0; u < Q; ++u) {
+        V d[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) d[r] = c[r][u];
-      dft_small<R, INV>(d);
+        for (int r = 0; r < R; ++r) d[r] = c[r][u];
+        dft_small<R, INV>(d);
 #pragma unroll
-      for (int s = 0; s < R; ++s) a[u + Q * s] = d[s];
+        for (int s = 0; s < R; ++s) a[u + Q * s] = d[s];
+      }
     }
   }
 }
