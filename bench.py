@@ -33,7 +33,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of single-kernel
 # slots, from the ncu captures summarised in profiles/ (diamond 4x4x4 workload, 1024 bands per
 # launch); a kernel changed since its capture must be removed from this table.
-NCU_TRAFFIC_BYTES = {"plane_h_f64": 394.4e6, "plane_h_f32": 169.7e6}
+NCU_TRAFFIC_BYTES = {"plane_h_f64": 393.6e6, "plane_h_f32": 170.0e6}
 # profile slots that time exactly one kernel (the roofline is reported for the top one)
 SINGLE_KERNEL_SLOTS = ("plane_h", "plane_rho", "xpass_inv", "xpass_fwd", "xpass_rho", "fom_solve")
 

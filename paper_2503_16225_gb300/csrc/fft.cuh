@@ -8,8 +8,9 @@
 // so thread t first forms the N1-point DFT of its strided values in registers and applies
 // the twiddles w_N^{t k1} (step 1), the values go through shared memory once, and thread t
 // then forms the N2-point DFTs of the columns k1 = t + N2 j (j < N1 / N2), again in
-// registers (step 2).  The register DFTs are mixed-radix Cooley-Tukey with every index
-// known at compile time.  Twiddles come from a per-line table tw[e] = e^{-2 pi i e / N} in
+// registers (step 2).  The register DFTs split coprime lengths by the prime-factor
+// (Good-Thomas) index map, which needs no twiddles, and the rest by mixed-radix
+// Cooley-Tukey, with every index known at compile time.  Twiddles come from a per-line table tw[e] = e^{-2 pi i e / N} in
 // shared memory; all threads of a warp read the same entry (broadcast).
 //
 // Convention: forward X_k = sum_j x_j e^{-2 pi i k j / N}, inverse with +i; neither is
