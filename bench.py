@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="diamond_k444", choices=["diamond_k444", "diamond_k222", "two_atom"])
+    ap.add_argument("--workload", default="diamond_k444",
+                    choices=["diamond_k444", "diamond_k222", "two_atom", "diamond64_gamma", "diamond64_k222"],
+                    help="diamond64_*: the 64-atom supercell (96^3 grid, 128 bands, 256 projectors), "
+                         "--op runs only (its p x p dense steps exceed the 64-band limit)")
     ap.add_argument("--serve", type=int, default=0,
                     help="serve a stream of this many synthetic crystals instead (Poisson arrivals)")
     ap.add_argument("--rate", type=float, default=2.0, help="arrival rate of the serving stream (requests/s)")
@@ -105,7 +108,9 @@ def workload(name):
     import synth
     return {"diamond_k444": lambda: synth.config_diamond(2, kgrid=(4, 4, 4)),
             "diamond_k222": lambda: synth.config_diamond(2, kgrid=(2, 2, 2)),
-            "two_atom": lambda: synth.config_two_atom(1)}[name]()
+            "two_atom": lambda: synth.config_two_atom(1),
+            "diamond64_gamma": lambda: synth.config_diamond_supercell(2),
+            "diamond64_k222": lambda: synth.config_diamond_supercell(2, kgrid=(2, 2, 2))}[name]()
 
 
 def measured_peaks():
@@ -459,6 +464,7 @@ def run_op(args):
     """A few calls of one hot-path operation (H application, density or energy-adaptive
     gradient) on the workload's start point, timed with CUDA events: a short program for
     profiler captures."""
+    import numpy as np
     import torch
     import synth
     import paper_2503_16225_gb300 as E
@@ -467,9 +473,14 @@ def run_op(args):
     prec = 1 if args.precision == "mixed" else 0
     sysm = E.System(cfg, E.eacg_default_params(precision=prec))
     raw = synth.raw_coefficients(cfg["seed"], sysm.nk, sysm.p, sysm.n_max)
-    E.eacg_set_psi(sysm.h, torch.from_numpy(raw).cuda())
     phi = sysm.block()
-    E.eacg_get_psi(sysm.h, phi)
+    if sysm.p <= E.EACG_MAX_BANDS_DENSE:
+        E.eacg_set_psi(sysm.h, torch.from_numpy(raw).cuda())
+        E.eacg_get_psi(sysm.h, phi)
+    else:  # orthonormal start by host QR (the library's polar factor needs p <= 64)
+        for k, n in enumerate(sysm.nk):
+            q = np.linalg.qr(raw[k, :, :n].T)[0]
+            phi[k, :, :n] = torch.from_numpy(np.ascontiguousarray(q.T))
     E.eacg_density(sysm.h, phi, None, 0)
     out = sysm.block()
     if args.op == "apply_h":
@@ -488,8 +499,14 @@ def run_op(args):
         call()
     e1.record(stream)
     e1.synchronize()
-    print(json.dumps({"op": args.op, "workload": cfg["name"], "precision": args.precision, "calls": args.steps,
-                      "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps), "bands": sysm.K * sysm.p}))
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    line = {"op": args.op, "workload": cfg["name"], "precision": args.precision, "calls": args.steps,
+            "ms_per_call": ms, "bands": sysm.K * sysm.p}
+    if args.op == "apply_h":
+        # band applications per second and algorithmic H-psi bytes (pruned transforms) per second
+        line["band_apps_per_s"] = sysm.K * sysm.p / (ms / 1e3)
+        line["hpsi_gbs"] = sysm.K * sysm.p * hpsi_bytes_per_band(sysm, 8 if prec else 16) / (ms / 1e3) / 1e9
+    print(json.dumps(line))
     sysm.close()
 
 

@@ -35,6 +35,15 @@ extern "C" {
 
 typedef struct eacg_system eacg_system;
 
+/* Band limits.  The transforms, the density, the potential, H application and the energy
+ * evaluation take up to EACG_MAX_BANDS bands per k-point.  The calls that decompose p x p
+ * matrices (eacg_set_psi, eacg_step, eacg_solve, eacg_solve_host, eacg_ea_gradient,
+ * eacg_retract: polar factor, inverse, Lyapunov solve, rank-revealing QR, projected FOM
+ * solves) hold a p x p block in one CTA's shared memory and return EACG_EUNSUPPORTED for
+ * p > EACG_MAX_BANDS_DENSE. */
+#define EACG_MAX_BANDS 1024
+#define EACG_MAX_BANDS_DENSE 64
+
 typedef enum {
   EACG_OK = 0,
   EACG_EINVAL = 1,        /* invalid argument or model                          */
@@ -63,7 +72,7 @@ typedef struct {
   const double* D;         /* host, natoms x 2 (Ha)                            */
   double ecut;             /* basis: 1/2 |k+G|^2 <= ecut (Ha)                  */
   int N;                   /* FFT grid edge: 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80 or 96 */
-  int nbands;              /* p: occupied orbitals per k-point                 */
+  int nbands;              /* p: occupied orbitals per k-point, <= EACG_MAX_BANDS */
   int nk;                  /* K: number of k-points                            */
   const double* kfrac;     /* host, K x 3 fractional coordinates (units of 2 pi / a) */
   const double* kweight;   /* host, K weights (sum 1)                          */

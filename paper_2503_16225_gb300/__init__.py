@@ -19,8 +19,12 @@ __all__ = [
     "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
-    "System", "STATUS",
+    "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
 ]
+
+# band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
+EACG_MAX_BANDS = 1024
+EACG_MAX_BANDS_DENSE = 64
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBREAKDOWN", 5: "ENONCOERCIVE",
           6: "ELINESEARCH", 7: "ENAN", 8: "ENOTCONV", 9: "EUNSUPPORTED"}

@@ -261,23 +261,26 @@ void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int
 }
 
 // ----------------------------------------------------------------------------- A B (small B)
-// C (L x n, cplx<T>) = alpha A (L x m, cplx<T>) B (m x n, FP64, staged in T) + beta C.
+// C (L x n, VC) = alpha A (L x m, cplx<T>) B (m x n, FP64, staged in T) + beta C; the products
+// accumulate in T and the result is formed in the precision of C (VC = cplx<T>, or double2
+// for FP32 operands added into an FP64 block).
 constexpr int NN_COLS = 8;
 constexpr int NN_ROWS = 64;
-template <typename T>
+template <typename T, typename VC>
 __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
-                          const double2* __restrict__ B, size_t sB, int ldb, cplx<T>* __restrict__ C, size_t sC,
+                          const double2* __restrict__ B, size_t sB, int ldb, VC* __restrict__ C, size_t sC,
                           int ldc, double2 alpha, double2 beta, const int* __restrict__ kactive) {
   using V = cplx<T>;
+  using TC = decltype(C[0].x);
   const int k = blockIdx.y;
   if (kactive && !kactive[k]) return;
   __shared__ V sb[NN_ROWS][NN_COLS];
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   const V* Ak = A + k * sA;
   const double2* Bk = B + k * sB;
-  V* Ck = C + k * sC;
+  VC* Ck = C + k * sC;
   const bool bz = (beta.x == 0.0 && beta.y == 0.0);
-  const V al = to_c<T>(alpha), be = to_c<T>(beta);
+  const VC al = to_c<TC>(alpha), be = to_c<TC>(beta);
   V zero;
   zero.x = 0;
   zero.y = 0;
@@ -305,8 +308,8 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
 #pragma unroll
       for (int jj = 0; jj < NN_COLS; ++jj) {
         if (j0 + jj < n) {
-          V* cp = Ck + (size_t)(j0 + jj) * ldc + l;
-          V r = cmul(al, acc[jj]);
+          VC* cp = Ck + (size_t)(j0 + jj) * ldc + l;
+          VC r = cmul(al, cvt<VC>(acc[jj]));
           if (!bz) r = r + cmul(be, *cp);
           *cp = r;
         }
@@ -315,13 +318,13 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
   }
 }
 
-template <typename T>
+template <typename T, typename VC>
 static void gemm_nn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const double2* B, size_t sB,
-                      int ldb, cplx<T>* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
+                      int ldb, VC* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                       cudaStream_t st) {
   if (K <= 0 || L <= 0 || n <= 0) return;
   dim3 g((L + 127) / 128, K);
-  k_gemm_nn<T><<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
+  k_gemm_nn<T, VC><<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
   count_launch();
 }
 
@@ -333,6 +336,11 @@ void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int 
 void dense_gemm_nn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B, size_t sB,
                      int ldb, float2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                      cudaStream_t st) {
+  gemm_nn_t<float>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
+}
+void dense_gemm_nn32_into64(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B,
+                            size_t sB, int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta,
+                            const int* kactive, cudaStream_t st) {
   gemm_nn_t<float>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
 }
 

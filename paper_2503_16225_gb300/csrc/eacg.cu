@@ -145,11 +145,11 @@ std::atomic<long long> g_launches{0};
 const char* const PROF_NAMES[] = {"xpass_inv_f64",  "plane_h_f64",  "xpass_fwd_f64", "nonlocal_f64",
                                   "xpass_rho_f64",  "plane_rho_f64", "fom_solve_f64", "potential",
                                   "xpass_inv_f32",  "plane_h_f32",  "xpass_fwd_f32", "nonlocal_f32",
-                                  "xpass_rho_f32",  "plane_rho_f32", "fom_solve_f32", "unused",
+                                  "xpass_rho_f32",  "plane_rho_f32", "fom_solve_f32", "nonlocal_eval_f32",
                                   "fom_setup",      "fom_residual", "fom_orth",      "fom_block",
                                   "trial_retract",  "fom_final",    "unused2",       "unused3"};
 enum { P_XINV = 0, P_PLANE_H, P_XFWD, P_NONLOCAL, P_XINV_RHO, P_PLANE_RHO, P_FOMSOLVE, P_POT, P_F32,
-       P_FOM_SETUP = 16, P_FOM_RES, P_FOM_ORTH, P_FOM_BLOCK, P_TRIAL_RET, P_FOM_FINAL, P_NSLOTS = 24 };
+       P_NONLOCAL32 = P_F32 + 7, P_FOM_SETUP = 16, P_FOM_RES, P_FOM_ORTH, P_FOM_BLOCK, P_TRIAL_RET, P_FOM_FINAL, P_NSLOTS = 24 };
 // algorithmic FLOPs of one N-point complex transform (5 N log2 N convention)
 inline double fft_flops(int N) { return 5.0 * N * std::log2((double)N); }
 
@@ -299,8 +299,12 @@ static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::st
     *why = "k-points missing";
     return EACG_EINVAL;
   }
-  if (m->nbands > 64) {
-    *why = "nbands > 64 is not supported by this build";
+  if (m->nbands > EACG_MAX_BANDS) {
+    *why = "nbands above the largest supported block (1024 bands)";
+    return EACG_EUNSUPPORTED;
+  }
+  if ((long long)m->nk * m->nbands > 65535) {
+    *why = "nk * nbands above 65535 (the transforms launch one CTA row per band)";
     return EACG_EUNSUPPORTED;
   }
   if (!grid_supported(m->N)) {
@@ -442,8 +446,8 @@ static eacg_status build_potential_and_projectors(eacg_system* s) {
   }
   if (s->nproj > 0) {
     TRY(dalloc(s, &s->d_B, sizeof(double2) * (size_t)s->K * s->nproj * s->n_max));
-    TRY(dalloc(s, &s->d_P, sizeof(double2) * (size_t)s->K * s->nproj * 64));
-    TRY(dalloc(s, &s->d_P2, sizeof(double2) * (size_t)s->K * s->nproj * 64));
+    TRY(dalloc(s, &s->d_P, sizeof(double2) * (size_t)s->K * s->nproj * s->p));
+    TRY(dalloc(s, &s->d_P2, sizeof(double2) * (size_t)s->K * s->nproj * s->p));
     grid_projectors(s->K, s->n_max, s->d_nk, s->d_m, s->d_kfrac, s->b, s->omega, s->natoms, s->d_pos, s->npa,
                     s->width, s->d_B, s->st);
     CKL(s);
@@ -484,7 +488,7 @@ static eacg_status alloc_work(eacg_system* s) {
                               dense_cn_work(K, s->n_max, std::max(p, s->nproj), p));
   s->cn_elems = std::max(cnw, (size_t)K * 4096);
   TRY(dalloc(s, &s->cn_work, sizeof(double2) * s->cn_elems));
-  TRY(dalloc(s, &s->d_red, sizeof(double) * (size_t)(K * 64 + 4096)));
+  TRY(dalloc(s, &s->d_red, sizeof(double) * ((size_t)K * std::max(p, 64) + 4096)));
   TRY(dalloc(s, &s->d_out, sizeof(double) * 4096));
   TRY(dalloc(s, &s->d_esum, sizeof(double) * 3 * 256));
   TRY(dalloc(s, &s->d_kactive, sizeof(int) * K));
@@ -592,7 +596,7 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
   PROF_RUN(P_XFWD + off, nb * (inter + 2.0 * coef), fx, nb,
            grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
   CKL(s);
-  if (s->nproj > 0) {
+  if (s->nproj > 0 && prec == 0) {
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
     PROF_RUN(P_NONLOCAL, (double)K * np * nm * 16.0 * 2 + 3.0 * nb * coef, 16.0 * K * np * nm * p, nb, {
       dense_gemm_cn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np,
@@ -602,6 +606,22 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
       dense_gemm_nn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm, nm,
                     ONE, ONE, kactive, s->st);
     });
+    CKL(s);
+  } else if (s->nproj > 0) {
+    // FP32 phase: projector overlaps of complex64 copies (FP32 products, FP64 chunk sums), the
+    // back-projection accumulated in FP32 and added into the FP64 result
+    const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
+    float2* in32 = reinterpret_cast<float2*>(s->c32);
+    PROF_RUN(P_NONLOCAL32, (double)K * np * nm * 8.0 * 2 + nb * nm * (16.0 + 8.0 + 8.0 + 32.0), 16.0 * K * np * nm * p,
+             nb, {
+               dense_to32(s->blk, in, 1.0, in32, s->st);
+               dense_gemm_cn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, in32, (size_t)p * nm, nm, s->d_P,
+                               (size_t)np * p, np, ONE, ZERO, s->cn_work, kactive, s->st);
+               dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
+               dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
+               dense_gemm_nn32_into64(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out,
+                                      (size_t)p * nm, nm, ONE, ONE, kactive, s->st);
+             });
     CKL(s);
   }
   s->h_apps += (long long)s->K * s->p;
@@ -1520,6 +1540,16 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
     if (!(sys)) return EACG_EINVAL;         \
   } while (0)
 
+// Calls that need the p x p dense kernels (eigen-decompositions, inverses, Lyapunov solves,
+// pivoted Cholesky, projected FOM solves), which hold a p x p block in one CTA's shared memory.
+#define DENSE_CHECK(sys)                                                                         \
+  do {                                                                                           \
+    if ((sys)->p > EACG_MAX_BANDS_DENSE) {                                                      \
+      (sys)->err = "this call needs the p x p dense kernels, which support at most 64 bands";   \
+      return EACG_EUNSUPPORTED;                                                                  \
+    }                                                                                            \
+  } while (0)
+
 // ---- autotune of the line-FFT plan
 // For grid sizes with two compiled line plans, time both on this system's transform pipeline
 // (inverse x pass, plane, forward x pass over all bands) in each precision and keep the faster.
@@ -1595,8 +1625,10 @@ static eacg_status autotune_plans(eacg_system* s) {
 // of at most 8 k-points (the choice is recorded per shape bucket for the whole process).
 static eacg_status autotune_gemm(eacg_system* s) {
   const int p = s->p, nm = s->n_max, Kt = std::min(s->K, 8);
-  const int mmax = std::min(16 * p, 1024);
-  std::vector<int> ms = {p, 2 * p, 4 * p, 8 * p, 16 * p};
+  // Krylov shapes q x p exist only where the FOM runs (p within the dense kernels' limit)
+  const bool fom = p <= EACG_MAX_BANDS_DENSE;
+  const int mmax = fom ? std::min(16 * p, 1024) : p;
+  std::vector<int> ms = fom ? std::vector<int>{p, 2 * p, 4 * p, 8 * p, 16 * p} : std::vector<int>{p};
   if (s->nproj > 0) ms.push_back(s->nproj);
   double2 *A = nullptr, *C = nullptr, *W = nullptr;
   const size_t na = (size_t)Kt * std::max(mmax, s->nproj) * nm;
@@ -1778,6 +1810,7 @@ extern "C" eacg_status eacg_get_basis(const eacg_system* cs, int* m_dev) {
 
 extern "C" eacg_status eacg_set_psi(eacg_system* s, const double* psi_dev) {
   SYS_CHECK(s);
+  DENSE_CHECK(s);
   if (!psi_dev) return EACG_EINVAL;
   CK(cudaMemcpyAsync(s->tmp2, psi_dev, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
   TRY(polar(s, s->tmp2, s->phi, s->eval, s->evec, s->sm3));
@@ -1849,6 +1882,7 @@ extern "C" eacg_status eacg_energy(eacg_system* s, const double* psi_dev, double
 extern "C" eacg_status eacg_ea_gradient(eacg_system* s, const double* psi_dev, double* g_dev, int* fom_iters,
                                         int precision) {
   SYS_CHECK(s);
+  DENSE_CHECK(s);
   if (!psi_dev || !g_dev) return EACG_EINVAL;
   EvalOut ev;
   CK(cudaMemcpyAsync(s->phi_t, psi_dev, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
@@ -1863,6 +1897,7 @@ extern "C" eacg_status eacg_ea_gradient(eacg_system* s, const double* psi_dev, d
 extern "C" eacg_status eacg_retract(eacg_system* s, const double* phi_dev, const double* eta_dev, double tau,
                                     double* phi_out_dev, double* teta_out_dev) {
   SYS_CHECK(s);
+  DENSE_CHECK(s);
   if (!phi_dev || !eta_dev || !phi_out_dev) return EACG_EINVAL;
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
@@ -1887,6 +1922,7 @@ extern "C" eacg_status eacg_retract(eacg_system* s, const double* phi_dev, const
 
 extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {
   SYS_CHECK(s);
+  DENSE_CHECK(s);
   eacg_status st = do_step(s, info);
   if (st == EACG_OK) {
     cudaError_t e = cudaStreamSynchronize(s->st);
@@ -1900,6 +1936,7 @@ extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {
 
 extern "C" eacg_status eacg_solve(eacg_system* s, eacg_result* out) {
   SYS_CHECK(s);
+  DENSE_CHECK(s);
   eacg_status st = EACG_OK;
   eacg_step_info info;
   while (true) {
@@ -1926,6 +1963,7 @@ extern "C" eacg_status eacg_solve(eacg_system* s, eacg_result* out) {
 extern "C" eacg_status eacg_solve_host(eacg_system* s, const double* psi0_host, double* psi_out_host,
                                        eacg_result* out) {
   SYS_CHECK(s);
+  DENSE_CHECK(s);
   if (!psi0_host) return EACG_EINVAL;
   CK(cudaMemcpyAsync(s->tmp2, psi0_host, sizeof(double2) * s->blk, cudaMemcpyHostToDevice, s->st));
   TRY(polar(s, s->tmp2, s->phi, s->eval, s->evec, s->sm3));

@@ -95,6 +95,10 @@ void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int
 void dense_gemm_nn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B, size_t sB,
                      int ldb, float2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                      cudaStream_t st);
+// complex64 A times FP64 B (staged in FP32, FP32 accumulation) formed and added into an FP64 C
+void dense_gemm_nn32_into64(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B,
+                            size_t sB, int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta,
+                            const int* kactive, cudaStream_t st);
 void dense_to32(size_t n, const double2* x, double sc, float2* y, cudaStream_t st);
 void dense_to64(size_t n, const float2* x, double2* y, cudaStream_t st);
 void dense_axpby32(size_t n, double2 a, const float2* x, double2 b, const float2* y, float2* out, cudaStream_t st);

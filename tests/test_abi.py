@@ -44,3 +44,17 @@ def test_bytes_required_and_model_validation_on_host():
     bad = dict(synth.config_two_atom(1))
     bad["N"] = 7   # not a supported FFT size
     assert E.eacg_bytes_required(bad)[0] == 0
+    # band limits: the 64-atom supercell (128 bands) is accepted, 1025 bands are not
+    assert E.eacg_bytes_required(synth.config_diamond_supercell(2))[0] > 0
+    big = dict(synth.config_diamond(2, kgrid=(1, 1, 1)))
+    big["nbands"] = E.EACG_MAX_BANDS + 1
+    assert E.eacg_bytes_required(big)[0] == 0
+
+
+def test_binding_band_limits_match_the_header():
+    ensure_library()
+    import paper_2503_16225_gb300 as E
+    src = open(os.path.join(ROOT, "include", "eacg.h")).read()
+    for name in ("EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE"):
+        val = int(re.search(rf"#define {name} (\d+)", src).group(1))
+        assert getattr(E, name) == val, name
