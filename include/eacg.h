@@ -107,6 +107,9 @@ typedef struct {
                        * (same warm-up; then eta = -G with an alternating Barzilai-Borwein step
                        * and Zhang-Hager non-monotone backtracking, rho 0.85, delta 1e-4).
                        * Default 0 */
+  int tensor_cores;   /* 1: projector overlaps of complex64 blocks (FP32 phase, FP32 FOM) on the
+                       * tensor cores (see eacg_overlap_c64, method 1) where nproj >= 128 and
+                       * nbands is a multiple of 16; 0: SIMT FP32.  Default 1 */
 } eacg_params;
 
 typedef struct {
@@ -241,6 +244,18 @@ long long eacg_launch_count(void);
 #define EACG_NOALLOC_MAX_PARTIALS 524288
 eacg_status eacg_overlap_noalloc(int K, int n, int p, const double* a_dev, const double* b_dev, double* c_dev,
                                  void* stream);
+
+/* Block overlaps of complex64 blocks, the contraction of the projector overlaps P = B^* Psi
+ * of the nonlocal term (Sec. 5.1) in the FP32 phase: c_k = a_k^* b_k for k < K, where a_k is
+ * L x m and b_k is L x n complex64 (column-major, ld L, laid out [K][m][L] and [K][n][L]) and
+ * c_k is m x n complex double (column-major, [K][n][m]); caller-owned device buffers.
+ * method 0: SIMT FP32 products; 1: tensor cores (tcgen05, each FP32 operand split into two
+ * TF32 parts, three TF32 products per product), for m >= 128 and n a multiple of 16, else
+ * EACG_EUNSUPPORTED.  Both accumulate in FP32 within chunks of 1024 rows and sum the chunks in
+ * FP64 in a fixed order.  Allocates and frees its own scratch; stream: cudaStream_t or NULL;
+ * returns after synchronising it.  EACG_EINVAL for negative sizes or null buffers. */
+eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, const float* b_dev, double* c_dev,
+                             int method, void* stream);
 
 /* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
 eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);

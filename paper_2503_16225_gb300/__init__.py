@@ -19,7 +19,7 @@ __all__ = [
     "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
-    "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
+    "eacg_overlap_noalloc", "eacg_overlap_c64", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
 ]
 
 # band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
@@ -47,7 +47,7 @@ class EacgParams(ctypes.Structure):
                 ("eps", ctypes.c_double), ("warm_res", ctypes.c_double), ("switch_res", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("max_warm", ctypes.c_int), ("max_fom", ctypes.c_int),
                 ("max_ls", ctypes.c_int), ("precision", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("fft_plan", ctypes.c_int), ("method", ctypes.c_int)]
+                ("fft_plan", ctypes.c_int), ("method", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class EacgStepInfo(ctypes.Structure):
@@ -107,6 +107,8 @@ def _load():
         "eacg_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(EacgKernelStat), ctypes.c_int]),
         "eacg_launch_count": (ctypes.c_longlong, []),
         "eacg_overlap_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
+        "eacg_overlap_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                            ctypes.c_int, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -312,6 +314,15 @@ def eacg_overlap_noalloc(a, b, c, stream=None):
     p x p per k), through the allocation-free entry point; returns the eacg_status code."""
     K, p, n = a.shape
     return int(lib.eacg_overlap_noalloc(K, n, p, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
+
+
+def eacg_overlap_c64(a, b, c, method=1, stream=None):
+    """c[k] = a[k]^* b[k] for complex64 tensors a [K, m, L], b [K, n, L] and complex128 c [K, n, m]
+    (column-major m x n per k); method 1 = tensor cores (3 x TF32), 0 = SIMT FP32.  Returns the
+    eacg_status code."""
+    K, m, L = a.shape
+    n = b.shape[1]
+    return int(lib.eacg_overlap_c64(K, L, m, n, _ptr(a), _ptr(b), _ptr(c), int(method), _stream(stream)))
 
 
 class System:

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeacg.so")
 SOURCES = [
     "grid_fft_xl.cu", "grid_fft_large.cu", "grid_fft_mid.cu", "grid_fft_48.cu", "grid_fft_small.cu",
-    "grid_kernels.cu", "dense_kernels.cu", "eacg.cu", "noalloc.cu",
+    "grid_kernels.cu", "dense_kernels.cu", "eacg.cu", "noalloc.cu", "tc_kernels.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

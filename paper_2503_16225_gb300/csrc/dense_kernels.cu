@@ -177,6 +177,14 @@ static void gemm_cn_partial_launch(int G, dim3 g1, int L, int m, int n, const cp
   count_launch();
 }
 
+void dense_cn_reduce(int K, int m, int n, int nch, const double2* work, double2* C, size_t sC, int ldc,
+                     double2 alpha, double2 beta, const int* kactive, cudaStream_t st) {
+  if (K <= 0 || m <= 0 || n <= 0) return;
+  dim3 g2((m * n + 255) / 256, K);
+  k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
+  count_launch();
+}
+
 template <typename T>
 static void gemm_cn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const cplx<T>* B, size_t sB,
                       int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,

@@ -137,6 +137,7 @@ struct eacg_system {
   HGraph* cap = nullptr;              // graph being captured (profile events go to it)
   long long graph_launches = 0;       // replays of captured graphs
   bool graphs_off = false;            // set when capture is not possible on this system
+  bool tc_proj = false;               // FP32 projector overlaps on the tensor cores
 };
 
 namespace {
@@ -337,6 +338,7 @@ extern "C" void eacg_default_params(eacg_params* prm) {
   prm->graphs = 1;
   prm->fft_plan = -1;
   prm->method = 0;
+  prm->tensor_cores = 1;
 }
 
 static double sphere_volume_estimate(const eacg_model* m) {
@@ -576,6 +578,18 @@ static eacg_status fom_reserve(eacg_system* s, int qneed) {
 }
 
 // ============================================================================ operators
+// P = B32^* in32 (projector overlaps of complex64 blocks): on the tensor cores (3 x TF32) when
+// the shape allows it, else the SIMT FP32 block-overlap kernel.
+static void projector_overlaps32(eacg_system* s, const float2* in32, const int* kactive) {
+  const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
+  if (s->tc_proj)
+    dense_overlap_tf32x3(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, in32, (size_t)p * nm, nm, s->d_P,
+                         (size_t)np * p, np, ONE, ZERO, s->cn_work, kactive, s->st);
+  else
+    dense_gemm_cn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, in32, (size_t)p * nm, nm, s->d_P, (size_t)np * p,
+                    np, ONE, ZERO, s->cn_work, kactive, s->st);
+}
+
 // out = H in with the current potential (prec 0: FP64 transforms, 1: FP32).
 static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out, int prec, const int* kactive) {
   const int nb = s->K * s->p;
@@ -615,8 +629,7 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
     PROF_RUN(P_NONLOCAL32, (double)K * np * nm * 8.0 * 2 + nb * nm * (16.0 + 8.0 + 8.0 + 32.0), 16.0 * K * np * nm * p,
              nb, {
                dense_to32(s->blk, in, 1.0, in32, s->st);
-               dense_gemm_cn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, in32, (size_t)p * nm, nm, s->d_P,
-                               (size_t)np * p, np, ONE, ZERO, s->cn_work, kactive, s->st);
+               projector_overlaps32(s, in32, kactive);
                dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
                dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
                dense_gemm_nn32_into64(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out,
@@ -832,8 +845,7 @@ static eacg_status apply_H_block32(eacg_system* s, const float2* in, float2* out
   if (s->nproj > 0) {
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
     PROF_RUN(P_NONLOCAL + P_F32, (double)K * np * nm * 8.0 * 2 + 3.0 * nb * coef, 16.0 * K * np * nm * p, nb, {
-      dense_gemm_cn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np,
-                      ONE, ZERO, s->cn_work, kactive, s->st);
+      projector_overlaps32(s, in, kactive);
       dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
       dense_gemm_nn32(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm,
                       nm, ONE, ONE, kactive, s->st);
@@ -1749,6 +1761,7 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   s->g.tw64 = s->d_tw64;
   s->g.tw32 = s->d_tw32;
   if ((st = build_potential_and_projectors(s)) != EACG_OK) return fail(st);
+  s->tc_proj = s->prm.tensor_cores && s->nproj > 0 && dense_overlap_tc_eligible(s->nproj, s->p);
   if ((st = alloc_work(s)) != EACG_OK) return fail(st);
   if ((st = autotune_plans(s)) != EACG_OK) return fail(st);
   if ((st = autotune_gemm(s)) != EACG_OK) return fail(st);
@@ -1918,6 +1931,34 @@ extern "C" eacg_status eacg_retract(eacg_system* s, const double* phi_dev, const
   CK(cudaStreamSynchronize(s->st));
   s->fresh = 1;
   return EACG_OK;
+}
+
+extern "C" eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, const float* b_dev,
+                                        double* c_dev, int method, void* stream) {
+  if (K < 0 || L < 0 || m < 0 || n < 0 || method < 0 || method > 1) return EACG_EINVAL;
+  if (K == 0 || m == 0 || n == 0) return EACG_OK;
+  if (!a_dev || !b_dev || !c_dev) return EACG_EINVAL;
+  if (method == 1 && !dense_overlap_tc_eligible(m, n)) return EACG_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nw = std::max<size_t>(1, method ? dense_overlap_tc_work(K, L, m, n) : dense_cn_work(K, L, m, n));
+  double2* work = nullptr;
+  if (cudaMalloc(&work, sizeof(double2) * nw) != cudaSuccess) {
+    cudaGetLastError();
+    return EACG_ENOMEM;
+  }
+  const float2* A = reinterpret_cast<const float2*>(a_dev);
+  const float2* B = reinterpret_cast<const float2*>(b_dev);
+  double2* C = reinterpret_cast<double2*>(c_dev);
+  if (method)
+    dense_overlap_tf32x3(K, L, m, n, A, (size_t)m * L, L, B, (size_t)n * L, L, C, (size_t)m * n, m, ONE, ZERO, work,
+                         nullptr, st);
+  else
+    dense_gemm_cn32(K, L, m, n, A, (size_t)m * L, L, B, (size_t)n * L, L, C, (size_t)m * n, m, ONE, ZERO, work,
+                    nullptr, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(work);
+  return e == cudaSuccess ? EACG_OK : EACG_ECUDA;
 }
 
 extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {

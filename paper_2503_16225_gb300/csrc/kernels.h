@@ -72,6 +72,17 @@ void grid_projectors(int K, int n_max, const int* nk, const int* m, const double
 // Deterministic: fixed row chunks reduced in a fixed order.  work must hold
 // K * nchunks * m * n double2 (see dense_cn_work).
 size_t dense_cn_work(int K, int L, int m, int n);
+// C_k = alpha sum_ch part[k][ch] + beta C_k (fixed chunk order), part[k][ch][n][m]
+void dense_cn_reduce(int K, int m, int n, int nch, const double2* work, double2* C, size_t sC, int ldc,
+                     double2 alpha, double2 beta, const int* kactive, cudaStream_t st);
+// Block overlaps of complex64 blocks on the tensor cores (tcgen05, 3 x TF32 split, FP32
+// accumulation per chunk of 1024 rows, FP64 chunk sums); C_k = alpha A_k^* B_k + beta C_k.
+// Eligible shapes: m >= 128 and n a multiple of 16.  work: dense_overlap_tc_work elements.
+bool dense_overlap_tc_eligible(int m, int n);
+size_t dense_overlap_tc_work(int K, int L, int m, int n);
+void dense_overlap_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const float2* B,
+                          size_t sB, int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta,
+                          double2* work, const int* kactive, cudaStream_t st);
 void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
                    const int* kactive, cudaStream_t st);
