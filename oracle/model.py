@@ -13,6 +13,10 @@ H as the DFTK-style Hamiltonian -1/2 Laplacian + V of Sec. 5.2):
   * density rho = sum_k w_k f sum_i |u_ik|^2, integral (Omega/N^3) sum_j;
   * V_loc(G) = sum_a -4 pi Z_a/(Omega |G|^2) exp(-|G|^2 rc_a^2/4) exp(-i G.R_a), G != 0;
   * V_H(G) = 4 pi rho(G)/|G|^2 (G != 0), V_x = -(3 rho/pi)^{1/3} (Slater exchange);
+  * xc = 2 adds LDA correlation: the spin-unpolarised Perdew-Wang 1992 fit of the homogeneous
+    electron gas correlation energy per electron, eps_c(r_s), r_s = (3 / (4 pi rho))^{1/3},
+    E_c = int rho eps_c, V_c = eps_c - (r_s / 3) d eps_c / d r_s (the paper's experiments use
+    DFTK's LDA model, Sec. 5.3; its correlation is this fit);
   * Nyquist planes and G = 0 of every potential are zero;
   * s/p Gaussian projectors beta_al(G) = Omega^{-1/2} F_l(k+G) exp(-i (k+G).R_a)
     with coupling D_al; E_nl = sum_k w_k f sum_i sum_al D_al |<beta_al, c_i>|^2;
@@ -63,6 +67,10 @@ def frequencies(N: int):
     f = np.fft.fftfreq(N, d=1.0 / N).astype(np.int64)
     nyq = (f == -(N // 2)) if N % 2 == 0 else np.zeros(N, bool)
     return f, nyq
+
+
+# Perdew-Wang 1992 parameters of the spin-unpolarised correlation energy (Table I, zeta = 0)
+PW92 = dict(A=0.031091, alpha1=0.21370, beta1=7.5957, beta2=3.5876, beta3=1.6382, beta4=0.49294)
 
 
 class Model:
@@ -138,10 +146,35 @@ class Model:
     def exchange_energy_density(rho):
         return -0.75 * np.cbrt(3.0 / math.pi) * np.maximum(rho, 0.0) ** (4.0 / 3.0)
 
+    @staticmethod
+    def correlation(rho):
+        """Perdew-Wang 1992 LDA correlation (spin-unpolarised; Phys. Rev. B 45, 13244, Eq. (10)
+        with the zeta = 0 column of its Table I):
+            eps_c(r_s) = -2 A (1 + alpha1 r_s) ln(1 + 1 / (2 A (beta1 r_s^1/2 + beta2 r_s
+                                                          + beta3 r_s^3/2 + beta4 r_s^2))).
+        Returns (rho eps_c, V_c) with V_c = d(rho eps_c)/d rho = eps_c - (r_s/3) eps_c'(r_s);
+        both are 0 where rho <= 0."""
+        A, a1 = PW92["A"], PW92["alpha1"]
+        b1, b2, b3, b4 = PW92["beta1"], PW92["beta2"], PW92["beta3"], PW92["beta4"]
+        rho = np.asarray(rho, np.float64)
+        pos = rho > 0.0
+        rs = np.where(pos, np.cbrt(3.0 / (4.0 * math.pi * np.where(pos, rho, 1.0))), 1.0)
+        sq = np.sqrt(rs)
+        q0 = -2.0 * A * (1.0 + a1 * rs)
+        q1 = 2.0 * A * (b1 * sq + b2 * rs + b3 * rs * sq + b4 * rs * rs)
+        dq1 = A * (b1 / sq + 2.0 * b2 + 3.0 * b3 * sq + 4.0 * b4 * rs)
+        lg = np.log1p(1.0 / q1)
+        eps = q0 * lg
+        deps = -2.0 * A * a1 * lg - q0 * dq1 / (q1 * q1 + q1)
+        vc = eps - rs / 3.0 * deps
+        return np.where(pos, rho * eps, 0.0), np.where(pos, vc, 0.0)
+
     def potentials(self, rho):
-        """Total potential V_tot = V_loc + V_H + V_x and its Hartree/exchange parts."""
+        """Total potential V_tot = V_loc + V_H + V_xc and its Hartree/exchange-correlation parts."""
         vh = self.hartree_potential(rho) if self.hartree else np.zeros_like(rho)
         vx = self.exchange_potential(rho) if self.xc else np.zeros_like(rho)
+        if self.xc == 2:
+            vx = vx + self.correlation(rho)[1]
         return self.vloc + vh + vx, vh, vx
 
     # ------------------------------------------------------------------ projectors
@@ -238,6 +271,8 @@ class Model:
         eloc = self.integrate(self.vloc * rho)
         eh = 0.5 * self.integrate(self.hartree_potential(rho) * rho) if self.hartree else 0.0
         ex = self.integrate(self.exchange_energy_density(rho)) if self.xc else 0.0
+        if self.xc == 2:
+            ex += self.integrate(self.correlation(rho)[0])
         return dict(kin=ekin, loc=float(eloc), hartree=float(eh), xc=float(ex), nl=enl)
 
     def energy(self, Phi, rho=None):

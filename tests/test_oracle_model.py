@@ -7,7 +7,7 @@ import pytest
 
 import synth
 from oracle import earcg
-from oracle.model import Model, pairing
+from oracle.model import PW92, Model, pairing
 from tests.small_models import free_electron, small, start
 
 
@@ -95,6 +95,46 @@ def test_exchange_potential_is_derivative_of_exchange_energy():
     np.testing.assert_allclose(Model.exchange_potential(rho), fd, rtol=1e-8)
 
 
+def test_correlation_potential_is_derivative_of_correlation_energy():
+    """V_c = d(rho eps_c)/d rho by central differences (pins eps_c' and the r_s chain rule)."""
+    rho = np.array([1e-5, 1e-3, 0.05, 0.3, 2.0, 40.0])
+    h = 1e-6 * rho
+    fd = (Model.correlation(rho + h)[0] - Model.correlation(rho - h)[0]) / (2 * h)
+    np.testing.assert_allclose(Model.correlation(rho)[1], fd, rtol=1e-7)
+    e, v = Model.correlation(np.array([0.0, -1e-12]))
+    assert np.all(e == 0) and np.all(v == 0)
+
+
+def _eps_c(rs):
+    rho = 3.0 / (4.0 * math.pi * rs ** 3)
+    return Model.correlation(np.array([rho]))[0][0] / rho
+
+
+def test_correlation_high_density_limit():
+    """r_s -> 0: eps_c = c0 ln r_s - c1 + o(1) with the exact Gell-Mann-Brueckner coefficient
+    c0 = (1 - ln 2) / pi^2 and the second-order constant c1 = 0.046644 Ha that the Perdew-Wang
+    fit is built on; with them its beta2 equals 2 A beta1^2."""
+    c0 = (1.0 - math.log(2.0)) / math.pi ** 2
+    slope = (_eps_c(1e-9) - _eps_c(1e-10)) / math.log(10.0)
+    assert abs(slope - c0) < 1e-4 * c0
+    assert abs(_eps_c(1e-12) - c0 * math.log(1e-12) + 0.046644) < 2e-5
+    A, b1 = PW92["A"], PW92["beta1"]
+    assert abs(PW92["beta2"] - 2 * A * b1 * b1) < 1e-4 * PW92["beta2"]
+
+
+def test_correlation_agrees_with_an_independent_fit_of_the_same_gas():
+    """Perdew-Zunger 1981 fit of the same Ceperley-Alder energies (Phys. Rev. B 23, 5048,
+    unpolarised: r_s >= 1: gamma / (1 + beta1 sqrt(r_s) + beta2 r_s), gamma = -0.1423,
+    beta1 = 1.0529, beta2 = 0.3334; r_s < 1: 0.0311 ln r_s - 0.048 + 0.0020 r_s ln r_s
+    - 0.0116 r_s, Ha): the two agree within 1 mHa from r_s = 0.1 to 50."""
+    for rs in (0.1, 0.3, 0.5, 1.0, 2.0, 5.0, 10.0, 20.0, 50.0):
+        if rs >= 1:
+            pz = -0.1423 / (1 + 1.0529 * math.sqrt(rs) + 0.3334 * rs)
+        else:
+            pz = 0.0311 * math.log(rs) - 0.048 + 0.0020 * rs * math.log(rs) - 0.0116 * rs
+        assert abs(_eps_c(rs) - pz) < 1e-3, rs
+
+
 def test_local_potential_minimum_sits_on_the_atom():
     """A single Gaussian-screened ion placed on a grid point: V_loc is lowest there."""
     a, N = 8.0, 16
@@ -127,7 +167,7 @@ def _tangent(Phi, Z):
     return [Z[k] - Phi[k] @ (0.5 * (Phi[k].conj().T @ Z[k] + Z[k].conj().T @ Phi[k])) for k in range(len(Phi))]
 
 
-@pytest.mark.parametrize("nproj,hartree,xc", [(0, 1, 1), (4, 1, 1), (4, 0, 0)])
+@pytest.mark.parametrize("nproj,hartree,xc", [(0, 1, 1), (4, 1, 1), (4, 0, 0), (4, 1, 2)])
 def test_energy_derivative_equals_residual_pairing(nproj, hartree, xc):
     """Eq. (2.4)/(2.5): d/dh E(pf(Phi + h W)) at h = 0 equals 2 f <R, W> for tangent W
     (central differences, O(h^2)); pins the factors of every energy term against H."""
