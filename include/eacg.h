@@ -77,7 +77,9 @@ typedef struct {
   const double* kfrac;     /* host, K x 3 fractional coordinates (units of 2 pi / a) */
   const double* kweight;   /* host, K weights (sum 1)                          */
   int hartree;             /* 1: Hartree term on                               */
-  int xc;                  /* 1: Slater exchange on                            */
+  int xc;                  /* 0: none; 1: Slater exchange; 2: LDA = Slater exchange
+                            * + spin-unpolarised Perdew-Wang 1992 correlation
+                            * (DFTK's LDA model of the experiments, Sec. 5.3)     */
   double occ;              /* occupation f of every orbital (2: spin paired)   */
 } eacg_model;
 
@@ -192,7 +194,7 @@ eacg_status eacg_apply_H(eacg_system* sys, const double* psi_dev, double* hpsi_d
 
 /* Full evaluation at an orthonormal block: density, potential, H Phi, Lambda =
  * herm(Phi^* H Phi) (Eq. (2.6)), residual R = H Phi - Phi Lambda, energy terms.
- * terms_host[6] = {kinetic, local, Hartree, exchange, nonlocal, total}.  lam_dev and
+ * terms_host[6] = {kinetic, local, Hartree, exchange-correlation, nonlocal, total}.  lam_dev and
  * res_dev may be NULL.  *rnorm = ||R||_F. */
 eacg_status eacg_energy(eacg_system* sys, const double* psi_dev, double* terms_host, double* lam_dev,
                         double* res_dev, double* rnorm, int precision);

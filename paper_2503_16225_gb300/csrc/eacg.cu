@@ -296,6 +296,10 @@ static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::st
     *why = "projectors without couplings";
     return EACG_EINVAL;
   }
+  if (m->xc < 0 || m->xc > 2) {
+    *why = "xc must be 0 (none), 1 (Slater exchange) or 2 (LDA: Slater exchange + PW92 correlation)";
+    return EACG_EINVAL;
+  }
   if (!m->kfrac || !m->kweight) {
     *why = "k-points missing";
     return EACG_EINVAL;

@@ -186,7 +186,26 @@ __global__ void k_complex_real_part(const double2* __restrict__ c, double* __res
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) r[i] = c[i].x;
 }
 
-// V_tot = V_loc + V_H + V_x(rho) and the energy integrands (loc, hartree, xc) reduced per block.
+// LDA correlation of the spin-unpolarised homogeneous gas, Perdew-Wang 1992 fit (Phys. Rev. B
+// 45, 13244, Eq. (10), zeta = 0 parameters of Table I): with r_s = (3 / (4 pi rho))^{1/3},
+//   eps_c = -2 A (1 + alpha1 r_s) ln(1 + 1 / Q),  Q = 2 A (beta1 r_s^1/2 + beta2 r_s + beta3 r_s^3/2
+//   + beta4 r_s^2);  V_c = eps_c - (r_s / 3) d eps_c / d r_s.  rho > 0; returns rho eps_c.
+__device__ __forceinline__ double pw92_correlation(double rho, double* vc) {
+  const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+  const double rs = cbrt(3.0 / (4.0 * M_PI * rho));
+  const double sq = sqrt(rs);
+  const double pre = -2.0 * A * (1.0 + a1 * rs);
+  const double q = 2.0 * A * (sq * (b1 + b3 * rs) + rs * (b2 + b4 * rs));
+  const double dq = A * (b1 / sq + 2.0 * b2 + 3.0 * b3 * sq + 4.0 * b4 * rs);
+  const double lg = log1p(1.0 / q);
+  const double eps = pre * lg;
+  const double deps = -2.0 * A * a1 * lg - pre * dq / (q * (q + 1.0));
+  *vc = eps - rs * deps / 3.0;
+  return rho * eps;
+}
+
+// V_tot = V_loc + V_H + V_xc(rho) and the energy integrands (loc, hartree, xc) reduced per
+// block; xc: 0 none, 1 Slater exchange, 2 Slater exchange + PW92 correlation.
 __global__ void k_vtot_energy(size_t n, const double* __restrict__ vloc, const double* __restrict__ vh,
                               const double* __restrict__ rho, int hartree, int xc, double* __restrict__ vtot,
                               float* __restrict__ vtot32, double* __restrict__ blocksums /*[gridDim][3]*/) {
@@ -206,6 +225,11 @@ __global__ void k_vtot_energy(size_t n, const double* __restrict__ vloc, const d
       const double c3 = cbrt(rp);
       v -= cbrt(3.0 * rp / M_PI);
       ex += cx * rp * c3;
+      if (xc == 2 && rp > 0.0) {
+        double vc;
+        ex += pw92_correlation(rp, &vc);
+        v += vc;
+      }
     }
     vtot[i] = v;
     if (vtot32) vtot32[i] = (float)v;

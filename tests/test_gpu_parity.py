@@ -31,6 +31,7 @@ import paper_2503_16225_gb300 as E  # noqa: E402
 def _configs():
     return {
         "small_nl": small(nproj=4, kgrid=(2, 1, 1), nb=3),
+        "small_lda": small(nproj=4, kgrid=(2, 1, 1), nb=3, xc=2),   # exchange + PW92 correlation
         "small_p1": small(nproj=1, kgrid=(1, 1, 1), nb=1, N=16),
         "small_odd": small(nproj=0, kgrid=(3, 1, 1), nb=5, ecut=4.0, N=24),
         "two_atom": synth.config_two_atom(1),
@@ -196,7 +197,7 @@ def _angle(A, B):
     return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
 
 
-@pytest.mark.parametrize("name", ["small_nl", "small_p1", "two_atom"])
+@pytest.mark.parametrize("name", ["small_nl", "small_lda", "small_p1", "two_atom"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_solve_matches_oracle(name, precision):
     cfg = CFG[name]
