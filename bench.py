@@ -104,6 +104,45 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def rank_env():
+    """(world size, rank, local rank) of this process, from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, device=None):
+    """The largest of a per-rank value over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units of all ranks per second over the slowest rank's time (replicas: weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
+WORKLOAD_LABEL = {"diamond_k444": "diamond8 4x4x4k 48^3 p16"}
+
+
+def metric_name(args, cfg):
+    """The headline metric, shared by this arm and the reference arm."""
+    label = WORKLOAD_LABEL.get(args.workload, cfg["name"])
+    return f"served {'EARGD' if args.method == 'eargd' else 'eARCG'} solves/s ({label}, to ||R||<=1e-8)"
+
+
+def config_of(args, cfg, world):
+    """The workload description, shared by this arm and the reference arm."""
+    return {"workload": cfg["name"], "kpoints": len(cfg["kweight"]), "bands": cfg["nbands"], "grid": cfg["N"],
+            "ecut": cfg["ecut"], "precision": args.precision, "method": args.method,
+            "parallelism": f"replicas{world}", "concurrent_systems": max(1, args.concurrent),
+            "l2": "flushed between rounds of concurrent solves (256 MiB write)"}
+
+
 def workload(name):
     import synth
     return {"diamond_k444": lambda: synth.config_diamond(2, kgrid=(4, 4, 4)),
@@ -197,7 +236,7 @@ def oracle_band_apps(name):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return
     cfg = workload(args.workload)
@@ -212,12 +251,11 @@ def run_reference(args):
         apps, src = 15000 * len(cfg["kweight"]) * cfg["nbands"] // 1024, "estimate"
     solve_s = per_band * apps
     value = 1.0 / solve_s
-    line = {"impl": "reference", "metric": "eARCG solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)",
+    line = {"impl": "reference", "metric": metric_name(args, cfg),
             "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "kpoints": len(cfg["kweight"]), "bands": cfg["nbands"],
-                       "grid": cfg["N"], "ecut": cfg["ecut"]},
+            "config": config_of(args, cfg, args.gpus),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{sample}; scaled by {apps} band applications per solve ({src})"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -232,9 +270,7 @@ def run_gpu(args):
     import synth
     import paper_2503_16225_gb300 as E
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -328,12 +364,8 @@ def run_gpu(args):
             for key in acc:
                 acc[key] += st[key]
         E.eacg_profile_enable(sy.h, 0)
-    total_ms = sum(per)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * C * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(per), world, dev)
+    value = whole_job_rate(world, C * args.steps, total_ms)
 
     # ---- end to end through the host-buffer entry point (copies inside the timed region)
     e2e_ms = []
@@ -359,7 +391,8 @@ def run_gpu(args):
         for r in res:
             if isinstance(r, Exception) or r.status != 0:
                 raise RuntimeError("host-buffer solve failed")
-    e2e_value = world * C / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
+    e2e_value = (whole_job_rate(world, C, max_over_ranks(statistics.mean(e2e_ms), world, dev))
+                 if e2e_ms else None)
 
     # ---- plain FP64, one system at a time (the comparison the served number is quoted against)
     fp64_ref = None
@@ -413,15 +446,11 @@ def run_gpu(args):
     hpsi_gbs = (apps * bytes_per_band) / (total_ms / 1e3) / 1e9
 
     line = {
-        "metric": ("served eARCG solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)" if method == 0 else
-                   "served EARGD solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)"),
+        "metric": metric_name(args, cfg),
         "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if prec else "f64", "data": "synthetic",
-        "config": {"workload": cfg["name"], "kpoints": len(cfg["kweight"]), "bands": cfg["nbands"],
-                   "grid": cfg["N"], "ecut": cfg["ecut"], "precision": args.precision, "method": args.method,
-                   "parallelism": f"replicas{world}", "concurrent_systems": C,
-                   "l2": "flushed between rounds of concurrent solves (256 MiB write)"},
+        "config": config_of(args, cfg, world),
         "time_to_1e8_ms": {"p50": statistics.median(latencies), "p99": max(latencies), "all": latencies},
         "vs_fp64_one_at_a_time": fp64_ref,
         "solve": {"E": results[-1].E, "rnorm": results[-1].rnorm, "iterations": results[-1].iterations,
