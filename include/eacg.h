@@ -38,7 +38,7 @@ typedef struct eacg_system eacg_system;
 /* Band limits.  The transforms, the density, the potential, H application and the energy
  * evaluation take up to EACG_MAX_BANDS bands per k-point.  The calls that decompose p x p
  * matrices (eacg_set_psi, eacg_step, eacg_solve, eacg_solve_host, eacg_ea_gradient,
- * eacg_retract: polar factor, inverse, Lyapunov solve, rank-revealing QR, projected FOM
+ * eacg_retract, eacg_scf_guess: polar factor, inverse, Lyapunov solve, rank-revealing QR, projected FOM
  * solves) hold a p x p block in one CTA's shared memory and return EACG_EUNSUPPORTED for
  * p > EACG_MAX_BANDS_DENSE. */
 #define EACG_MAX_BANDS 1024
@@ -258,6 +258,22 @@ eacg_status eacg_overlap_noalloc(int K, int n, int p, const double* a_dev, const
  * returns after synchronising it.  EACG_EINVAL for negative sizes or null buffers. */
 eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, const float* b_dev, double* c_dev,
                              int method, void* stream);
+
+/* Initial guess of the experiments (Sec. 5.2): self-consistent field iterations until the
+ * density difference of two successive iterates is below drho_tol (0.1 in the paper).  The
+ * first input density is that of polar(psi0) (psi0: caller's device buffer [K][p][n_max]);
+ * each step minimises the band energy f sum_k w_k tr(Phi_k^* H[rho_in] Phi_k) with the
+ * potential of the input density held fixed (the same warm-up and energy-adaptive iterations
+ * as eacg_step, params.precision applies) until ||H Phi - Phi Lambda||_F <= eig_tol, takes
+ * rho_out = rho(Phi) and d = ||rho_out - rho_in||_2 = (integral over the cell of
+ * (rho_out - rho_in)^2)^{1/2}; d < drho_tol ends it with Phi as the system's iterate, else
+ * rho_in <- rho_in + alpha (rho_out - rho_in) (simple mixing, 0 < alpha <= 1).  *steps_out
+ * (may be NULL) = steps taken; history_host (may be NULL, max_scf doubles) receives d per step.
+ * Afterwards eacg_step / eacg_solve continue from Phi with its own density and potential.
+ * EACG_ENOTCONV when max_scf steps do not reach drho_tol (Phi is the last step's); errors of
+ * an inner step are returned as they are; EACG_EINVAL for invalid arguments. */
+eacg_status eacg_scf_guess(eacg_system* sys, const double* psi0_dev, double drho_tol, double alpha, int max_scf,
+                           double eig_tol, int* steps_out, double* history_host);
 
 /* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
 eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);

@@ -19,7 +19,7 @@ __all__ = [
     "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
-    "eacg_overlap_noalloc", "eacg_overlap_c64", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
+    "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
 ]
 
 # band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
@@ -109,6 +109,8 @@ def _load():
         "eacg_overlap_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "eacg_overlap_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                             ctypes.c_int, vp]),
+        "eacg_scf_guess": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                          _ip, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -314,6 +316,16 @@ def eacg_overlap_noalloc(a, b, c, stream=None):
     p x p per k), through the allocation-free entry point; returns the eacg_status code."""
     K, p, n = a.shape
     return int(lib.eacg_overlap_noalloc(K, n, p, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
+
+
+def eacg_scf_guess(sys, psi0, tol=0.1, alpha=0.5, max_scf=100, eig_tol=1e-10):
+    """SCF initial guess (Sec. 5.2) from the device block psi0 [K, p, n_max]; returns the
+    density differences ||rho_out - rho_in||_2 of the steps taken (the last is below tol)."""
+    steps = ctypes.c_int(0)
+    hist = (ctypes.c_double * max_scf)()
+    _check(sys, lib.eacg_scf_guess(sys, _ptr(psi0), float(tol), float(alpha), int(max_scf), float(eig_tol),
+                                   ctypes.byref(steps), hist))
+    return list(hist[:steps.value])
 
 
 def eacg_overlap_c64(a, b, c, method=1, stream=None):

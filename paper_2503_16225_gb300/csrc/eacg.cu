@@ -137,6 +137,10 @@ struct eacg_system {
   HGraph* cap = nullptr;              // graph being captured (profile events go to it)
   long long graph_launches = 0;       // replays of captured graphs
   bool graphs_off = false;            // set when capture is not possible on this system
+  // SCF initial guess: evaluations keep the potential (built from the mixed input density) and
+  // minimise the band energy f sum_k w_k tr(Phi_k^* H Phi_k) of that fixed Hamiltonian
+  bool frozen = false;
+  double* d_rho_in = nullptr;         // SCF input density (allocated by the first SCF call)
   bool tc_proj = false;               // FP32 projector overlaps on the tensor cores
 };
 
@@ -645,8 +649,8 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
   return EACG_OK;
 }
 
-// rho of an orthonormal block and the potential built from it; E_loc, E_H, E_x into d_red[0..2].
-static eacg_status density_and_potential(eacg_system* s, const double2* phi, int prec) {
+// rho of an orthonormal block into d_rho.
+static eacg_status density_only(eacg_system* s, const double2* phi, int prec) {
   const int nb = s->K * s->p;
   const int N = s->N;
   const size_t N3 = (size_t)N * N * N;
@@ -661,6 +665,14 @@ static eacg_status density_and_potential(eacg_system* s, const double2* phi, int
     grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
   });
   CKL(s);
+  return EACG_OK;
+}
+
+// The potential of the density in d_rho (FP64 and FP32 copies); E_loc, E_H, E_xc integrands
+// into d_esum.
+static eacg_status potential_from_rho(eacg_system* s) {
+  const int N = s->N;
+  const size_t N3 = (size_t)N * N * N;
   int nblk = 0;
   PROF_RUN(P_POT, (double)N3 * 8.0 * 8, 6.0 * N * N * fft_flops(N), 0, {
     if (s->hartree) {
@@ -675,6 +687,12 @@ static eacg_status density_and_potential(eacg_system* s, const double2* phi, int
   });
   CKL(s);
   return (nblk == 256) ? EACG_OK : EACG_ECUDA;
+}
+
+// rho of an orthonormal block and the potential built from it.
+static eacg_status density_and_potential(eacg_system* s, const double2* phi, int prec) {
+  TRY(density_only(s, phi, prec));
+  return potential_from_rho(s);
 }
 
 // ============================================================================ reductions to host
@@ -713,7 +731,7 @@ struct EvalOut {
 static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, double2* res, double2* lam, int prec,
                             EvalOut* out) {
   const int K = s->K, p = s->p, nm = s->n_max;
-  TRY(density_and_potential(s, phi, prec));
+  if (!s->frozen) TRY(density_and_potential(s, phi, prec));
   TRY(apply_H_block(s, phi, hphi, prec, nullptr));
   // Lambda = herm(Phi^* H Phi)
   dense_gemm_cn(K, nm, p, p, phi, (size_t)p * nm, nm, hphi, (size_t)p * nm, nm, lam, (size_t)p * p, p, ONE, ZERO,
@@ -724,6 +742,21 @@ static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, d
   dense_gemm_nn(K, nm, p, p, phi, (size_t)p * nm, nm, lam, (size_t)p * p, p, res, (size_t)p * nm, nm, MONE, ONE,
                 nullptr, s->st);
   CKL(s);
+  if (s->frozen) {
+    // band energy of the fixed Hamiltonian: f <Phi, H Phi> in the weighted pairing
+    pairing_dev(s, phi, hphi, 0, true);
+    pairing_dev(s, res, res, 1, false);
+    CKL(s);
+    TRY(sync_read(s, 2));
+    for (double& t : out->terms) t = 0.0;
+    out->E = s->occ * s->h_out[0];
+    out->rnorm = std::sqrt(std::max(s->h_out[1], 0.0));
+    if (!std::isfinite(out->E) || !std::isfinite(out->rnorm)) {
+      s->err = "non-finite band energy or residual";
+      return EACG_ENAN;
+    }
+    return EACG_OK;
+  }
   // kinetic energy partials -> d_red[0..K*p), summed into d_out[0]
   dense_kin_energy(K, p, nm, s->d_kin, phi, s->d_kw, s->occ, s->d_red, s->st);
   dense_sum_partials(s->d_red, K * p, s->d_out + 0, s->st);
@@ -1935,6 +1968,74 @@ extern "C" eacg_status eacg_retract(eacg_system* s, const double* phi_dev, const
   CK(cudaStreamSynchronize(s->st));
   s->fresh = 1;
   return EACG_OK;
+}
+
+// Initial guess of the experiments (Sec. 5.2): SCF iterations until the density difference of
+// two successive iterates is below drho_tol.  Readings: the first input density is that of
+// polar(psi0); one step minimises the band energy of the Hamiltonian of the input density (this
+// library's warm-up and energy-adaptive iterations with the potential held fixed) to
+// ||H Phi - Phi Lambda||_F <= eig_tol; ||rho_out - rho_in||_2 is the L2 norm over the cell;
+// otherwise simple mixing rho_in <- rho_in + alpha (rho_out - rho_in).
+extern "C" eacg_status eacg_scf_guess(eacg_system* s, const double* psi0_dev, double drho_tol, double alpha,
+                                      int max_scf, double eig_tol, int* steps_out, double* history_host) {
+  SYS_CHECK(s);
+  DENSE_CHECK(s);
+  if (!psi0_dev || !(drho_tol > 0) || !(alpha > 0 && alpha <= 1) || max_scf < 1 || !(eig_tol > 0))
+    return EACG_EINVAL;
+  if (steps_out) *steps_out = 0;
+  const size_t N3 = (size_t)s->N * s->N * s->N;
+  const size_t nh = N3 / 2;  // real grids viewed as complex pairs (every supported N is even)
+  if (!s->d_rho_in) TRY(dalloc(s, &s->d_rho_in, sizeof(double) * N3));
+  CK(cudaMemcpyAsync(s->tmp2, psi0_dev, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
+  TRY(polar(s, s->tmp2, s->phi, s->eval, s->evec, s->sm3));
+  s->have_psi = 1;
+  s->h_apps = 0;
+  s->ls_total = 0;
+  TRY(density_only(s, s->phi, 0));
+  CK(cudaMemcpyAsync(s->d_rho_in, s->d_rho, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s->st));
+  TRY(potential_from_rho(s));
+  const eacg_params saved = s->prm;
+  s->prm.res_tol = eig_tol;
+  s->frozen = true;
+  bool inner = false;  // an inner minimisation failed (its message is kept)
+  double2* rin = reinterpret_cast<double2*>(s->d_rho_in);
+  double2* rout = reinterpret_cast<double2*>(s->d_rho);
+  double2* delta = s->d_fft3;  // scratch: rebuilt by the next potential build
+  auto iterate = [&]() -> eacg_status {
+    for (int step = 1; step <= max_scf; ++step) {
+      s->fresh = 1;
+      eacg_step_info info;
+      eacg_status e = EACG_OK;
+      do {
+        e = do_step(s, &info);
+      } while (e == EACG_OK && !info.converged);
+      if (e != EACG_OK) {
+        inner = true;
+        return e;
+      }
+      TRY(density_only(s, s->phi, 0));
+      dense_axpby(nh, ONE, rout, MONE, rin, delta, s->st);
+      dense_norms2(1, nh, delta, s->d_out, s->st);
+      CKL(s);
+      TRY(sync_read(s, 1));
+      const double d = std::sqrt(s->omega / (double)N3 * std::max(s->h_out[0], 0.0));
+      if (history_host) history_host[step - 1] = d;
+      if (steps_out) *steps_out = step;
+      if (d < drho_tol) return EACG_OK;
+      dense_axpby(nh, ONE, rin, cr(alpha), delta, rin, s->st);
+      CK(cudaMemcpyAsync(s->d_rho, s->d_rho_in, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s->st));
+      TRY(potential_from_rho(s));
+    }
+    return EACG_ENOTCONV;
+  };
+  const eacg_status st = iterate();
+  // leave the system in its normal mode whatever happened
+  s->frozen = false;
+  s->prm = saved;
+  s->fresh = 1;  // the next step evaluates Phi with its own density and potential
+  if (st == EACG_ENOTCONV && !inner) s->err = "SCF did not reach the density tolerance within max_scf steps";
+  CK(cudaStreamSynchronize(s->st));
+  return st;
 }
 
 extern "C" eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, const float* b_dev,
