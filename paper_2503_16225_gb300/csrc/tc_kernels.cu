@@ -300,9 +300,7 @@ void dense_overlap_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA
                           size_t sB, int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta,
                           double2* work, const int* kactive, cudaStream_t st) {
   if (K <= 0 || m <= 0 || n <= 0) return;
-  static const bool attr =
-      cudaFuncSetAttribute(k_overlap_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess;
-  (void)attr;
+  ensure_smem((const void*)k_overlap_tf32x3, TC_SMEM);  // per device
   const int nch = (L + TC_CHUNK - 1) / TC_CHUNK;
   if (nch > 0) {
     const int tiles = ((m + TC_M - 1) / TC_M) * ((n + TC_N - 1) / TC_N);
