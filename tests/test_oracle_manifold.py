@@ -267,3 +267,39 @@ def test_oracle_defaults_are_the_paper_constants():
     for key in ("delta", "sigma", "gamma", "eps", "mu", "fom_rtol"):
         assert getattr(prm, key) == c[key]["value"], key
     assert min(prm.sigma, 1 - 2 * prm.delta) == c["wolfe_curvature_factor"]["value"]
+
+
+def test_tpa_shift_of_a_plane_wave_orbital_is_its_kinetic_energy():
+    """alpha_i (orbital-wise mean kinetic energy, the TPA shift of Sec. 5.2) of an orbital that
+    is one plane wave e^{i(k+G)r} equals 1/2 |k+G|^2."""
+    m = Model(small(nb=2, kgrid=(2, 1, 1)))
+    for k in range(m.K):
+        n = m.nk[k]
+        j1, j2 = 3, n - 5
+        Phi = np.zeros((n, 2), complex)
+        Phi[j1, 0] = 1.0
+        Phi[j2, 1] = 1j
+        kf = m.kfrac[k]
+        want = [0.5 * m.b ** 2 * float(((m.basis[k][j] + kf) ** 2).sum()) for j in (j1, j2)]
+        np.testing.assert_allclose(earcg.kinetic_alpha(m, [Phi if q == k else np.eye(m.nk[q], 2)
+                                                           for q in range(m.K)])[k], want, rtol=1e-14)
+
+
+def test_preconditioned_direction_is_tangent_and_a_descent_direction():
+    """g = Z - Phi herm(Phi^* Z), Z = P^-1 R: Phi^* g is skew-Hermitian (tangent) and
+    <R, g> = <R, P^-1 R> > 0 because Phi^* R = 0 and P^-1 is positive; with P^-1 of unit gain
+    at |k+G| = 0 the direction shrinks every plane-wave component of R."""
+    m = Model(small(nproj=4, nb=3, kgrid=(2, 1, 1)))
+    Phi = earcg.lowdin(start(m))
+    pt = earcg.evaluate(m, Phi)
+    g = earcg.precond_gradient(m, pt)
+    for k in range(m.K):
+        M = Phi[k].conj().T @ g[k]
+        assert np.abs(M + M.conj().T).max() < 1e-12
+    from oracle.model import pairing
+    rg = pairing(m, pt.R, g)
+    assert rg > 0
+    alpha = earcg.kinetic_alpha(m, Phi)
+    for k in range(m.K):
+        Z = fom.tpa_inverse(m.kin[k], alpha[k])(pt.R[k]) * alpha[k][None, :]
+        assert np.all(np.abs(Z) <= np.abs(pt.R[k]) * (1 + 1e-15))
