@@ -16,7 +16,8 @@ H as the DFTK-style Hamiltonian -1/2 Laplacian + V of Sec. 5.2):
   * xc = 2 adds LDA correlation: the spin-unpolarised Perdew-Wang 1992 fit of the homogeneous
     electron gas correlation energy per electron, eps_c(r_s), r_s = (3 / (4 pi rho))^{1/3},
     E_c = int rho eps_c, V_c = eps_c - (r_s / 3) d eps_c / d r_s (the paper's experiments use
-    DFTK's LDA model, Sec. 5.3; its correlation is this fit);
+    DFTK's LDA model, Sec. 5.3; its correlation is this fit; the fitted constants alpha1,
+    beta3, beta4: parity unpinned beyond a 1 mHa agreement with the Perdew-Zunger fit);
   * Nyquist planes and G = 0 of every potential are zero;
   * s/p Gaussian projectors beta_al(G) = Omega^{-1/2} F_l(k+G) exp(-i (k+G).R_a)
     with coupling D_al; E_nl = sum_k w_k f sum_i sum_al D_al |<beta_al, c_i>|^2;
