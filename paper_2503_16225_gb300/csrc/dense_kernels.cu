@@ -881,7 +881,6 @@ void dense_norms2(int K, size_t len, const double2* V, double* out, cudaStream_t
 void dense_copy(double2* dst, const double2* src, size_t n, cudaStream_t st) {
   cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
 }
-void dense_zero(double2* dst, size_t n, cudaStream_t st) { cudaMemsetAsync(dst, 0, n * sizeof(double2), st); }
 
 __global__ void k_tpa(int p, int n_max, const double* __restrict__ kin, const double* __restrict__ alpha,
                       const double2* __restrict__ in, double2* __restrict__ out, bool unit_gain) {

@@ -409,8 +409,6 @@ void grid_xmap(int N, int K, int n_max, const int* nk, const int* m, const int* 
   k_xmap<<<grid, 256, 0, st>>>(N, K, n_max, nk, m, colidx, ncols, xmap);
   count_launch();
 }
-void grid_fill_int(int* p, size_t n, int v, cudaStream_t st) { k_fill_int<<<256, 256, 0, st>>>(p, n, v);
-  count_launch(); }
 void grid_vloc_g(int N, double b, double omega, int natoms, const double* pos, const double* Z, const double* rc,
                  double2* out, cudaStream_t st) {
   k_vloc_g<<<1024, 256, 0, st>>>(N, b, omega, natoms, pos, Z, rc, out);

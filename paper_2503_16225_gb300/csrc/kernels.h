@@ -41,7 +41,6 @@ void grid_columns(int N, const int* colmark, int* colidx, int* cmapy, int* rowma
                   cudaStream_t st);
 void grid_xmap(int N, int K, int n_max, const int* nk, const int* m, const int* colidx, int ncols, int* xmap,
                cudaStream_t st);
-void grid_fill_int(int* p, size_t n, int v, cudaStream_t st);
 void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, int nbands, const int* kactive,
                     cudaStream_t st);
 void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
@@ -136,9 +135,8 @@ int dense_dot(int K, size_t len, const double2* V, const double2* W, const doubl
 void dense_sum_partials(const double* partials, int n, double* out, cudaStream_t st);
 // Per-k Frobenius norm squared of blocks [K][len] -> out[K] (deterministic).
 void dense_norms2(int K, size_t len, const double2* V, double* out, cudaStream_t st);
-// Copy / zero helpers
+// Copy helper
 void dense_copy(double2* dst, const double2* src, size_t n, cudaStream_t st);
-void dense_zero(double2* dst, size_t n, cudaStream_t st);
 // Column-wise TPA preconditioner: out[k][i][g] = in * scale_i / (kin[k][g] + alpha[k][i]).
 void dense_tpa(int K, int p, int n_max, const double* kin, const double* alpha, const double2* in, double2* out,
                bool unit_gain, cudaStream_t st);
