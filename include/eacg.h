@@ -259,6 +259,17 @@ eacg_status eacg_overlap_noalloc(int K, int n, int p, const double* a_dev, const
 eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, const float* b_dev, double* c_dev,
                              int method, void* stream);
 
+/* Back-projection of the nonlocal term (Sec. 5.1: H Psi += B (D P)) for complex64 projector
+ * blocks: c_k += a_k q_k for k < K, a_k L x m complex64 ([K][m][L], column-major, ld L),
+ * q_k m x n complex double ([K][n][m]), c_k L x n complex double ([K][n][L]); caller-owned
+ * device buffers.  method 0: SIMT FP32 products (FP32 accumulation), result added in FP64;
+ * 1: tensor cores (tcgen05, 3 x TF32 split, accumulation runs of 48 MMAs summed with
+ * round-to-nearest FP32 adds) for 16 <= n <= 256 with n a multiple of 16, else
+ * EACG_EUNSUPPORTED.  stream: cudaStream_t or NULL; returns after synchronising it.
+ * EACG_EINVAL for negative sizes or null buffers. */
+eacg_status eacg_backproject_c64(int K, int L, int m, int n, const float* a_dev, const double* q_dev, double* c_dev,
+                                 int method, void* stream);
+
 /* Initial guess of the experiments (Sec. 5.2): self-consistent field iterations until the
  * density difference of two successive iterates is below drho_tol (0.1 in the paper).  The
  * first input density is that of polar(psi0) (psi0: caller's device buffer [K][p][n_max]);

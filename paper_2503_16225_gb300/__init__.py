@@ -19,7 +19,7 @@ __all__ = [
     "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
-    "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
+    "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_backproject_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
 ]
 
 # band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
@@ -109,6 +109,8 @@ def _load():
         "eacg_overlap_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "eacg_overlap_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                             ctypes.c_int, vp]),
+        "eacg_backproject_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                                vp, ctypes.c_int, vp]),
         "eacg_scf_guess": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           _ip, _dp]),
     }
@@ -326,6 +328,14 @@ def eacg_scf_guess(sys, psi0, tol=0.1, alpha=0.5, max_scf=100, eig_tol=1e-10):
     _check(sys, lib.eacg_scf_guess(sys, _ptr(psi0), float(tol), float(alpha), int(max_scf), float(eig_tol),
                                    ctypes.byref(steps), hist))
     return list(hist[:steps.value])
+
+
+def eacg_backproject_c64(a, q, c, method=1, stream=None):
+    """c[k] += a[k] q[k] for complex64 a [K, m, L], complex128 q [K, n, m] and complex128 c
+    [K, n, L] (column-major per k); method 1 = tensor cores, 0 = SIMT FP32.  Returns the status."""
+    K, m, L = a.shape
+    n = q.shape[1]
+    return int(lib.eacg_backproject_c64(K, L, m, n, _ptr(a), _ptr(q), _ptr(c), int(method), _stream(stream)))
 
 
 def eacg_overlap_c64(a, b, c, method=1, stream=None):

@@ -640,8 +640,12 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
                projector_overlaps32(s, in32, kactive);
                dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
                dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
-               dense_gemm_nn32_into64(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out,
-                                      (size_t)p * nm, nm, ONE, ONE, kactive, s->st);
+               if (s->tc_proj && dense_backproject_tc_eligible(np, p))
+                 dense_backproject_tf32x3(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np,
+                                          out, (size_t)p * nm, nm, kactive, s->st);
+               else
+                 dense_gemm_nn32_into64(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np,
+                                        out, (size_t)p * nm, nm, ONE, ONE, kactive, s->st);
              });
     CKL(s);
   }
@@ -2063,6 +2067,29 @@ extern "C" eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float*
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaFree(work);
+  return e == cudaSuccess ? EACG_OK : EACG_ECUDA;
+}
+
+extern "C" eacg_status eacg_backproject_c64(int K, int L, int m, int n, const float* a_dev, const double* q_dev,
+                                            double* c_dev, int method, void* stream) {
+  if (K < 0 || L < 0 || m < 0 || n < 0 || method < 0 || method > 1) return EACG_EINVAL;
+  if (K == 0 || L == 0 || n == 0) return EACG_OK;
+  if (!a_dev || !q_dev || !c_dev) return EACG_EINVAL;
+  if (method == 1 && !dense_backproject_tc_eligible(m, n)) return EACG_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* A = reinterpret_cast<const float2*>(a_dev);
+  const double2* Q = reinterpret_cast<const double2*>(q_dev);
+  double2* C = reinterpret_cast<double2*>(c_dev);
+  if (m > 0) {
+    if (method)
+      dense_backproject_tf32x3(K, L, m, n, A, (size_t)m * L, L, Q, (size_t)n * m, m, C, (size_t)n * L, L, nullptr,
+                               st);
+    else
+      dense_gemm_nn32_into64(K, L, m, n, A, (size_t)m * L, L, Q, (size_t)n * m, m, C, (size_t)n * L, L, ONE, ONE,
+                             nullptr, st);
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? EACG_OK : EACG_ECUDA;
 }
 

@@ -82,6 +82,13 @@ size_t dense_overlap_tc_work(int K, int L, int m, int n);
 void dense_overlap_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const float2* B,
                           size_t sB, int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta,
                           double2* work, const int* kactive, cudaStream_t st);
+// Back-projection C_k += A_k Q_k on the tensor cores (same split and accumulation): A_k L x m
+// complex64 ([m][lda]), Q_k m x n complex double ([n][ldq]), C_k L x n complex double
+// ([n][ldc]).  Eligible: 16 <= n <= 256, n a multiple of 16.
+bool dense_backproject_tc_eligible(int m, int n);
+void dense_backproject_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* Q,
+                              size_t sQ, int ldq, double2* C, size_t sC, int ldc, const int* kactive,
+                              cudaStream_t st);
 void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
                    const int* kactive, cudaStream_t st);

@@ -288,6 +288,192 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// Back-projection C_k += A_k Q_k (the nonlocal term's H Psi += B (D P)): A_k is L x m complex64
+// stored column by column ([m][lda], the projectors), Q_k is m x n complex double ([n][ldq]),
+// C_k is L x n complex double ([n][ldc]).  With the rows of C interleaved (re, im) and the
+// reduction index interleaved the same way, C' = A_exp Q' is one real GEMM of M = 2L, K = 2m:
+//   A_exp[2l][2i] = ar, A_exp[2l][2i+1] = -ai, A_exp[2l+1][2i] = ai, A_exp[2l+1][2i+1] = ar,
+//   Q'[j][2i] = qr, Q'[j][2i+1] = qi (B operand, K-major: a column of Q is a row).
+// Same 3 x TF32 split, stages of 16 complex reduction indices, accumulation runs of 48 MMAs
+// summed in the other half of the tensor memory, bounded waits, as k_overlap_tf32x3.  CTA =
+// 128 interleaved rows (64 rows of C) x all n <= 256 columns.  Warps 0-3 move the
+// accumulators (row 32 w + lane); all 8 warps stage the operands.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_backproject_tf32x3(int L, int m, int n, const float2* __restrict__ A, size_t sA, int lda,
+                         const double2* __restrict__ Q, size_t sQ, int ldq, double2* __restrict__ C, size_t sC,
+                         int ldc, const int* __restrict__ kactive) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  const int k = blockIdx.y;
+  if (kactive && !kactive[k]) return;
+  const int l0 = blockIdx.x * (TC_M / 2);  // first row of C of this tile
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float2* Ak = A + k * sA;
+  const double2* Qk = Q + k * sQ;
+  const uint32_t mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  // columns [0, n): the current run's accumulator; [256, 256 + n): the sum of the runs
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = tc_idesc(n);
+  const int nstage = (m + TC_ROWS - 1) / TC_ROWS;
+  const bool mover = warp < 4;  // warps that read and write the accumulators
+  const uint32_t tcol = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t tsum = tcol + 256u;
+  // staging maps: A elements (row l0 + la, reduction index ia + 4 q), coalesced along rows;
+  // Q elements (column rq + 16 q, reduction index cq) as in k_overlap_tf32x3
+  const int la = tid & 63, ia = tid >> 6;
+  const int cq = (tid & 3) + 4 * ((tid >> 5) & 3), rq = ((tid >> 2) & 7) + 8 * (tid >> 7);
+  float2 ra[4], rb[16];
+  auto load_stage = [&](int s) {
+    const int i0 = s * TC_ROWS;
+    const int l = l0 + la;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + ia + 4 * q;
+      ra[q] = (l < L && i < m) ? Ak[(size_t)i * lda + l] : make_float2(0.f, 0.f);
+    }
+    const int i = i0 + cq;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = rq + 16 * q;
+      if (j < n) {
+        const double2 v = (i < m) ? Qk[(size_t)j * ldq + i] : make_double2(0.0, 0.0);
+        rb[q] = make_float2((float)v.x, (float)v.y);
+      }
+    }
+  };
+  bool failed = false;
+  int issued = 0;
+  if (nstage > 0) load_stage(0);
+  for (int s = 0; s < nstage; ++s) {
+    const int buf = s & 1;
+    unsigned char* st = smem + buf * TC_STAGE;
+    if (s >= 2) {
+      const bool ok = tc_wait(buf ? mb1 : mb0, (uint32_t)(((s >> 1) - 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+    }
+    // A_exp hi/lo: rows 2 la and 2 la + 1, reals 2 i and 2 i + 1
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 a = ra[q];
+      const float hr = tf32_hi(a.x), hi_ = tf32_hi(a.y);
+      const float lr = a.x - hr, li = a.y - hi_;
+      const int c = ia + 4 * q;
+      const int o0 = tc_off(2 * la, c), o1 = tc_off(2 * la + 1, c);
+      *reinterpret_cast<float2*>(st + o0) = make_float2(hr, -hi_);
+      *reinterpret_cast<float2*>(st + o1) = make_float2(hi_, hr);
+      *reinterpret_cast<float2*>(st + TC_TILE_A + o0) = make_float2(lr, -li);
+      *reinterpret_cast<float2*>(st + TC_TILE_A + o1) = make_float2(li, lr);
+    }
+    // Q' hi/lo: rows = columns of Q (up to 256 rows: two 16 KB halves per part)
+    unsigned char* sb = st + 2 * TC_TILE_A;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = rq + 16 * q;
+      if (j < n) {
+        const float2 b = rb[q];
+        const float hr = tf32_hi(b.x), hi_ = tf32_hi(b.y);
+        const int o = tc_off(j, cq);
+        *reinterpret_cast<float2*>(sb + o) = make_float2(hr, hi_);
+        *reinterpret_cast<float2*>(sb + 2 * TC_TILE_B + o) = make_float2(b.x - hr, b.y - hi_);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t base = smem_u32(st);
+      const uint32_t aH = base, aL = base + TC_TILE_A;
+      const uint32_t bH = base + 2 * TC_TILE_A, bL = bH + 2 * TC_TILE_B;
+      for (int ks = 0; ks < TC_KT / 8; ++ks) {
+        const uint32_t ko = (uint32_t)ks * 256u;
+        const uint32_t first = (s % TC_FLUSH == 0 && ks == 0) ? 0u : 1u;
+        tc_mma(tmem, tc_desc(aH + ko), tc_desc(bH + ko), idesc, first);
+        tc_mma(tmem, tc_desc(aH + ko), tc_desc(bL + ko), idesc, 1u);
+        tc_mma(tmem, tc_desc(aL + ko), tc_desc(bH + ko), idesc, 1u);
+      }
+      tc_commit(buf ? mb1 : mb0);
+    }
+    issued = s + 1;
+    if (s + 1 < nstage) load_stage(s + 1);
+    if ((s + 1) % TC_FLUSH == 0 || s + 1 == nstage) {
+      const bool ok = tc_wait(buf ? mb1 : mb0, (uint32_t)((s >> 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (mover) {
+        const bool first_run = s < TC_FLUSH;
+        for (int c0 = 0; c0 < n; c0 += 16) {
+          uint32_t v[16], w[16];
+          tmem_ld16(tcol + (uint32_t)c0, v);
+          if (!first_run) {
+            tmem_ld16(tsum + (uint32_t)c0, w);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+          }
+          tmem_st16(tsum + (uint32_t)c0, v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+    }
+  }
+  {
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+      if (issued > b) {
+        const int sb = ((issued - 1 - b) >> 1) * 2 + b;
+        ok = tc_wait(b ? mb1 : mb0, (uint32_t)((sb >> 1) & 1)) && ok;
+      }
+    }
+    failed = __syncthreads_or(!ok) || failed;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  // epilogue: interleaved row 32 w + lane -> row l of C, part re/im; C += the sums (FP64)
+  if (mover && nstage > 0) {
+    const int r = 32 * warp + (tid & 31);
+    const int l = l0 + (r >> 1), part = r & 1;
+    double* out = reinterpret_cast<double*>(C + k * sC);
+    for (int c0 = 0; c0 < n; c0 += 16) {
+      uint32_t v[16];
+      if (!failed) {
+        tmem_ld16(tsum + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0x7FC00000u;  // NaN marks a wait that gave up
+      }
+      if (l < L) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) out[2 * ((size_t)(c0 + q) * ldc + l) + part] += (double)__uint_as_float(v[q]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
 }  // namespace
 
 bool dense_overlap_tc_eligible(int m, int n) { return m >= TC_M && n >= 16 && n % 16 == 0; }
@@ -309,6 +495,18 @@ void dense_overlap_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA
     count_launch();
   }
   dense_cn_reduce(K, m, n, nch, work, C, sC, ldc, alpha, beta, kactive, st);
+}
+
+bool dense_backproject_tc_eligible(int m, int n) { return m >= 1 && n >= 16 && n <= 256 && n % 16 == 0; }
+
+void dense_backproject_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* Q,
+                              size_t sQ, int ldq, double2* C, size_t sC, int ldc, const int* kactive,
+                              cudaStream_t st) {
+  if (K <= 0 || L <= 0 || m <= 0 || n <= 0) return;
+  ensure_smem((const void*)k_backproject_tf32x3, TC_SMEM);  // per device
+  dim3 g((L + TC_M / 2 - 1) / (TC_M / 2), K);
+  k_backproject_tf32x3<<<g, TC_THREADS, TC_SMEM, st>>>(L, m, n, A, sA, lda, Q, sQ, ldq, C, sC, ldc, kactive);
+  count_launch();
 }
 
 }  // namespace eacg

@@ -81,3 +81,32 @@ def test_tensor_core_and_simt_paths_agree_on_the_supercell_H():
         finally:
             s.close()
     assert np.abs(outs[0] - outs[1]).max() / np.abs(outs[1]).max() < 5e-6
+
+
+BP_SHAPES = [(1, 23847, 256, 128), (3, 1000, 130, 16), (2, 65, 5, 256), (1, 1, 16, 32)]
+
+
+@pytest.mark.parametrize("K,L,m,n", BP_SHAPES)
+@pytest.mark.parametrize("method", [1, 0])
+def test_backprojection_matches_fp64(K, L, m, n, method):
+    """c_k += a_k q_k (the nonlocal back-projection B (D P)): ragged 64-row tiles of C, ragged
+    16-index reduction stages, the largest column count (256), one row; c keeps what it held."""
+    rng = np.random.default_rng(L + 7 * m + n)
+    a = (rng.standard_normal((K, m, L)) + 1j * rng.standard_normal((K, m, L))).astype(np.complex64)
+    q = rng.standard_normal((K, n, m)) + 1j * rng.standard_normal((K, n, m))
+    c0 = rng.standard_normal((K, n, L)) + 1j * rng.standard_normal((K, n, L))
+    # column-major: C_k[l, j] = sum_i A_k[l, i] Q_k[i, j], A_k[l, i] = a[k, i, l], Q_k[i, j] = q[k, j, i]
+    prod = np.einsum("kil,kji->kjl", a.astype(np.complex128), q)
+    c = torch.from_numpy(c0.copy()).cuda()
+    assert E.eacg_backproject_c64(torch.from_numpy(a).cuda(), torch.from_numpy(q).cuda(), c, method) == 0
+    got = c.cpu().numpy() - c0
+    err = np.abs(got - prod).max() / np.abs(prod).max()
+    assert err < 2e-6, (method, err)
+
+
+def test_backprojection_ineligible_shapes():
+    a = torch.zeros((1, 16, 64), dtype=torch.complex64, device="cuda")
+    for n in (20, 272):
+        q = torch.zeros((1, n, 16), dtype=torch.complex128, device="cuda")
+        c = torch.zeros((1, n, 64), dtype=torch.complex128, device="cuda")
+        assert E.eacg_backproject_c64(a, q, c, 1) == 9
