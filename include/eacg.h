@@ -109,9 +109,11 @@ typedef struct {
                        * (same warm-up; then eta = -G with an alternating Barzilai-Borwein step
                        * and Zhang-Hager non-monotone backtracking, rho 0.85, delta 1e-4).
                        * Default 0 */
-  int tensor_cores;   /* 1: projector overlaps of complex64 blocks (FP32 phase, FP32 FOM) on the
-                       * tensor cores (see eacg_overlap_c64, method 1) where nproj >= 128 and
-                       * nbands is a multiple of 16; 0: SIMT FP32.  Default 1 */
+  int tensor_cores;   /* 1: where nproj >= 128 and nbands is a multiple of 16, the projector
+                       * overlaps of complex64 blocks (FP32 phase, FP32 FOM; eacg_overlap_c64,
+                       * method 1) and the back-projection of FP32-phase evaluations (nbands <= 256;
+                       * eacg_backproject_c64, method 1) on the tensor cores; 0: SIMT FP32.
+                       * Default 1 */
 } eacg_params;
 
 typedef struct {
