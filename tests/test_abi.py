@@ -58,3 +58,31 @@ def test_binding_band_limits_match_the_header():
     for name in ("EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE"):
         val = int(re.search(rf"#define {name} (\d+)", src).group(1))
         assert getattr(E, name) == val, name
+
+
+def _header_struct_fields(name):
+    """Field names of a typedef struct { ... } name; in include/eacg.h, in order."""
+    src = open(os.path.join(ROOT, "include", "eacg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    end = re.search(r"\}\s*" + name + ";", src).start()
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[[^\]]*\]", "", decl)          # array extents
+        for part in decl.split(","):                       # the declared name ends each part
+            fields.append(re.findall(r"[A-Za-z_]\w*", part)[-1])
+    return fields
+
+
+def test_binding_structs_match_the_header_layout():
+    """The ctypes mirrors of the ABI structs list the header's fields in the header's order
+    (a mismatch would shift every later field silently)."""
+    ensure_library()
+    import paper_2503_16225_gb300 as E
+    for cname, py in (("eacg_model", E.EacgModel), ("eacg_params", E.EacgParams),
+                      ("eacg_step_info", E.EacgStepInfo), ("eacg_result", E.EacgResult),
+                      ("eacg_kernel_stat", E.EacgKernelStat)):
+        assert _header_struct_fields(cname) == [f[0] for f in py._fields_], cname
