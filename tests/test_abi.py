@@ -86,3 +86,20 @@ def test_binding_structs_match_the_header_layout():
                       ("eacg_step_info", E.EacgStepInfo), ("eacg_result", E.EacgResult),
                       ("eacg_kernel_stat", E.EacgKernelStat)):
         assert _header_struct_fields(cname) == [f[0] for f in py._fields_], cname
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every entry point the binding declares takes as many arguments as its header prototype."""
+    lib = ctypes.CDLL(ensure_library())
+    import paper_2503_16225_gb300 as E
+    src = open(os.path.join(ROOT, "include", "eacg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    checked = 0
+    for name, args in re.findall(r"\b(eacg_[A-Za-z_0-9]+)\s*\(([^)]*)\)\s*;", src, flags=re.S):
+        fn = getattr(E.lib, name, None)
+        if fn is None or fn.argtypes is None:
+            continue
+        n = 0 if args.strip() in ("", "void") else len(args.split(","))
+        assert len(fn.argtypes) == n, name
+        checked += 1
+    assert checked >= 20 and lib is not None
