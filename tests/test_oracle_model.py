@@ -214,3 +214,19 @@ def test_synthetic_configs_are_well_formed():
     assert synth.mp_grid(4, 4, 4)[0].shape == (64, 3)
     assert np.all(synth.mp_grid(4, 4, 4)[0] >= -0.5) and np.all(synth.mp_grid(4, 4, 4)[0] < 0.5)
     assert len(c2["pos"]) == 8 and c2["nbands"] == 16
+
+
+def test_workload_sizes():
+    """Plane waves at Gamma of the four crystal workloads: two-atom 1,503 (32^3 grid, 2 bands),
+    diamond8 2,945 (48^3, 16 bands), diamond64 23,847 (96^3, 128 bands, 256 projectors),
+    diamond216 80,725 (128^3, 432 bands, 864 projectors)."""
+    from oracle.model import sphere_basis
+    cases = [(synth.config_two_atom(1), 1503, 32, 2, 0),
+             (synth.config_diamond(2, kgrid=(1, 1, 1)), 2945, 48, 16, 32),
+             (synth.config_diamond_supercell(2), 23847, 96, 128, 256),
+             (synth.config_diamond_supercell(3), 80725, 128, 432, 864)]
+    for cfg, n, N, p, nproj in cases:
+        b = 2 * math.pi / cfg["a"]
+        assert len(sphere_basis(cfg["N"], np.zeros(3), cfg["ecut"], b)) == n
+        assert cfg["N"] == N and cfg["nbands"] == p
+        assert len(cfg["pos"]) * cfg["nproj_per_atom"] == nproj
