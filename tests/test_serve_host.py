@@ -98,3 +98,23 @@ def test_failed_request_does_not_stop_the_server(monkeypatch):
     assert outs[1].status.startswith("failed") and not outs[1].converged
     assert outs[0].converged and outs[2].converged
     assert tr.count == 0   # every system was closed
+
+
+def test_serving_stream_requests_are_valid_models():
+    """The 256 seeded requests of the serving stream: an even electron count (bands = sum Z / 2),
+    1-16 atoms, 1-27 k-points, a grid that holds the cutoff sphere with the margin of the
+    potential's frequencies (N >= 4 m_max + 1), and a model the library accepts (positive HBM
+    estimate, computed on the host)."""
+    import math
+    import numpy as np
+    import synth
+    ensure_library()
+    import paper_2503_16225_gb300 as E
+    for i in range(256):
+        cfg = synth.config_serving_request(i)
+        Z = np.asarray(cfg["Z"])
+        assert int(Z.sum()) % 2 == 0 and cfg["nbands"] == int(Z.sum()) // 2
+        assert 1 <= len(Z) <= 16 and len(cfg["kweight"]) in (1, 8, 27)
+        mmax = math.sqrt(2.0 * cfg["ecut"]) / (2.0 * math.pi / cfg["a"])
+        assert cfg["N"] >= 4 * mmax + 1
+        assert E.eacg_bytes_required(cfg)[0] > 0, i
