@@ -1,6 +1,8 @@
-// Block overlaps C_k = A_k^* B_k of complex64 blocks on the fifth-generation tensor cores
-// (tcgen05.mma kind::tf32, accumulators in tensor memory), for the projector overlaps
-// P = B^* Psi of the nonlocal term (Sec. 5.1) in the FP32 phase of the mixed precision.
+// The two projector contractions of the nonlocal term (Sec. 5.1) for complex64 blocks on the
+// fifth-generation tensor cores (tcgen05.mma kind::tf32, accumulators in tensor memory), used
+// in the FP32 phase of the mixed precision: the block overlaps C_k = A_k^* B_k
+// (k_overlap_tf32x3, P = B^* Psi) and the back-projection C_k += A_k Q_k
+// (k_backproject_tf32x3, H Psi += B (D P), below).
 //
 // Complex to real: with the complex rows of a column interleaved (re, im) along the
 // reduction index (2 L reals),
