@@ -150,7 +150,11 @@ size_t eacg_bytes_required(const eacg_model* model, const eacg_params* prm, size
 /* Builds the basis (Sec. 5.1), local potential and projectors on the device.
  * stream: a cudaStream_t (NULL = legacy default stream).  *out owns all device state. */
 eacg_status eacg_create_system(const eacg_model* model, const eacg_params* prm, void* stream, eacg_system** out);
+/* Synchronises the system's stream and frees every device and pinned host buffer the system
+ * owns; NULL is ignored.  Resource management only, the paper has no counterpart. */
 void eacg_destroy(eacg_system* sys);
+/* Message of the last failing call on sys ("null system" for NULL); owned by the system and
+ * valid until its next call.  Error reporting only, the paper has no counterpart. */
 const char* eacg_last_error(const eacg_system* sys);
 
 /* n_k per k-point (nk_host: K ints, may be NULL), n_max = max n_k, union column count. */
@@ -181,6 +185,10 @@ eacg_status eacg_get_basis(const eacg_system* sys, int* m_dev);
 /* Sets the iterate to pf(psi) (polar factor, Eq. (3.1)) of a raw block and resets the
  * CG state; the next eacg_step starts Algorithm 3 from it. */
 eacg_status eacg_set_psi(eacg_system* sys, const double* psi_dev);
+/* Copies the current iterate Phi = (Phi_k) of the product of Stiefel manifolds (Sec. 5.1,
+ * Eq. (5.1)) into psi_dev_out, a caller-owned device buffer [K][p][n_max] in the block
+ * layout above (orthonormal columns per k; entries n_k .. n_max-1 zero).  EACG_EINVAL before
+ * the first eacg_set_psi. */
 eacg_status eacg_get_psi(eacg_system* sys, double* psi_dev_out);
 
 /* Density rho(r_j) = sum_k w_k f sum_i |u_ik(r_j)|^2 of an orthonormal block (Sec. 1),
@@ -234,14 +242,15 @@ int eacg_profile_read(eacg_system* sys, eacg_kernel_stat* out, int max);
 long long eacg_launch_count(void);
 
 /* Allocation-free block overlaps (the paper has no counterpart; this serves callers that
- * cannot allocate device memory, e.g. code inside a pool that forbids cudaMalloc or a step
- * that must not allocate between graph replays).  Computes c_k = a_k^* b_k for k < K, where
+ * cannot allocate device memory, e.g. code running inside a memory pool or framework that
+ * owns all device allocations and forbids cudaMalloc).  Computes c_k = a_k^* b_k for k < K, where
  * a_k, b_k are n x p complex double blocks (column-major, ld n, laid out [K][p][n]) and c_k
  * is p x p column-major ([K][p][p]); all three are caller-owned device buffers.  Needs no
  * system and calls no allocator: its scratch is a fixed device array of
  * EACG_NOALLOC_MAX_PARTIALS complex doubles (8 MiB), held by every GPU that loads the library
  * until the process exits, and shared by all calls.  Returns EACG_EINVAL when
- * K * ceil(n / 1024) * p * p exceeds EACG_NOALLOC_MAX_PARTIALS or an argument is invalid.
+ * K * ceil(n / 1024) * p * p exceeds EACG_NOALLOC_MAX_PARTIALS, K exceeds 65535 (one grid row
+ * per k-point) or an argument is invalid.
  * The first call on a device looks up the scratch address for that device (make it before
  * any stream capture).  stream: cudaStream_t or NULL; the call returns after synchronising
  * it.  Calls that overlap on the GPU (other host threads or streams) race on the scratch. */
@@ -290,10 +299,14 @@ eacg_status eacg_scf_guess(eacg_system* sys, const double* psi0_dev, double drho
 
 /* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
 eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);
-/* Iterates eacg_step until ||R||_F <= res_tol or max_outer; result in *out. */
+/* Algorithm 3 to convergence: iterates eacg_step from the current iterate until the
+ * residual ||R||_F of Sec. 5.3 is <= res_tol (status EACG_OK) or max_outer iterations
+ * (EACG_ENOTCONV); E, ||R||_F and the counts in *out (out may not be NULL).  Errors of a step
+ * end the solve with that step's status. */
 eacg_status eacg_solve(eacg_system* sys, eacg_result* out);
-/* eacg_set_psi + eacg_solve + eacg_get_psi through host buffers (copies on the system's
- * stream; psi0_host and psi_out_host are [K][p][n_max] complex double, may alias). */
+/* eacg_set_psi + eacg_solve + eacg_get_psi (Algorithm 3 from pf(psi0)) through host buffers
+ * (copies on the system's stream; psi0_host and psi_out_host are [K][p][n_max] complex
+ * double, may alias). */
 eacg_status eacg_solve_host(eacg_system* sys, const double* psi0_host, double* psi_out_host, eacg_result* out);
 
 #ifdef __cplusplus

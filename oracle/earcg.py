@@ -113,17 +113,21 @@ def precond_gradient(model: Model, pt: Point):
     return g
 
 
-def ea_gradient(model: Model, pt: Point, prm: Params, stats=None):
+def ea_gradient(model: Model, pt: Point, prm: Params, stats=None, fixed_iters=None):
     """G_k = Phi_k - X_k (Phi_k^* X_k)^{-1} with H X - X Sigma = Phi, Sigma = Lambda - mu I
-    (Sec. 5.2, Eq. (5.2)), X by Algorithm 4 per k."""
+    (Sec. 5.2, Eq. (5.2)), X by Algorithm 4 per k.  fixed_iters (one count per k, optional)
+    replaces the stopping test of block k by exactly that many FOM iterations (fewer only on
+    a rank-0 block), so that another implementation's iterate after the same number of
+    iterations can be compared directly."""
     alpha = kinetic_alpha(model, pt.Phi)
     G = []
     p = model.p
     for k in range(model.K):
         Sigma = pt.Lam[k] - prm.mu * np.eye(p)
+        rtol, cap = (prm.fom_rtol, prm.max_fom) if fixed_iters is None else (0.0, int(fixed_iters[k]))
         X, it, rel, ncols = fom_mod.fom(
             lambda V, k=k: model.apply_H(k, V, pt.vtot), pt.Phi[k], pt.HPhi[k], Sigma, prm.mu,
-            fom_mod.tpa_inverse(model.kin[k], alpha[k]), prm.fom_rtol, prm.max_fom)
+            fom_mod.tpa_inverse(model.kin[k], alpha[k]), rtol, cap)
         if stats is not None:
             stats["fom_iters"].append(it)
             stats["h_cols"] += ncols

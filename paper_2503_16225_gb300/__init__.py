@@ -316,7 +316,13 @@ def eacg_launch_count():
 def eacg_overlap_noalloc(a, b, c, stream=None):
     """c[k] = a[k]^* b[k] for complex128 tensors a, b [K, p, n] and c [K, p, p] (column-major
     p x p per k), through the allocation-free entry point; returns the eacg_status code."""
+    import torch
     K, p, n = a.shape
+    for t, shape in ((a, (K, p, n)), (b, (K, p, n)), (c, (K, p, p))):
+        if (tuple(t.shape) != shape or t.dtype != torch.complex128 or not t.is_cuda
+                or not t.is_contiguous()):
+            raise ValueError(f"eacg_overlap_noalloc: expected contiguous complex128 CUDA tensors "
+                             f"a, b [K, p, n] and c [K, p, p]; got {tuple(t.shape)} {t.dtype}")
     return int(lib.eacg_overlap_noalloc(K, n, p, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
 
 

@@ -58,14 +58,17 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // ----------------------------------------------------------------------------- A^H B
 // Templated on the block precision T (double or float): A and B are cplx<T>, the products
 // are accumulated in T within a chunk of rows, the chunk partials and the result are FP64.
-// A CTA computes one 16 x 16 tile of C over one chunk of CN_CHUNK rows with G = 1, 2 or 4 groups
-// of 256 threads, each group taking every G-th stage of CN_SUB rows; the groups' tiles are
-// summed in a fixed order in shared memory (one partial per chunk, deterministic).  G is picked
-// per shape by dense_tune_cn (timed at system set-up, cached for the process); untuned shapes
-// use 4.
+// A CTA computes one 16 x 16 tile of C over one chunk of CN_CHUNK rows.  The chunk is read in
+// rounds of CN_LANES stages of CN_SUB rows; stage v of every round belongs to summation lane v,
+// whose products accumulate in their own T-precision sum, and the lane sums are added in FP64
+// in lane order at the end.  G = 1, 2 or 4 groups of 256 threads share the lanes (group g takes
+// lanes g, g + G, ...), so every G performs the same additions in the same order and gives
+// bitwise the same partial: the tile choice (dense_tune_cn, timed at system set-up and cached
+// for the process; untuned shapes use 4) changes only the speed.
 constexpr int CN_TILE = 16;
 constexpr int CN_CHUNK = 1024;  // rows per partial
-constexpr int CN_SUB = 16;      // rows staged per step and group
+constexpr int CN_SUB = 16;      // rows per stage
+constexpr int CN_LANES = 4;     // summation lanes (stages per round)
 
 size_t dense_cn_work(int K, int L, int m, int n) {
   const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
@@ -85,6 +88,8 @@ __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
                       const cplx<T>* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
                       const int* __restrict__ kactive) {
   using V = cplx<T>;
+  constexpr int PER = CN_LANES / CN_GROUPS;  // lanes per group
+  constexpr int NT = CN_TILE * CN_TILE * CN_GROUPS;
   const int k = blockIdx.z;
   if (kactive && !kactive[k]) return;
   const int tiles_m = (m + CN_TILE - 1) / CN_TILE;
@@ -93,35 +98,42 @@ __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
   const int g = threadIdx.x / (CN_TILE * CN_TILE), t = threadIdx.x % (CN_TILE * CN_TILE);
   const int ti = t % CN_TILE, tj = t / CN_TILE;
   const int i0 = tm * CN_TILE, j0 = tn * CN_TILE;
-  __shared__ V sa[CN_GROUPS][CN_SUB][CN_TILE + 1];
-  __shared__ V sb[CN_GROUPS][CN_SUB][CN_TILE + 1];
+  __shared__ V sa[CN_LANES][CN_SUB][CN_TILE + 1];
+  __shared__ V sb[CN_LANES][CN_SUB][CN_TILE + 1];
   const V* Ak = A + k * sA;
   const V* Bk = B + k * sB;
   V zero;
   zero.x = 0;
   zero.y = 0;
-  V acc = zero;
+  V acc[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) acc[i] = zero;
   const int l_beg = ch * CN_CHUNK, l_end = min(L, l_beg + CN_CHUNK);
-  for (int s0 = l_beg; s0 < l_end; s0 += CN_SUB * CN_GROUPS) {  // uniform trip count over the CTA
-    const int l0 = s0 + g * CN_SUB;
-    for (int e = t; e < CN_SUB * CN_TILE; e += CN_TILE * CN_TILE) {
-      const int c = e / CN_SUB, r = e - c * CN_SUB;
-      const int l = l0 + r;
-      sa[g][r][c] = (l < l_end && i0 + c < m) ? Ak[(size_t)(i0 + c) * lda + l] : zero;
-      sb[g][r][c] = (l < l_end && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + l] : zero;
+  for (int s0 = l_beg; s0 < l_end; s0 += CN_SUB * CN_LANES) {  // uniform trip count over the CTA
+    for (int e = threadIdx.x; e < CN_LANES * CN_SUB * CN_TILE; e += NT) {
+      const int v = e / (CN_SUB * CN_TILE), w = e - v * (CN_SUB * CN_TILE);
+      const int c = w / CN_SUB, r = w - c * CN_SUB;
+      const int l = s0 + v * CN_SUB + r;
+      sa[v][r][c] = (l < l_end && i0 + c < m) ? Ak[(size_t)(i0 + c) * lda + l] : zero;
+      sb[v][r][c] = (l < l_end && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + l] : zero;
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < CN_SUB; ++r) acc = cfmac(sa[g][r][ti], sb[g][r][tj], acc);
+    for (int i = 0; i < PER; ++i) {
+      const int v = g + i * CN_GROUPS;
+#pragma unroll
+      for (int r = 0; r < CN_SUB; ++r) acc[i] = cfmac(sa[v][r][ti], sb[v][r][tj], acc[i]);
+    }
     __syncthreads();
   }
-  // fixed-order sum of the groups' tiles
-  V* red = &sa[0][0][0];  // CN_GROUPS * 256 values fit in sa (CN_SUB * (CN_TILE + 1) >= 256)
-  red[g * CN_TILE * CN_TILE + t] = acc;
+  // lane sums added in lane order (CN_LANES * 256 values fit in sa)
+  V* red = &sa[0][0][0];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) red[(g + i * CN_GROUPS) * CN_TILE * CN_TILE + t] = acc[i];
   __syncthreads();
   if (g == 0 && i0 + ti < m && j0 + tj < n) {
     double2 sum = to_d(red[t]);
-    for (int q = 1; q < CN_GROUPS; ++q) sum = sum + to_d(red[q * CN_TILE * CN_TILE + t]);
+    for (int v = 1; v < CN_LANES; ++v) sum = sum + to_d(red[v * CN_TILE * CN_TILE + t]);
     part[(((size_t)k * nch + ch) * n + (j0 + tj)) * m + (i0 + ti)] = sum;
   }
 }

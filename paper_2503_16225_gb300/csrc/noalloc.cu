@@ -2,8 +2,8 @@
 //
 // eacg_overlap_noalloc computes the same block overlaps A_k^* B_k as the library's Gram
 // kernels, for callers that cannot allocate device memory themselves: code running inside
-// a memory pool that forbids cudaMalloc, a host process whose allocations are owned by
-// another runtime, or a step that must not allocate between graph replays.  Its one piece
+// a memory pool that forbids cudaMalloc, or a host process whose device allocations are all
+// owned by another runtime that would not see (or would fail) a cudaMalloc of ours.  Its one piece
 // of scratch (the partial sums of the split reduction) is a fixed array in this file's
 // device memory, so the call itself never allocates.  Every GPU that loads the library
 // holds that array until the process exits.
@@ -45,6 +45,7 @@ cudaError_t scratch_address(void** out) {
 extern "C" eacg_status eacg_overlap_noalloc(int K, int n, int p, const double* a_dev, const double* b_dev,
                                             double* c_dev, void* stream) {
   if (K < 1 || n < 1 || p < 1 || !a_dev || !b_dev || !c_dev) return EACG_EINVAL;
+  if (K > 65535) return EACG_EINVAL;  // the kernels take one grid row (z or y) per k-point
   if (eacg::dense_cn_work(K, n, p, p) > (size_t)EACG_NOALLOC_MAX_PARTIALS) return EACG_EINVAL;
   void* work = nullptr;
   if (scratch_address(&work) != cudaSuccess) {

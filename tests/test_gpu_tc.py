@@ -114,37 +114,43 @@ def test_backprojection_ineligible_shapes():
 
 def test_fom_projector_overlaps_on_tensor_cores_inside_graphs():
     """32 atoms with 4 projectors each (nproj = 128) and 32 bands: the FP32 FOM's projector
-    overlaps take the tensor-core kernel, captured in the FOM's CUDA graph and replayed.  The
-    FOM stops at a relative residual of 2.5e-2, so FP32-level differences between the two
-    overlap kernels can move its stopping iteration by one at this random point (14 and 15
-    here): the gradients are compared where the counts agree, and the tensor-core gradient is
-    checked to be tangent at Phi (Phi^* G = 0 for G = Phi - X (Phi^* X)^-1) either way."""
+    overlaps take the tensor-core kernel, captured in the FOM's CUDA graph and replayed.  At a
+    point eight warm-up iterations in (Sec. 5.2's setting: the shifted operator is near its
+    coercive regime, Prop. 4) the gradient of both overlap kernels equals, element by element,
+    the oracle's gradient after the same number of FOM iterations per k (Algorithm 4), within
+    the FP32 bound of the mixed-mode FOM (1e-4 of max |G|; FP32 Krylov blocks and transforms,
+    the 2.5e-2 stopping test is far above that)."""
     import synth
+    from oracle import earcg
+    from oracle.model import Model
     rng = np.random.default_rng(31)
     pos = rng.uniform(0.0, 12.0, size=(32, 3))
     cfg = synth._config("tc_fom", 12.0, pos, [2] * 32, [1.0] * 32, 4, 0.7,
                         rng.uniform(0.5, 2.0, size=(32, 2)), 3.0, 16, 32, (1, 1, 1), 31)
-    grads, iters, replays, phis = [], [], [], []
+    model = Model(cfg)
+    raw = synth.raw_coefficients(cfg["seed"], model.nk, model.p)
+    Psi0 = [raw[k, :, :model.nk[k]].T.copy() for k in range(model.K)]
+    Phi = earcg.solve(model, Psi0, earcg.Params(max_outer=8), warm=True).Phi
+    pt = earcg.evaluate(model, Phi)
+    stats = {"fom_iters": [], "h_cols": 0}
+    earcg.ea_gradient(model, pt, earcg.Params(), stats)
+    n = model.nk[0]
     for tc in (1, 0):
         st = torch.cuda.Stream()
         s = E.System(cfg, E.eacg_default_params(precision=1, tensor_cores=tc), stream=st.cuda_stream)
         try:
-            n = s.nk[0]
-            Q = np.linalg.qr(rng.standard_normal((n, s.p)) + 1j * rng.standard_normal((n, s.p)))[0] if tc else Q
+            assert s.nk == model.nk
             t = torch.zeros((1, s.p, s.n_max), dtype=torch.complex128)
-            t[0, :, :n] = torch.from_numpy(np.ascontiguousarray(Q.T))
+            t[0, :, :n] = torch.from_numpy(np.ascontiguousarray(Phi[0].T))
             phi, g = t.cuda(), s.block()
             torch.cuda.synchronize()
-            iters.append(E.eacg_ea_gradient(s.h, phi, g, 1, 1))
-            grads.append(g.cpu().numpy()[0, :, :n].T)
-            phis.append(Q)
-            replays.append(E.eacg_graph_launches(s.h))
+            iters = E.eacg_ea_gradient(s.h, phi, g, 1, 1)
+            got = g.cpu().numpy()[0, :, :n].T
+            replays = E.eacg_graph_launches(s.h)
         finally:
             s.close()
-    assert iters[0][0] >= 3 and replays[0] > 0
-    M = phis[0].conj().T @ grads[0]
-    assert np.abs(M + M.conj().T).max() < 1e-2 * max(1.0, np.abs(grads[0]).max())
-    if iters[0] == iters[1]:
-        assert np.abs(grads[0] - grads[1]).max() / np.abs(grads[1]).max() < 1e-4
-    else:
-        assert abs(iters[0][0] - iters[1][0]) <= 2
+        assert iters[0] >= 3 and replays > 0, (iters, replays)
+        assert abs(iters[0] - stats["fom_iters"][0]) <= 1, (iters, stats["fom_iters"])
+        want = earcg.ea_gradient(model, pt, earcg.Params(), fixed_iters=iters)[0]
+        err = np.abs(got - want).max() / np.abs(want).max()
+        assert err < 1e-4, (tc, iters, err)

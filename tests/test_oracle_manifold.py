@@ -82,6 +82,39 @@ def test_transport_is_the_derivative_of_the_retraction():
     np.testing.assert_allclose(transport_general(Phi, xi, eta), fd, atol=1e-8)
 
 
+def test_algorithm3_transports_are_the_retraction_derivatives():
+    """earcg.transports (the two transports of each EARCG step, Sec. 3.2; they feed beta,
+    Sec. 3.4, and the BB step of EARGD) on two k-blocks of different sizes: T(eta) equals
+    the closed form and the central difference of t -> pf(Phi + (tau + t) eta); T(g) equals
+    the general Lyapunov form and the central difference of t -> pf(Phi + tau eta + t g).
+    A sign slip in the Lyapunov right-hand side, or the old point's Phi where the new one
+    belongs, moves T(g) by O(1) against both references."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(11)
+    tau, h = 0.43, 1e-5
+    base, new, eta, g = [], [], [], []
+    for n, p in ((27, 3), (19, 3)):
+        Phi = _stiefel(rng, n, p)
+        e = 0.8 * _tangent(Phi, _rand(rng, n, p))
+        base.append(Phi)
+        eta.append(e)
+        g.append(_tangent(Phi, _rand(rng, n, p)))
+        new.append(polar(Phi + tau * e)[0])
+    Teta, Tg = earcg.transports(SimpleNamespace(Phi=base), SimpleNamespace(Phi=new), eta, g, tau,
+                                SimpleNamespace(K=2))
+    for k in range(2):
+        Phi, e, gk = base[k], eta[k], g[k]
+        np.testing.assert_allclose(Teta[k], transport_self(Phi, tau, e), atol=1e-12)
+        fd_eta = (polar(Phi + (tau + h) * e)[0] - polar(Phi + (tau - h) * e)[0]) / (2 * h)
+        np.testing.assert_allclose(Teta[k], fd_eta, atol=1e-8)
+        np.testing.assert_allclose(Tg[k], transport_general(Phi, tau * e, gk), atol=1e-12)
+        fd_g = (polar(Phi + tau * e + h * gk)[0] - polar(Phi + tau * e - h * gk)[0]) / (2 * h)
+        np.testing.assert_allclose(Tg[k], fd_g, atol=1e-8)
+        # both transports are tangent at the new point (Eq. (2.3))
+        assert tangent_defect(new[k], Teta[k]) < 1e-12
+        assert tangent_defect(new[k], Tg[k]) < 1e-12
+
+
 def test_projected_sylvester_matches_library_solver():
     rng = np.random.default_rng(4)
     A = _rand(rng, 9, 9)
@@ -160,6 +193,34 @@ def test_fom_galerkin_condition_and_stopping_rule():
     rj = np.linalg.norm(H @ X - X @ Sig - Phi[0])
     assert rj <= 2.5e-2 * r0 + 1e-12
     assert abs(rj / r0 - rel) < 1e-10
+
+
+def test_ea_gradient_with_fixed_iteration_counts():
+    """ea_gradient(fixed_iters=...) runs exactly the given FOM iteration count per k: with the
+    counts the stopping test chose it reproduces the default result bit for bit, and with one
+    more iteration per k it gives the iterate of the FOM run for exactly that many iterations
+    (Algorithm 4; a Galerkin method, so its residual need not fall monotonically)."""
+    m = Model(small(nproj=4, nb=3, ecut=3.0, kgrid=(2, 1, 1)))
+    pt = earcg.evaluate(m, earcg.lowdin(start(m)))
+    prm = earcg.Params()
+    stats = {"fom_iters": [], "h_cols": 0}
+    G = earcg.ea_gradient(m, pt, prm, stats)
+    its = stats["fom_iters"]
+    assert all(i >= 1 for i in its)
+    G2 = earcg.ea_gradient(m, pt, prm, fixed_iters=its)
+    for a, b in zip(G, G2):
+        assert np.array_equal(a, b)
+    more = [i + 1 for i in its]
+    G3 = earcg.ea_gradient(m, pt, prm, fixed_iters=more)
+    for k in range(m.K):
+        Sig = pt.Lam[k] - prm.mu * np.eye(m.p)
+        alpha = earcg.kinetic_alpha(m, pt.Phi)[k]
+        for cap, rtol in ((its[k], prm.fom_rtol), (more[k], 0.0)):
+            X, it, rel, _ = fom.fom(lambda V: m.apply_H(k, V, pt.vtot), pt.Phi[k], pt.HPhi[k], Sig, prm.mu,
+                                    fom.tpa_inverse(m.kin[k], alpha), rtol=rtol, max_iter=cap)
+            assert it == cap
+        Gk = pt.Phi[k] - X @ np.linalg.inv(pt.Phi[k].conj().T @ X)
+        np.testing.assert_allclose(G3[k], Gk, atol=1e-12 * np.abs(Gk).max())
 
 
 def test_ea_gradient_with_uniform_shift_is_the_riesz_representative():

@@ -53,3 +53,17 @@ def test_overlap_noalloc_rejects_sizes_beyond_its_scratch():
     a = torch.zeros((K, p, n), dtype=torch.complex128, device="cuda")
     c = torch.zeros((K, p, p), dtype=torch.complex128, device="cuda")
     assert E.eacg_overlap_noalloc(a, a, c) == 1   # EACG_EINVAL
+    # more k-points than one grid row holds (65536 * 1 * 1 * 1 partials fit the scratch)
+    a1 = torch.zeros((65536, 1, 1), dtype=torch.complex128, device="cuda")
+    c1 = torch.zeros((65536, 1, 1), dtype=torch.complex128, device="cuda")
+    assert E.eacg_overlap_noalloc(a1, a1, c1) == 1
+    # mismatched operands are refused before the call
+    with pytest.raises(ValueError):
+        E.eacg_overlap_noalloc(a, a[:, :, :512], c)
+    # more k-points than one grid row holds (65536 * 1 * 1 * 1 partials fit the scratch)
+    a1 = torch.zeros((65536, 1, 1), dtype=torch.complex128, device="cuda")
+    c1 = torch.zeros((65536, 1, 1), dtype=torch.complex128, device="cuda")
+    assert E.eacg_overlap_noalloc(a1, a1, c1) == 1
+    # mismatched operands are refused before the call
+    with pytest.raises(ValueError):
+        E.eacg_overlap_noalloc(a, a[:, :, :512], c)
