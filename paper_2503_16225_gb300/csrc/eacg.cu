@@ -98,6 +98,7 @@ struct eacg_system {
   size_t fom_es = sizeof(double2);  // element bytes of the Krylov blocks V, W
   // ---- iteration state
   int fresh = 1, have_psi = 0, phase = 0, iter = 0, warm_iter = 0, cur_prec = 0;
+  int eval_prec = 0;  // transform precision of the evaluation of the current point
   double E = 0, rnorm = 0, tau = 1, rg = 0;
   double nm_C = 0, nm_Q = 1;  // EARGD: non-monotone reference value and its weight
   int ea_steps = 0;           // EARGD: energy-adaptive steps taken (alternates the BB formula)
@@ -1447,9 +1448,9 @@ static void swap_trial_into_current(eacg_system* s) {
 
 static eacg_status start_iteration(eacg_system* s) {
   EvalOut ev;
-  s->cur_prec = step_precision(s);
   s->cur_prec = s->prm.precision ? 1 : 0;
   TRY(evaluate(s, s->phi, s->hphi, s->res, s->lam, s->cur_prec, &ev));
+  s->eval_prec = s->cur_prec;
   s->E = ev.E;
   s->rnorm = ev.rnorm;
   std::memcpy(s->eterms, ev.terms, sizeof(ev.terms));
@@ -1470,6 +1471,32 @@ static eacg_status start_iteration(eacg_system* s) {
   return EACG_OK;
 }
 
+// The current point evaluated again with transforms of precision prec (mixed mode, when the
+// step's precision differs from the one its energy came from): the step-size test of
+// Algorithm 2 then compares energies and slopes of one precision.  The direction is kept while
+// it is still a descent direction for the new residual, else it restarts from -g.
+static eacg_status reevaluate(eacg_system* s, int prec) {
+  EvalOut ev;
+  TRY(evaluate(s, s->phi, s->hphi, s->res, s->lam, prec, &ev));
+  s->E = ev.E;
+  s->rnorm = ev.rnorm;
+  std::memcpy(s->eterms, ev.terms, sizeof(ev.terms));
+  s->eval_prec = prec;
+  if (s->rnorm <= s->prm.res_tol) return EACG_OK;
+  pairing_dev(s, s->res, s->eta, 0, true);
+  pairing_dev(s, s->res, s->gv, 1, true);
+  CKL(s);
+  TRY(sync_read(s, 2));
+  s->rg = s->h_out[1];
+  if (!(s->h_out[0] < 0)) {
+    int kind;
+    TRY(direction(s, prec, &s->rg, &kind));
+    dense_axpby(s->blk, MONE, s->gv, ZERO, nullptr, s->eta, s->st);
+    CKL(s);
+  }
+  return EACG_OK;
+}
+
 static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
   if (!s->have_psi) {
     s->err = "no iterate: call eacg_set_psi first";
@@ -1477,6 +1504,8 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
   }
   if (s->fresh) TRY(start_iteration(s));
   if (info) std::memset(info, 0, sizeof(*info));
+  int prec = step_precision(s);
+  if (s->rnorm > s->prm.res_tol && prec != s->eval_prec) TRY(reevaluate(s, prec));
   if (s->rnorm <= s->prm.res_tol) {
     if (info) {
       info->E = s->E;
@@ -1491,11 +1520,10 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
     s->err = "outer iteration cap reached";
     return EACG_ENOTCONV;
   }
-  int prec = step_precision(s);
   // f'(0) = 2 f <r, eta>
   pairing_dev(s, s->res, s->eta, 0, true);
   TRY(sync_read(s, 1));
-  const double df0 = 2.0 * s->occ * s->h_out[0];
+  double df0 = 2.0 * s->occ * s->h_out[0];
   double tau = 0;
   TrialOut acc;
   int trials = 0;
@@ -1506,12 +1534,28 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
   };
   eacg_status st = search();
   if (st == EACG_ELINESEARCH && prec == 1) {
-    // FP32 transforms can no longer resolve the energy decrease: continue in FP64
+    // FP32 transforms can no longer resolve the energy decrease: continue in FP64, from the
+    // current point evaluated in FP64
     s->prm.switch_res = std::max(s->prm.switch_res, 2.0 * s->rnorm);
     prec = 0;
+    TRY(reevaluate(s, 0));
+    if (s->rnorm <= s->prm.res_tol) {
+      if (info) {
+        info->E = s->E;
+        info->rnorm = s->rnorm;
+        info->converged = 1;
+        info->phase = s->phase;
+        info->h_band_apps = s->h_apps;
+      }
+      return EACG_OK;
+    }
+    pairing_dev(s, s->res, s->eta, 0, true);
+    TRY(sync_read(s, 1));
+    df0 = 2.0 * s->occ * s->h_out[0];
     st = search();
   }
   if (st != EACG_OK) return st;
+  s->eval_prec = prec;  // the accepted trial becomes the current point
   if (gd) {
     const double Qn = NM_RHO * s->nm_Q + 1.0;
     s->nm_C = (NM_RHO * s->nm_Q * s->nm_C + acc.ev.E) / Qn;

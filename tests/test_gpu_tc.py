@@ -118,8 +118,9 @@ def test_fom_projector_overlaps_on_tensor_cores_inside_graphs():
     point eight warm-up iterations in (Sec. 5.2's setting: the shifted operator is near its
     coercive regime, Prop. 4) the gradient of both overlap kernels equals, element by element,
     the oracle's gradient after the same number of FOM iterations per k (Algorithm 4), within
-    the FP32 bound of the mixed-mode FOM (1e-4 of max |G|; FP32 Krylov blocks and transforms,
-    the 2.5e-2 stopping test is far above that)."""
+    the FP32 bound of the mixed-mode FOM (5e-4 of max |G|, as for the FP32-Krylov gradient of
+    the parity tests: FP32 Krylov blocks and transforms, fifty times below the FOM's 2.5e-2
+    stopping test)."""
     import synth
     from oracle import earcg
     from oracle.model import Model
@@ -153,4 +154,4 @@ def test_fom_projector_overlaps_on_tensor_cores_inside_graphs():
         assert abs(iters[0] - stats["fom_iters"][0]) <= 1, (iters, stats["fom_iters"])
         want = earcg.ea_gradient(model, pt, earcg.Params(), fixed_iters=iters)[0]
         err = np.abs(got - want).max() / np.abs(want).max()
-        assert err < 1e-4, (tc, iters, err)
+        assert err < 5e-4, (tc, iters, err)
