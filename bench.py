@@ -1,13 +1,29 @@
 #!/usr/bin/env python
-"""Benchmark: converged eARCG solves per second of the 8-atom diamond crystal
-(4x4x4 k-points, 48^3 grid, 16 bands, Ecut 15 Ha) on one GB300, from the seeded
-random start to ||R||_F <= 1e-8, with the Hamiltonian-application bandwidth and the
-roofline of the dominant kernel.  One step = one complete solve.
+"""Benchmark: served eARCG solves per second on one GB300.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+Default workload: the serving stream of 256 seeded synthetic crystals
+(synth.config_serving_request: cubic cells a 6-14 bohr with 1-16 atoms of Z 1-4, 0/1/4 Gaussian
+projectors per atom, Ecut 8-20 Ha, 1-23 bands, 1, 8 or 27 k-points, grids 20^3-64^3), each
+solved from its seeded random start to ||R||_F <= 1e-8 in mixed precision, admitted by HBM
+budget and slot count and served with continuous batching (one system, CUDA stream and host
+thread per resident request).  One step = ceil(256 / K) consecutive requests of the stream;
+the timed region queues the K steps' requests at t = 0 (saturating load) and serves them
+continuously, so that it covers the whole stream once.
 
-Multi-GPU: replicas only (each rank solves its own copy; no collective on the data path).
+Beside the headline: the same stream through host buffers (e2e), the plain FP64
+one-system-at-a-time solve rate on a sample of the stream (the denominator of the served
+speed-up), p50/p99 arrival-to-converged latency of Poisson streams at 0.5x and 2x that FP64
+rate, the energy error per atom against stored oracle solves, the roofline of the dominant
+kernel (timed on the sample solved one at a time, no overlapping kernels) and the CPU oracle
+timed on sampled requests.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+  python bench.py --impl reference ...          # the FP64 CPU oracle on sampled requests
+  python bench.py --workload diamond_k444|two_atom|...   # one-workload solve benches
+  python bench.py --op apply_h --workload diamond64_gamma # a few calls of one operation
+
+Multi-GPU: replicas only (each rank serves its own copy of the stream; no collective on the
+data path).
 """
 from __future__ import annotations
 
@@ -26,8 +42,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_BYTES = 129 * 2 ** 20
-# FP64 FMA throughput of a GB300 from unit counts and the maximum SM clock:
-# 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (a probe measured 1.196 TFLOP/s at ~2.0 GHz)
+STREAM = 256                 # requests of the serving stream
+FP64_SAMPLE_STRIDE = 16      # the FP64 one-at-a-time sample: every 16th request of the stream
+# FMA throughput of a GB300 from unit counts and the maximum SM clock (a probe measured
+# 1.196 TFLOP/s FP64 and 69.7 TFLOP/s FP32 at ~2.0 GHz)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of single-kernel
@@ -36,74 +54,40 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2
 NCU_TRAFFIC_BYTES = {"plane_h_f64": 393.6e6, "plane_h_f32": 170.0e6}
 # profile slots that time exactly one kernel (the roofline is reported for the top one)
 SINGLE_KERNEL_SLOTS = ("plane_h", "plane_rho", "xpass_inv", "xpass_fwd", "xpass_rho", "fom_solve")
+# profile slots of the H application and density (algorithmic H-psi bytes)
+HPSI_SLOTS = ("xpass_inv", "plane_h", "xpass_fwd", "nonlocal", "xpass_rho", "plane_rho", "nonlocal_eval")
+GOLDEN_SERVING = os.path.join(ROOT, "tests", "golden", "oracle_serving.json")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="diamond_k444",
-                    choices=["diamond_k444", "diamond_k222", "two_atom", "diamond64_gamma", "diamond64_k222"],
-                    help="diamond64_*: the 64-atom supercell (96^3 grid, 128 bands, 256 projectors), "
-                         "--op runs only (its p x p dense steps exceed the 64-band limit)")
-    ap.add_argument("--serve", type=int, default=0,
-                    help="serve a stream of this many synthetic crystals instead (Poisson arrivals)")
-    ap.add_argument("--rate", type=float, default=2.0, help="arrival rate of the serving stream (requests/s)")
-    ap.add_argument("--resident", type=int, default=8, help="maximum resident requests while serving")
+    ap.add_argument("--workload", default="serving_stream",
+                    choices=["serving_stream", "diamond_k444", "diamond_k222", "two_atom", "diamond64_gamma",
+                             "diamond64_k222"],
+                    help="serving_stream: the 256-request stream (headline); the others: concurrent solves "
+                         "of one workload; diamond64_*: the 64-atom supercell (96^3 grid, 128 bands, 256 "
+                         "projectors), --op runs only (its p x p dense steps exceed the 64-band limit)")
+    ap.add_argument("--resident", type=int, default=16, help="maximum resident requests while serving")
     ap.add_argument("--op", default="solve", choices=["solve", "apply_h", "density", "ea_gradient"],
                     help="apply_h / density / ea_gradient: time a few calls of one operation on the "
                          "workload's start point instead of solves (short runs under a profiler)")
     ap.add_argument("--method", default="earcg", choices=["earcg", "eargd"],
                     help="eargd: the paper's gradient-descent comparator (BB step, non-monotone backtracking)")
     ap.add_argument("--concurrent", type=int, default=4,
-                    help="resident systems solved concurrently (own stream and host thread each); "
-                         "value = whole-job served solves/s")
-    ap.add_argument("--no-fp64-ref", action="store_true",
-                    help="skip the plain FP64 one-system solve that the served number is compared with")
+                    help="one-workload solves: resident systems solved concurrently (own stream and host "
+                         "thread each)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the host-buffer (e2e) solves and the CPU baseline (short runs under a profiler)")
+                    help="only the timed region (short runs under a profiler): no e2e, FP64 sample, Poisson "
+                         "latency runs or CPU baseline")
     return ap.parse_args()
 
 
-def run_serve(args):
-    """Continuous-batching stream: requests i = 0..n-1 of the serving generator arrive as a
-    seeded Poisson process; reports converged solves/s and p50/p99 arrival-to-converged latency."""
-    import numpy as np
-    import torch
-    import synth
-    from paper_2503_16225_gb300 import serve
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(7)
-    t = 0.0
-    reqs = []
-    for i in range(args.serve):
-        cfg = synth.config_serving_request(i)
-
-        def raw(nk, n_max, cfg=cfg):
-            return torch.from_numpy(synth.raw_coefficients(cfg["seed"], nk, cfg["nbands"], n_max))
-        reqs.append(serve.Request(rid=i, cfg=cfg, raw=raw, arrival=t))
-        t += rng.exponential(1.0 / args.rate)
-    free, total = torch.cuda.mem_get_info()
-    prec = 1 if args.precision == "mixed" else 0
-    srv = serve.Server(hbm_budget=int(0.8 * free), max_resident=args.resident, precision=prec)
-    t0 = time.perf_counter()
-    outs = srv.run(reqs)
-    wall = time.perf_counter() - t0
-    st = serve.latency_stats(outs)
-    line = {"metric": "served eARCG solves/s (synthetic crystal stream, to ||R||<=1e-8)",
-            "value": st["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.serve, "warmup": 0,
-            "ms_per_step": wall * 1e3 / max(1, args.serve), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32/f64" if prec else "f64", "data": "synthetic",
-            "config": {"workload": "serving_stream", "requests": args.serve, "rate_per_s": args.rate,
-                       "max_resident": args.resident, "precision": args.precision},
-            "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"]}, "converged": st["converged"],
-            "failed": [o.status for o in outs if not o.converged]}
-    print(json.dumps(line))
-
-
+# ------------------------------------------------------------------------ shared helpers
 def rank_env():
     """(world size, rank, local rank) of this process, from the torchrun environment."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -126,17 +110,40 @@ def whole_job_rate(world, units_per_rank, ms):
     return world * units_per_rank / (ms / 1e3)
 
 
+def per_step(steps):
+    """Requests per step: the K steps cover the 256-request stream once."""
+    return int(math.ceil(STREAM / max(1, steps)))
+
+
+def stream_ids(start, count):
+    return [(start + j) % STREAM for j in range(count)]
+
+
+def fp64_sample_ids():
+    return list(range(0, STREAM, FP64_SAMPLE_STRIDE))
+
+
 WORKLOAD_LABEL = {"diamond_k444": "diamond8 4x4x4k 48^3 p16"}
 
 
-def metric_name(args, cfg):
+def metric_name(args, cfg=None):
     """The headline metric, shared by this arm and the reference arm."""
+    meth = "EARGD" if args.method == "eargd" else "eARCG"
+    if args.workload == "serving_stream":
+        return f"served {meth} solves/s (stream of {STREAM} synthetic crystals, to ||R||<=1e-8)"
     label = WORKLOAD_LABEL.get(args.workload, cfg["name"])
-    return f"served {'EARGD' if args.method == 'eargd' else 'eARCG'} solves/s ({label}, to ||R||<=1e-8)"
+    return f"served {meth} solves/s ({label}, to ||R||<=1e-8)"
 
 
 def config_of(args, cfg, world):
     """The workload description, shared by this arm and the reference arm."""
+    if args.workload == "serving_stream":
+        return {"workload": f"serving_stream_{STREAM}", "requests_per_step": per_step(args.steps),
+                "requests": "synth.config_serving_request(i), i < 256: a 6-14, 1-16 atoms, Z 1-4, Ecut 8-20, "
+                            "1/8/27 k, N 20-64, p 1-23",
+                "arrivals": "all queued at t=0 (saturating load)", "precision": args.precision,
+                "method": args.method, "parallelism": f"replicas{world}", "max_resident": args.resident,
+                "l2": "inputs of the stream (GBs) exceed L2; no flush"}
     return {"workload": cfg["name"], "kpoints": len(cfg["kweight"]), "bands": cfg["nbands"], "grid": cfg["N"],
             "ecut": cfg["ecut"], "precision": args.precision, "method": args.method,
             "parallelism": f"replicas{world}", "concurrent_systems": max(1, args.concurrent),
@@ -159,6 +166,18 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def golden_serving():
+    try:
+        with open(GOLDEN_SERVING) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
+
+
+def r4(x):
+    return None if x is None else float(f"{x:.4g}")
 
 
 class Clocks:
@@ -201,11 +220,81 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def profile_summary(prof, total_ms=None):
+    """Per-slot launches, ms, average ms, algorithmic GB/s and TFLOP/s (for stderr)."""
+    out = {}
+    for name, st in (prof or {}).items():
+        if st["ms"] <= 0:
+            continue
+        sec = st["ms"] / 1e3
+        out[name] = {"launches": st["launches"], "ms": round(st["ms"], 3), "avg_ms": st["ms"] / st["launches"],
+                     "GBps": st["bytes"] / sec / 1e9, "TFLOPs": st["flops"] / sec / 1e12}
+        if total_ms:
+            out[name]["share"] = st["ms"] / total_ms
+    return out
+
+
+def roofline_of(prof, traffic_table=None):
+    """Roofline of the single-kernel profile slot with the largest summed time: achieved
+    algorithmic FLOP/s per launch against the derived FP64 / FP32 ALU peak."""
+    single = {k: v for k, v in (prof or {}).items()
+              if k.rsplit("_", 1)[0] in SINGLE_KERNEL_SLOTS and v["ms"] > 0 and v["launches"] > 0}
+    if not single:
+        return None
+    top = max(single, key=lambda k: single[k]["ms"])
+    st = prof[top]
+    n = st["launches"]
+    avg_ms = st["ms"] / n
+    achieved = (st["flops"] / n) / (avg_ms / 1e3) / 1e12
+    if top.endswith("_f64"):
+        peak, pk = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz"
+    else:
+        peak, pk = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
+    hbm, hk = measured_peaks()
+    return {"bound": "alu", "kernel": top, "achieved": r4(achieved), "peak": r4(peak), "peak_kind": pk,
+            "unit": "TFLOP/s", "frac": r4(achieved / peak),
+            "traffic": (traffic_table or {}).get(top), "avg_launch_ms": r4(avg_ms), "launches": n,
+            "hbm_GBps_algorithmic": r4((st["bytes"] / n) / (avg_ms / 1e3) / 1e9), "hbm_peak_GBps": hbm,
+            "hbm_peak_kind": hk}
+
+
 # ------------------------------------------------------------------------ reference arm
+def oracle_serving_solves(ids):
+    """Full FP64 oracle solves of the given stream requests on the host cores: seconds each."""
+    import synth
+    from oracle import earcg
+    from oracle.model import Model
+    times = []
+    for i in ids:
+        cfg = synth.config_serving_request(i)
+        model = Model(cfg)
+        raw = synth.raw_coefficients(cfg["seed"], model.nk, model.p)
+        t0 = time.perf_counter()
+        res = earcg.solve(model, [raw[k, :, :model.nk[k]].T.copy() for k in range(model.K)])
+        times.append(time.perf_counter() - t0)
+        if res.status != "converged":
+            raise RuntimeError(f"oracle solve of request {i}: {res.status}")
+    return times
+
+
+def oracle_cpu_sample():
+    """The cheapest requests of the stored oracle sample (about 10-30 s of host work)."""
+    g = golden_serving()
+    if not g:
+        return []
+    rows = sorted(g["solves"].values(), key=lambda r: r["oracle_seconds"])
+    pick, tot = [], 0.0
+    for r in rows:
+        if tot > 12.0 and len(pick) >= 3:
+            break
+        pick.append(r["request"])
+        tot += r["oracle_seconds"]
+    return pick
+
+
 def oracle_sample(cfg, nk_sample=4):
     """One oracle evaluation (density of all k, potential, H applied at nk_sample k-points)
     timed on the host cores; returns seconds per band application of H and the cores."""
-    import numpy as np
     import synth
     from oracle.model import Model
     from oracle import earcg
@@ -221,9 +310,77 @@ def oracle_sample(cfg, nk_sample=4):
     for k in ks:
         model.apply_H(k, Phi[k], v)
     t_h = (time.perf_counter() - t1) / (len(ks) * model.p)
-    # density pass ~ half an H application per band
     per_band = t_h + t_dens / (model.K * model.p)
     return per_band, os.cpu_count(), f"oracle density of all {model.K} k-points + H at {len(ks)} k-points"
+
+
+def run_reference(args):
+    _, rank, _ = rank_env()
+    if rank != 0:
+        return
+    if args.workload == "serving_stream":
+        ids = oracle_cpu_sample()
+        if not ids:
+            print(json.dumps({"impl": "reference", "unavailable": "tests/golden/oracle_serving.json missing"}))
+            return
+        times = []
+        for j in range(args.warmup + args.steps):
+            t = oracle_serving_solves([ids[j % len(ids)]])[0]
+            if j >= args.warmup:
+                times.append(t)
+        value = len(times) / sum(times)
+        sample = (f"full FP64 oracle solves (warm-up + EARCG to ||R||<=1e-8) of stream requests {ids}, "
+                  f"cycled, one per step")
+        line = {"impl": "reference", "metric": metric_name(args), "value": value, "unit": "solves/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": config_of(args, None, args.gpus),
+                "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    cfg = workload(args.workload)
+    if args.workload == "two_atom":
+        times = []
+        for j in range(args.warmup + args.steps):
+            t = oracle_solve_seconds(cfg)
+            if j >= args.warmup:
+                times.append(t)
+        value, sample, kind = len(times) / sum(times), "full oracle solves of the workload, one per step", "oracle"
+    else:
+        apps, src = oracle_band_apps(args.workload)
+        times = []
+        for i in range(args.warmup + args.steps):
+            per_band, cores, smp = oracle_sample(cfg)
+            if i >= args.warmup:
+                times.append(per_band)
+        if apps is None:
+            apps, src = 15000 * len(cfg["kweight"]) * cfg["nbands"] // 1024, "estimate"
+        value = 1.0 / (statistics.median(times) * apps)
+        sample = f"{smp}; scaled by {apps} band applications per solve ({src})"
+        kind = "oracle (extrapolated from a timed sample)"
+    line = {"impl": "reference", "metric": metric_name(args, cfg),
+            "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config_of(args, cfg, args.gpus),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": kind,
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def oracle_solve_seconds(cfg):
+    import synth
+    from oracle import earcg
+    from oracle.model import Model
+    model = Model(cfg)
+    raw = synth.raw_coefficients(cfg["seed"], model.nk, model.p)
+    t0 = time.perf_counter()
+    res = earcg.solve(model, [raw[k, :, :model.nk[k]].T.copy() for k in range(model.K)])
+    if res.status != "converged":
+        raise RuntimeError(f"oracle solve: {res.status}")
+    return time.perf_counter() - t0
 
 
 def oracle_band_apps(name):
@@ -235,36 +392,223 @@ def oracle_band_apps(name):
     return None, None
 
 
-def run_reference(args):
-    _, rank, _ = rank_env()
-    if rank != 0:
-        return
-    cfg = workload(args.workload)
-    apps, src = oracle_band_apps(args.workload)
-    times = []
-    for i in range(args.warmup + args.steps):
-        per_band, cores, sample = oracle_sample(cfg)
-        if i >= args.warmup:
-            times.append(per_band)
-    per_band = statistics.median(times)
-    if apps is None:
-        apps, src = 15000 * len(cfg["kweight"]) * cfg["nbands"] // 1024, "estimate"
-    solve_s = per_band * apps
-    value = 1.0 / solve_s
-    line = {"impl": "reference", "metric": metric_name(args, cfg),
-            "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, cfg, args.gpus),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{sample}; scaled by {apps} band applications per solve ({src})"},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+# ------------------------------------------------------------------------ GPU arm: serving stream
+class StreamInputs:
+    """Seeded initial coefficients of stream requests: resident on the device (headline) and in
+    pinned host memory (end-to-end run), with pinned host result buffers."""
+
+    def __init__(self, ids, dev):
+        import torch
+        import synth
+        import paper_2503_16225_gb300 as E
+        self.cfg, self.dev, self.host, self.out = {}, {}, {}, {}
+        for i in sorted(set(ids)):
+            cfg = synth.config_serving_request(i)
+            s = E.System(cfg, E.eacg_default_params(precision=1))   # basis sizes of the request
+            raw = torch.from_numpy(synth.raw_coefficients(cfg["seed"], s.nk, s.p, s.n_max))
+            s.close()
+            self.cfg[i] = cfg
+            self.host[i] = raw.pin_memory()
+            self.dev[i] = self.host[i].to(dev)
+            self.out[i] = torch.empty_like(raw).pin_memory()
+        torch.cuda.synchronize()
+
+    def requests(self, ids, arrivals=None, host=False):
+        from paper_2503_16225_gb300 import serve
+        reqs = []
+        for j, i in enumerate(ids):
+            reqs.append(serve.Request(rid=j, cfg=self.cfg[i], raw=self.host[i] if host else self.dev[i],
+                                      arrival=0.0 if arrivals is None else arrivals[j],
+                                      out=self.out[i] if host else None))
+        return reqs
 
 
-# ------------------------------------------------------------------------ GPU arm
-def run_gpu(args):
+def serve_run(inputs, ids, precision, resident, profile=False, host=False, arrivals=None):
+    """Serves the requests; returns (device ms from one start event to the end of every request
+    stream, wall seconds, outcomes, summed kernel profile)."""
+    import torch
+    from paper_2503_16225_gb300 import serve
+    main = torch.cuda.current_stream()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(hbm_budget=int(0.8 * free), max_resident=resident, precision=precision,
+                       start_event=start, profile=profile, host_buffers=host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    start.record(main)
+    outs = srv.run(inputs.requests(ids, arrivals=arrivals, host=host))
+    for o in outs:
+        if o.end_event is not None:
+            main.wait_event(o.end_event)
+    stop.record(main)
+    stop.synchronize()
+    wall = time.perf_counter() - t0
+    return start.elapsed_time(stop), wall, outs, srv.profile
+
+
+def one_at_a_time(inputs, ids, precision, profile=False):
+    """Each request solved alone on a stream of its own (plain one-system-at-a-time solving):
+    CUDA-event ms per request, results, summed profile."""
+    import torch
+    import paper_2503_16225_gb300 as E
+    ms, res, prof = [], [], {}
+    for i in ids:
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = E.System(inputs.cfg[i], E.eacg_default_params(precision=precision), stream=st.cuda_stream)
+            if profile:
+                E.eacg_profile_enable(s.h, 1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            E.eacg_set_psi(s.h, inputs.dev[i])
+            r = E.eacg_solve(s.h, check=False)
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            res.append(r)
+            if profile:
+                for name, v in E.eacg_profile_read(s.h).items():
+                    acc = prof.setdefault(name, dict.fromkeys(v, 0))
+                    for key, x in v.items():
+                        acc[key] += x
+            s.close()
+    return ms, res, prof
+
+
+def accuracy_vs_oracle(outs, ids):
+    """|E - E_oracle| per atom for the stream requests that have a stored oracle solve."""
+    g = golden_serving()
+    if not g:
+        return None
+    errs = []
+    for o in outs:
+        i = ids[o.rid]
+        ref = g["solves"].get(str(i))
+        if ref is None or not o.converged:
+            continue
+        errs.append(abs(o.E - ref["E"]) / max(1, ref["natoms"]))
+    return {"max_dE_per_atom_Ha": r4(max(errs)) if errs else None, "requests": len(errs),
+            "tolerance": 1e-6, "oracle": "tests/golden/oracle_serving.json"}
+
+
+def run_serving(args):
     import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2503_16225_gb300 as E
+    from paper_2503_16225_gb300.serve import latency_stats
+
+    world, rank, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = 1 if args.precision == "mixed" else 0
+    M = per_step(args.steps)
+    timed = stream_ids(0, args.steps * M)
+    warm = stream_ids(0, args.warmup * M)
+    sample = fp64_sample_ids()
+    inputs = StreamInputs(timed + warm + sample, dev)
+    log = {}
+
+    # ---- warm-up: W steps of the stream (set-up caches: FFT plans, GEMM tiles per shape)
+    if warm:
+        serve_run(inputs, warm, prec, args.resident)
+
+    # ---- timed region: K steps (the whole stream), all queued at t = 0
+    clocks = Clocks(local)
+    launches0 = E.eacg_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, wall, outs, prof = serve_run(inputs, timed, prec, args.resident, profile=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = E.eacg_launch_count() - launches0
+    clk = clocks.stop()
+    conv = sum(1 for o in outs if o.converged)
+    total_ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(world, conv, total_ms)
+    st = latency_stats(outs)
+    hpsi_bytes = sum(v["bytes"] for k, v in prof.items() if k.rsplit("_", 1)[0] in HPSI_SLOTS)
+    failed = [f"{timed[o.rid]}: {o.status}" for o in outs if not o.converged]
+    log["served_profile_overlapped"] = profile_summary(prof, ms)
+
+    line = {
+        "metric": metric_name(args), "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64" if prec else "f64", "data": "synthetic", "config": config_of(args, None, world),
+        "converged": conv, "requests": len(outs), "failed": failed[:4],
+        "latency_s": {"saturated": {"solve_p50": r4(st["solve_p50_s"]), "solve_p99": r4(st["solve_p99_s"])}},
+        "hpsi_gbs": r4(hpsi_bytes / (ms / 1e3) / 1e9),
+        "gpu_launches": launches, "clocks": clk,
+    }
+    acc = accuracy_vs_oracle(outs, timed)
+    if acc:
+        line["accuracy"] = acc
+
+    if not args.no_extras:
+        # ---- end to end: the same stream through eacg_solve_host (pinned host input and output,
+        # copies inside each request), wall clock with a synchronize on both sides
+        torch.cuda.synchronize()
+        _, e2e_wall, e_outs, _ = serve_run(inputs, timed, prec, args.resident, host=True)
+        e2e_conv = sum(1 for o in e_outs if o.converged)
+        e2e_s = max_over_ranks(e2e_wall, world, dev)
+        nbytes = sum(inputs.host[i].numel() * 16 for i in timed)
+        line["e2e"] = {"value": whole_job_rate(world, e2e_conv, e2e_s * 1e3), "unit": "solves/s",
+                       "h2d_bytes_per_step": nbytes // args.steps, "d2h_bytes_per_step": nbytes // args.steps}
+
+        # ---- plain FP64, one system at a time, on the sample (the served speed-up's denominator),
+        # and the mixed mode alone on the same requests (profiled: no overlapping kernels)
+        f_ms, f_res, _ = one_at_a_time(inputs, sample, 0)
+        m_ms, m_res, m_prof = one_at_a_time(inputs, sample, prec, profile=True)
+        fp64_rate = len(sample) / (sum(f_ms) / 1e3)
+        line["fp64_one_at_a_time"] = {
+            "solves_per_s": r4(fp64_rate), "sample": f"stream requests i % {FP64_SAMPLE_STRIDE} == 0 "
+            f"({len(sample)})", "converged": sum(1 for r in f_res if r.status == 0),
+            "mixed_alone_solves_per_s": r4(len(sample) / (sum(m_ms) / 1e3))}
+        line["served_over_fp64"] = r4(value / world / fp64_rate)
+        line["roofline"] = roofline_of(m_prof)
+        if line["roofline"]:
+            line["roofline"]["timed"] = "sample requests solved one at a time in mixed precision"
+        log["mixed_alone_profile"] = profile_summary(m_prof, sum(m_ms))
+
+        # ---- Poisson streams at 0.5x and 2x the FP64 one-at-a-time rate (arrival -> converged)
+        rng = np.random.default_rng(7)
+        for tag, mult, count in (("poisson_2x_fp64", 2.0, 32), ("poisson_0.5x_fp64", 0.5, 12)):
+            rate = mult * fp64_rate
+            gaps = rng.exponential(1.0 / rate, size=count)
+            arrivals = list(np.concatenate([[0.0], np.cumsum(gaps[:-1])]))
+            ids = stream_ids(0, count)
+            _, _, p_outs, _ = serve_run(inputs, ids, prec, args.resident, arrivals=arrivals)
+            pst = latency_stats(p_outs)
+            line["latency_s"][tag] = {"rate_per_s": r4(rate), "requests": count, "p50": r4(pst["p50_s"]),
+                                      "p99": r4(pst["p99_s"]), "converged": pst["converged"]}
+
+        # ---- CPU baseline: the oracle as it stands, full solves of sampled requests (rank 0)
+        if rank == 0 and world == 1:
+            ids = oracle_cpu_sample()
+            try:
+                times = oracle_serving_solves(ids)
+                line["cpu_baseline"] = {
+                    "value": r4(len(ids) / sum(times)), "unit": "solves/s", "cores": os.cpu_count(),
+                    "kind": "oracle", "sample": f"full FP64 oracle solves of stream requests {ids} "
+                    f"({sum(times):.1f} s of host time)"}
+            except Exception as exc:  # the baseline is a report, not the measurement
+                line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": os.cpu_count(),
+                                        "kind": "oracle", "sample": f"failed: {exc}"}
+    if rank == 0:
+        sys.stderr.write(json.dumps(log) + "\n")
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------ GPU arm: one workload
+def run_solve(args):
     import torch
     import torch.distributed as dist
     import synth
@@ -281,7 +625,6 @@ def run_gpu(args):
     method = 1 if args.method == "eargd" else 0
     params = E.eacg_default_params(precision=prec, method=method)
     C = max(1, args.concurrent)
-    # C resident systems of the workload, each with its own stream and host thread (served)
     systems = []
     for _ in range(C):
         st_i = torch.cuda.Stream(device=dev)
@@ -305,8 +648,6 @@ def run_gpu(args):
         ends[i].record(st_i)
 
     def one_round():
-        """C concurrent solves from the same start; device time from one event that every
-        system stream waits on to an event that waits on every stream's end."""
         start = torch.cuda.Event(enable_timing=True)
         start.record(stream)
         for _, st_i in systems:
@@ -334,7 +675,6 @@ def run_gpu(args):
         one_round()
     torch.cuda.synchronize()
 
-    # ---- timed region: K rounds of C concurrent solves, L2 flushed between them (outside the events)
     clocks = Clocks(local)
     for sy, _ in systems:
         E.eacg_profile_enable(sy.h, 1)
@@ -342,9 +682,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    per = []
-    latencies = []
-    results = []
+    per, latencies, results = [], [], []
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -358,16 +696,15 @@ def run_gpu(args):
     launches = E.eacg_launch_count() - launches0
     clk = clocks.stop()
     prof = {}
-    for sy, _ in systems:  # summed over the resident systems
+    for sy, _ in systems:
         for name, st in E.eacg_profile_read(sy.h).items():
-            acc = prof.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0, "units": 0.0})
+            acc = prof.setdefault(name, dict.fromkeys(st, 0))
             for key in acc:
                 acc[key] += st[key]
         E.eacg_profile_enable(sy.h, 0)
     total_ms = max_over_ranks(sum(per), world, dev)
     value = whole_job_rate(world, C * args.steps, total_ms)
 
-    # ---- end to end through the host-buffer entry point (copies inside the timed region)
     e2e_ms = []
 
     def solve_host_on(i, res):
@@ -394,12 +731,10 @@ def run_gpu(args):
     e2e_value = (whole_job_rate(world, C, max_over_ranks(statistics.mean(e2e_ms), world, dev))
                  if e2e_ms else None)
 
-    # ---- plain FP64, one system at a time (the comparison the served number is quoted against)
     fp64_ref = None
-    if prec == 1 and not args.no_extras and not args.no_fp64_ref:
-        p64 = E.eacg_default_params(precision=0, method=method)
-        s64 = E.System(cfg, p64)
-        for it in range(2):  # one untimed solve, then one timed
+    if prec == 1 and not args.no_extras:
+        s64 = E.System(cfg, E.eacg_default_params(precision=0, method=method))
+        for _ in range(2):  # one untimed solve, then one timed
             E.eacg_set_psi(s64.h, psi0)
             torch.cuda.synchronize()
             flush.fill_(1.0)
@@ -410,40 +745,13 @@ def run_gpu(args):
             a1.synchronize()
         s64.close()
         fp64_ms = a0.elapsed_time(a1)
-        fp64_ref = {"solves_per_s": 1e3 / fp64_ms, "ms_per_solve": fp64_ms, "E": r64.E, "rnorm": r64.rnorm,
-                    "iterations": r64.iterations, "served_over_fp64": value / (1e3 / fp64_ms)}
+        fp64_ref = {"solves_per_s": r4(1e3 / fp64_ms), "iterations": r64.iterations}
 
-    # ---- roofline of the dominant kernel from the live profile
-    hbm, peak_kind = measured_peaks()
-    bytes_per_band = hpsi_bytes_per_band(sysm, prec_bytes=8)
-    roof = None
-    kernels = {}
-    for name, st in (prof or {}).items():
-        if st["ms"] <= 0:
-            continue
-        sec = st["ms"] / 1e3
-        kernels[name] = {"launches": st["launches"], "ms": round(st["ms"], 3),
-                         "avg_ms": st["ms"] / st["launches"], "GBps": st["bytes"] / sec / 1e9,
-                         "TFLOPs": st["flops"] / sec / 1e12}
-    single = {k: v for k, v in (prof or {}).items() if k.rsplit("_", 1)[0] in SINGLE_KERNEL_SLOTS}
-    top = max(single, key=lambda k: single[k]["ms"]) if single else None
-    if top is not None:
-        st = prof[top]
-        n = max(1, st["launches"])
-        avg_ms = st["ms"] / n
-        achieved = (st["flops"] / n) / (avg_ms / 1e3) / 1e12
-        if top.endswith("_f64"):
-            peak, pk = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz"
-        else:
-            peak, pk = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
-        roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "peak_kind": pk,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC_BYTES.get(top) if args.workload == "diamond_k444" else None,
-                "traffic_unit": "bytes per launch (ncu)", "avg_launch_ms": avg_ms,
-                "launches": n, "hbm_GBps_algorithmic": (st["bytes"] / n) / (avg_ms / 1e3) / 1e9,
-                "hbm_peak_GBps": hbm, "hbm_peak_kind": peak_kind}
+    roof = roofline_of(prof, NCU_TRAFFIC_BYTES if args.workload == "diamond_k444" else None)
+    if roof:
+        roof["timed"] = f"{C} concurrent systems (kernels of other systems may overlap)"
     apps = sum(r.h_band_apps for r in results)
-    hpsi_gbs = (apps * bytes_per_band) / (total_ms / 1e3) / 1e9
+    hpsi_gbs = sum(v["bytes"] for k, v in prof.items() if k.rsplit("_", 1)[0] in HPSI_SLOTS) / (total_ms / 1e3) / 1e9
 
     line = {
         "metric": metric_name(args, cfg),
@@ -451,30 +759,32 @@ def run_gpu(args):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if prec else "f64", "data": "synthetic",
         "config": config_of(args, cfg, world),
-        "time_to_1e8_ms": {"p50": statistics.median(latencies), "p99": max(latencies), "all": latencies},
-        "vs_fp64_one_at_a_time": fp64_ref,
+        "time_to_1e8_ms": {"p50": r4(statistics.median(latencies)), "p99": r4(max(latencies))},
+        "fp64_one_at_a_time": fp64_ref,
+        "served_over_fp64": r4(value / world / fp64_ref["solves_per_s"]) if fp64_ref else None,
         "solve": {"E": results[-1].E, "rnorm": results[-1].rnorm, "iterations": results[-1].iterations,
-                  "warm_iterations": results[-1].warm_iterations, "h_band_apps": results[-1].h_band_apps,
-                  "ls_trials": results[-1].ls_trials},
-        "hpsi_gbs": hpsi_gbs,
-        "roofline": roof,
-        "profile": kernels,
-        "gpu_launches": launches,
-        "clocks": clk,
+                  "h_band_apps": results[-1].h_band_apps, "band_apps_total": apps},
+        "hpsi_gbs": r4(hpsi_gbs), "roofline": roof, "gpu_launches": launches, "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": C * host.numel() * 16,
                 "d2h_bytes_per_step": C * host.numel() * 16},
     }
     if rank == 0 and world == 1 and not args.no_extras:
         try:
-            per_band, cores, sample = oracle_sample(cfg)
-            apps_solve = results[-1].h_band_apps
-            cpu_v = 1.0 / (per_band * apps_solve)
-            line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                                    "sample": f"{sample}, scaled by this solve's {apps_solve} band applications"}
-        except Exception as exc:  # the baseline is a report, not the measurement
+            if args.workload == "two_atom":
+                t = oracle_solve_seconds(cfg)
+                line["cpu_baseline"] = {"value": r4(1.0 / t), "unit": "solves/s", "cores": os.cpu_count(),
+                                        "kind": "oracle", "sample": "one full oracle solve of the workload"}
+            else:
+                per_band, cores, sample = oracle_sample(cfg)
+                apps_solve = results[-1].h_band_apps
+                line["cpu_baseline"] = {"value": r4(1.0 / (per_band * apps_solve)), "unit": "solves/s",
+                                        "cores": cores, "kind": "oracle (extrapolated from a timed sample)",
+                                        "sample": f"{sample}, scaled by this solve's {apps_solve} band applications"}
+        except Exception as exc:
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"failed: {exc}"}
     if rank == 0:
+        sys.stderr.write(json.dumps({"profile": profile_summary(prof, total_ms)}) + "\n")
         print(json.dumps(line))
     for sy, _ in systems:
         sy.close()
@@ -482,10 +792,11 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def hpsi_bytes_per_band(sysm, prec_bytes=8):
+def hpsi_bytes_per_band(sysm, prec_bytes):
     """Algorithmic HBM bytes of one band application of H with the pruned transforms:
     coefficients in + out (complex double) and the x-pass intermediate written, read and
-    written back by the plane kernel, then read (4 passes of N * ncols complex values)."""
+    written back by the plane kernel, then read (4 passes of N * ncols complex values of
+    2 * prec_bytes bytes: 8 for FP32 transforms, 16 for FP64)."""
     return 2 * sysm.n_max * 16 + 4 * sysm.N * sysm.ncols * 2 * prec_bytes
 
 
@@ -532,9 +843,8 @@ def run_op(args):
     line = {"op": args.op, "workload": cfg["name"], "precision": args.precision, "calls": args.steps,
             "ms_per_call": ms, "bands": sysm.K * sysm.p}
     if args.op == "apply_h":
-        # band applications per second and algorithmic H-psi bytes (pruned transforms) per second
         line["band_apps_per_s"] = sysm.K * sysm.p / (ms / 1e3)
-        line["hpsi_gbs"] = sysm.K * sysm.p * hpsi_bytes_per_band(sysm, 8 if prec else 16) / (ms / 1e3) / 1e9
+        line["hpsi_gbs"] = sysm.K * sysm.p * hpsi_bytes_per_band(sysm, 4 if prec else 8) / (ms / 1e3) / 1e9
     print(json.dumps(line))
     sysm.close()
 
@@ -543,12 +853,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.serve > 0:
-        run_serve(args)
     elif args.op != "solve":
         run_op(args)
+    elif args.workload == "serving_stream":
+        run_serving(args)
     else:
-        run_gpu(args)
+        run_solve(args)
 
 
 if __name__ == "__main__":

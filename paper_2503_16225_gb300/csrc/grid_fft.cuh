@@ -22,27 +22,35 @@ namespace eacg {
 
 constexpr int XPASS_THREADS = 256;  // x-pass CTA: 256 / N2 columns of one band
 
+// The segment (system) that grid row y of a multi-system launch belongs to.
+__device__ __forceinline__ int seg_of(const GridSegs& t, int y) {
+  int i = 0;
+  while (i + 1 < t.n && y >= t.s[i + 1].y0) ++i;
+  return i;
+}
+
 // Inverse x pass: sphere coefficients gathered straight into the step-1 registers; the
 // transformed columns are written to tbuf[band][jx][col] (coalesced over columns).
 template <typename T, int N, int PV, typename TIO>
-__global__ void __launch_bounds__(XPASS_THREADS)
-    k_xpass_inv(const TIO* __restrict__ psi, int n_max, int p, const int* __restrict__ xmap, int ncols,
-                cplx<T>* __restrict__ tbuf, const cplx<T>* __restrict__ tw_g, const int* __restrict__ kactive) {
+__global__ void __launch_bounds__(XPASS_THREADS) k_xpass_inv(const __grid_constant__ GridSegs tab) {
   using V = cplx<T>;
   constexpr int N2 = LinePlan<N, PV>::N2;
   __shared__ V tw[N];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
-  const int band = blockIdx.y, k = band / p;
-  if (kactive && !kactive[k]) return;
+  const GridSeg& S = tab.s[seg_of(tab, blockIdx.y)];
+  const int band = blockIdx.y - S.y0, k = band / S.p;
+  const int ncols = S.ncols;
   const int cpc = blockDim.x / N2;
   const int c0 = blockIdx.x * cpc;
+  if (c0 >= ncols || (S.kactive && !S.kactive[k])) return;
   const int nc = min(cpc, ncols - c0);
+  const V* tw_g = static_cast<const V*>(S.tw);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
   __syncthreads();
-  const int* xm = xmap + (size_t)k * N * ncols + c0;
-  const TIO* src = psi + (size_t)band * n_max;
-  V* dst = tbuf + (size_t)band * N * ncols + c0;
+  const int* xm = S.xmap + (size_t)k * N * ncols + c0;
+  const TIO* src = static_cast<const TIO*>(S.in) + (size_t)band * S.n_max;
+  V* dst = static_cast<V*>(S.tbuf) + (size_t)band * N * ncols + c0;
   fft_phase<N, PV, true, false>(
       nc, tw, PitchedScratch<V>{A, N + 1},
       [&](int l, int fx) {
@@ -52,31 +60,31 @@ __global__ void __launch_bounds__(XPASS_THREADS)
       [&](int l, int jx, V x, int) { dst[(size_t)jx * ncols + l] = x; });
 }
 
-// Forward x pass and gather: out = scale * FFT + kin * psi_in (kin may be null); the padding
+// Forward x pass and gather: out = scale * FFT + kin * in (kin may be null); the padding
 // beyond n_k is zeroed.
 template <typename T, int N, int PV, typename TIO>
-__global__ void __launch_bounds__(XPASS_THREADS)
-    k_xpass_fwd(const cplx<T>* __restrict__ tbuf, const int* __restrict__ xmap, int ncols,
-                const cplx<T>* __restrict__ tw_g, int n_max, int p, const int* __restrict__ nk,
-                const TIO* __restrict__ psi_in, const double* __restrict__ kin, double scale, TIO* __restrict__ out,
-                const int* __restrict__ kactive) {
+__global__ void __launch_bounds__(XPASS_THREADS) k_xpass_fwd(const __grid_constant__ GridSegs tab) {
   using V = cplx<T>;
   constexpr int N2 = LinePlan<N, PV>::N2;
   __shared__ V tw[N];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
-  const int band = blockIdx.y, k = band / p;
-  if (kactive && !kactive[k]) return;
+  const GridSeg& S = tab.s[seg_of(tab, blockIdx.y)];
+  const int band = blockIdx.y - S.y0, k = band / S.p;
+  const int ncols = S.ncols, n_max = S.n_max;
   const int cpc = blockDim.x / N2;
   const int c0 = blockIdx.x * cpc;
+  if (c0 >= ncols || (S.kactive && !S.kactive[k])) return;
   const int nc = min(cpc, ncols - c0);
+  const V* tw_g = static_cast<const V*>(S.tw);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
   __syncthreads();
-  const int* xm = xmap + (size_t)k * N * ncols + c0;
-  const V* src = tbuf + (size_t)band * N * ncols + c0;
-  TIO* o = out + (size_t)band * n_max;
-  const TIO* pin = psi_in + (size_t)band * n_max;
-  const double* kk = kin ? kin + (size_t)k * n_max : nullptr;
+  const int* xm = S.xmap + (size_t)k * N * ncols + c0;
+  const V* src = static_cast<const V*>(S.tbuf) + (size_t)band * N * ncols + c0;
+  TIO* o = static_cast<TIO*>(S.out) + (size_t)band * n_max;
+  const TIO* pin = static_cast<const TIO*>(S.in) + (size_t)band * n_max;
+  const double* kk = S.kin ? S.kin + (size_t)k * n_max : nullptr;
+  const double scale = S.scale;
   fft_phase<N, PV, false, false>(
       nc, tw, PitchedScratch<V>{A, N + 1}, [&](int l, int jx) { return src[(size_t)jx * ncols + l]; },
       [&](int l, int fx, V x, int) {
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(XPASS_THREADS)
         }
       });
   if (blockIdx.x == 0) {
-    for (int i = nk[k] + threadIdx.x; i < n_max; i += blockDim.x) o[i] = cvt<TIO>(make_double2(0.0, 0.0));
+    for (int i = S.nk[k] + threadIdx.x; i < n_max; i += blockDim.x) o[i] = cvt<TIO>(make_double2(0.0, 0.0));
   }
 }
 
@@ -143,10 +151,7 @@ struct YScratch {
 // Apply the local potential to one x-plane of one band.  Only rows that hold columns are
 // read before the y pass, so nothing is zeroed.
 template <typename T, int N, int PV>
-__global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
-    k_plane_h(cplx<T>* __restrict__ tbuf, int ncols, const int* __restrict__ cmapy, const int* __restrict__ ylist,
-              const int* __restrict__ rowmask, int ny, const T* __restrict__ v, const cplx<T>* __restrict__ tw_g, int p,
-              const int* __restrict__ kactive) {
+__global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_h(const __grid_constant__ GridSegs tab) {
   using V = cplx<T>;
   constexpr int PP = N + 1;
   constexpr bool PING = PlaneCfg<T, N>::pingpong;
@@ -156,11 +161,13 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
   V* B = reinterpret_cast<V*>(smem_raw);
   V* A = PING ? B + (size_t)N * PP : B;
   int* cm = reinterpret_cast<int*>(B + (size_t)(PING ? 2 : 1) * N * PP);
-  const int jx = blockIdx.x, band = blockIdx.y;
-  if (kactive && !kactive[band / p]) return;
-  plane_setup<V, N>(tw, rows, yl, cm, tw_g, rowmask, ylist, cmapy, ny);
-  V* tb = tbuf + ((size_t)band * N + jx) * ncols;
-  const T* vv = v + (size_t)jx * N * N;
+  const GridSeg& S = tab.s[seg_of(tab, blockIdx.y)];
+  const int jx = blockIdx.x, band = blockIdx.y - S.y0;
+  if (S.kactive && !S.kactive[band / S.p]) return;
+  const int ny = S.ny;
+  plane_setup<V, N>(tw, rows, yl, cm, static_cast<const V*>(S.tw), S.rowmask, S.ylist, S.cmapy, ny);
+  V* tb = static_cast<V*>(S.tbuf) + ((size_t)band * N + jx) * S.ncols;
+  const T* vv = static_cast<const T*>(S.v) + (size_t)jx * N * N;
   const ZScratch<V, N, PING> zs{A, B, yl};
   const YScratch<V, N, PING> ys{A, B};
   // z inverse over the rows with columns, straight from the column buffer
@@ -192,13 +199,9 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
 
 // Density of a group of bands on one x-plane: sum_b w_b |u_b|^2 in FP64 registers (each
 // grid point owned by one thread of the y pass, bands in a fixed order), written as
-// partial[g][jx][jy][jz].
+// partial[g][jx][jy][jz].  Grid rows are the band groups of the segments.
 template <typename T, int N, int PV>
-__global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
-    k_plane_rho(const cplx<T>* __restrict__ tbuf, int ncols, const int* __restrict__ cmapy,
-                const int* __restrict__ ylist, const int* __restrict__ rowmask, int ny,
-                const cplx<T>* __restrict__ tw_g, int nbands, int bands_per_group, const double* __restrict__ bw,
-                double* __restrict__ partial) {
+__global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_rho(const __grid_constant__ GridSegs tab) {
   using V = cplx<T>;
   constexpr int PP = N + 1, N1 = LinePlan<N, PV>::N1, N2 = LinePlan<N, PV>::N2;
   constexpr bool PING = PlaneCfg<T, N>::pingpong;
@@ -208,14 +211,18 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
   V* B = reinterpret_cast<V*>(smem_raw);
   V* A = PING ? B + (size_t)N * PP : B;
   int* cm = reinterpret_cast<int*>(B + (size_t)(PING ? 2 : 1) * N * PP);
-  const int jx = blockIdx.x, g = blockIdx.y;
-  plane_setup<V, N>(tw, rows, yl, cm, tw_g, rowmask, ylist, cmapy, ny);
+  const GridSeg& S = tab.s[seg_of(tab, blockIdx.y)];
+  const int jx = blockIdx.x, g = blockIdx.y - S.y0;
+  const int ny = S.ny, ncols = S.ncols, nbands = S.nbands;
+  plane_setup<V, N>(tw, rows, yl, cm, static_cast<const V*>(S.tw), S.rowmask, S.ylist, S.cmapy, ny);
   const ZScratch<V, N, PING> zs{A, B, yl};
   const YScratch<V, N, PING> ys{A, B};
   double acc[N1];
 #pragma unroll
   for (int q = 0; q < N1; ++q) acc[q] = 0.0;
-  const int b0 = g * bands_per_group, b1 = min(nbands, b0 + bands_per_group);
+  const int bpg = (nbands + S.groups - 1) / S.groups;
+  const int b0 = g * bpg, b1 = min(nbands, b0 + bpg);
+  const V* tbuf = static_cast<const V*>(S.tbuf);
   for (int band = b0; band < b1; ++band) {
     const V* tb = tbuf + ((size_t)band * N + jx) * ncols;
     fft_phase<N, PV, true, !PING>(
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
           return c >= 0 ? tb[c] : mk<V>(0, 0);
         },
         [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
-    const double w = bw[band];
+    const double w = S.bw[band];
     fft_phase<N, PV, true, false>(
         N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
         [&](int, int, V x, int q) {
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2)
   const int L = blockDim.x / N2;
   const int jz = threadIdx.x % L, t = threadIdx.x / L;
   if (t < N2 && jz < N) {
-    double* out = partial + ((size_t)g * N + jx) * N * N;
+    double* out = S.partial + ((size_t)g * N + jx) * N * N;
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       const int jy = (t + N2 * (q / N2)) + N1 * (q % N2);
@@ -272,93 +279,131 @@ __global__ void __launch_bounds__(XPASS_THREADS)
 }
 
 // Launchers of one grid size and line-plan variant; instantiated per supported (N, variant)
-// in the grid_fft_*.cu units.
+// in the grid_fft_*.cu units.  Each launch covers the requests r[0..n) (n <= GRID_MAX_SEGS).
 template <int N, int PV>
 struct GridFft {
   static constexpr int N2 = LinePlan<N, PV>::N2;
 
+  // segment table of the requests; rows(i) = grid rows of request i; returns the total
+  static int table(GridSegs& t, const GridReq* r, int n, int mode_t32, bool groups_as_rows) {
+    int y = 0;
+    t.n = n;
+    for (int i = 0; i < n; ++i) {
+      const GridCtx& g = *r[i].g;
+      GridSeg& S = t.s[i];
+      S.in = r[i].in;
+      S.tbuf = r[i].tbuf;
+      S.out = r[i].out;
+      S.kin = r[i].kin;
+      S.v = r[i].v;
+      S.kactive = r[i].kactive;
+      S.nk = g.nk;
+      S.xmap = g.xmap;
+      S.cmapy = g.cmapy;
+      S.ylist = g.ylist;
+      S.rowmask = g.rowmask;
+      S.tw = mode_t32 ? g.tw32 : g.tw64;
+      S.bw = r[i].bw;
+      S.partial = r[i].partial;
+      S.scale = r[i].scale;
+      S.n_max = g.n_max;
+      S.p = g.p;
+      S.ncols = g.ncols;
+      S.ny = g.ny;
+      S.nbands = r[i].nbands;
+      S.groups = r[i].groups;
+      S.y0 = y;
+      y += groups_as_rows ? r[i].groups : r[i].nbands;
+    }
+    return y;
+  }
+  static int max_cols(const GridReq* r, int n) {
+    int c = 0;
+    for (int i = 0; i < n; ++i) c = c > r[i].g->ncols ? c : r[i].g->ncols;
+    return c;
+  }
+  static int max_ny(const GridReq* r, int n) {
+    int c = 0;
+    for (int i = 0; i < n; ++i) c = c > r[i].g->ny ? c : r[i].g->ny;
+    return c;
+  }
+
   template <typename T, typename TIO>
-  static void xinv(const GridCtx& g, const TIO* psi, void* tbuf, const void* tw, int nbands, const int* kactive,
-                   cudaStream_t st) {
+  static void xinv(const GridReq* r, int n, cudaStream_t st) {
+    GridSegs t;
+    const int rows = table(t, r, n, sizeof(T) == 4, false);
     const int cpc = XPASS_THREADS / N2;
-    dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
+    dim3 grid((max_cols(r, n) + cpc - 1) / cpc, rows);
     const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
     ensure_smem((const void*)k_xpass_inv<T, N, PV, TIO>, sm);
-    k_xpass_inv<T, N, PV, TIO><<<grid, cpc * N2, sm, st>>>(psi, g.n_max, g.p, g.xmap, g.ncols, (cplx<T>*)tbuf,
-                                                        (const cplx<T>*)tw, kactive);
+    k_xpass_inv<T, N, PV, TIO><<<grid, cpc * N2, sm, st>>>(t);
     count_launch();
   }
 
   template <typename T, typename TIO>
-  static void xfwd(const GridCtx& g, const void* tbuf, const void* tw, const TIO* psi_in, const double* kin,
-                   double scale, TIO* out, int nbands, const int* kactive, cudaStream_t st) {
+  static void xfwd(const GridReq* r, int n, cudaStream_t st) {
+    GridSegs t;
+    const int rows = table(t, r, n, sizeof(T) == 4, false);
     const int cpc = XPASS_THREADS / N2;
-    dim3 grid((g.ncols + cpc - 1) / cpc, nbands);
+    dim3 grid((max_cols(r, n) + cpc - 1) / cpc, rows);
     const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
     ensure_smem((const void*)k_xpass_fwd<T, N, PV, TIO>, sm);
-    k_xpass_fwd<T, N, PV, TIO><<<grid, cpc * N2, sm, st>>>((const cplx<T>*)tbuf, g.xmap, g.ncols, (const cplx<T>*)tw,
-                                                        g.n_max, g.p, g.nk, psi_in, kin, scale, out, kactive);
+    k_xpass_fwd<T, N, PV, TIO><<<grid, cpc * N2, sm, st>>>(t);
     count_launch();
   }
 
   // mode 0: FP64 transforms of FP64 blocks; 1: FP32 transforms of FP64 blocks;
   // 2: FP32 transforms of FP32 blocks
-  static void xpass_inv(const GridCtx& g, int mode, const void* psi, void* tbuf, int nbands, const int* kactive,
-                        cudaStream_t st) {
+  static void xpass_inv(int mode, const GridReq* r, int n, cudaStream_t st) {
     if (mode == 0)
-      xinv<double>(g, (const double2*)psi, tbuf, g.tw64, nbands, kactive, st);
+      xinv<double, double2>(r, n, st);
     else if (mode == 1)
-      xinv<float>(g, (const double2*)psi, tbuf, g.tw32, nbands, kactive, st);
+      xinv<float, double2>(r, n, st);
     else
-      xinv<float>(g, (const float2*)psi, tbuf, g.tw32, nbands, kactive, st);
+      xinv<float, float2>(r, n, st);
   }
 
-  static void xpass_fwd(const GridCtx& g, int mode, const void* tbuf, const void* psi_in, const double* kin,
-                        double scale, void* out, int nbands, const int* kactive, cudaStream_t st) {
+  static void xpass_fwd(int mode, const GridReq* r, int n, cudaStream_t st) {
     if (mode == 0)
-      xfwd<double>(g, tbuf, g.tw64, (const double2*)psi_in, kin, scale, (double2*)out, nbands, kactive, st);
+      xfwd<double, double2>(r, n, st);
     else if (mode == 1)
-      xfwd<float>(g, tbuf, g.tw32, (const double2*)psi_in, kin, scale, (double2*)out, nbands, kactive, st);
+      xfwd<float, double2>(r, n, st);
     else
-      xfwd<float>(g, tbuf, g.tw32, (const float2*)psi_in, kin, scale, (float2*)out, nbands, kactive, st);
+      xfwd<float, float2>(r, n, st);
   }
 
   template <typename T>
-  static void plane_h_t(const GridCtx& g, void* tbuf, const void* tw, const void* v, int nbands, const int* kactive,
-                        cudaStream_t st) {
-    const size_t sm = PlaneCfg<T, N>::smem_bytes(g.ny);
+  static void plane_h_t(const GridReq* r, int n, cudaStream_t st) {
+    GridSegs t;
+    const int rows = table(t, r, n, sizeof(T) == 4, false);
+    const size_t sm = PlaneCfg<T, N>::smem_bytes(max_ny(r, n));
     ensure_smem((const void*)k_plane_h<T, N, PV>, sm);
-    k_plane_h<T, N, PV><<<dim3(N, nbands), N * N2, sm, st>>>((cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist, g.rowmask, g.ny,
-                                                         (const T*)v, (const cplx<T>*)tw, g.p, kactive);
+    k_plane_h<T, N, PV><<<dim3(N, rows), N * N2, sm, st>>>(t);
     count_launch();
   }
 
-  static void plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
-                      cudaStream_t st) {
+  static void plane_h(int prec, const GridReq* r, int n, cudaStream_t st) {
     if (prec == 0)
-      plane_h_t<double>(g, tbuf, g.tw64, v, nbands, kactive, st);
+      plane_h_t<double>(r, n, st);
     else
-      plane_h_t<float>(g, tbuf, g.tw32, v, nbands, kactive, st);
+      plane_h_t<float>(r, n, st);
   }
 
   template <typename T>
-  static void plane_rho_t(const GridCtx& g, const void* tbuf, const void* tw, int nbands, int groups,
-                          const double* bw, double* partial, cudaStream_t st) {
-    const size_t sm = PlaneCfg<T, N>::smem_bytes(g.ny);
+  static void plane_rho_t(const GridReq* r, int n, cudaStream_t st) {
+    GridSegs t;
+    const int rows = table(t, r, n, sizeof(T) == 4, true);
+    const size_t sm = PlaneCfg<T, N>::smem_bytes(max_ny(r, n));
     ensure_smem((const void*)k_plane_rho<T, N, PV>, sm);
-    const int bpg = (nbands + groups - 1) / groups;
-    k_plane_rho<T, N, PV><<<dim3(N, groups), N * N2, sm, st>>>((const cplx<T>*)tbuf, g.ncols, g.cmapy, g.ylist,
-                                                           g.rowmask, g.ny, (const cplx<T>*)tw, nbands, bpg, bw,
-                                                           partial);
+    k_plane_rho<T, N, PV><<<dim3(N, rows), N * N2, sm, st>>>(t);
     count_launch();
   }
 
-  static void plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
-                        double* partial, cudaStream_t st) {
+  static void plane_rho(int prec, const GridReq* r, int n, cudaStream_t st) {
     if (prec == 0)
-      plane_rho_t<double>(g, tbuf, g.tw64, nbands, groups, bw, partial, st);
+      plane_rho_t<double>(r, n, st);
     else
-      plane_rho_t<float>(g, tbuf, g.tw32, nbands, groups, bw, partial, st);
+      plane_rho_t<float>(r, n, st);
   }
 
   template <bool INV>

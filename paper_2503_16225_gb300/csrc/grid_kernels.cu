@@ -344,42 +344,98 @@ static void dispatch_n(int N, int plan, const F& f) {
 // line-plan variant of the transforms in this precision (0: FP64, else FP32)
 static int plan_of(const GridCtx& g, int prec) { return prec == 0 ? g.plan64 : g.plan32; }
 
+// Launches f over chunks of at most GRID_MAX_SEGS requests.
+template <typename F>
+static void in_chunks(const GridReq* r, int n, const F& f) {
+  for (int i = 0; i < n; i += GRID_MAX_SEGS) f(r + i, n - i < GRID_MAX_SEGS ? n - i : GRID_MAX_SEGS);
+}
+
+void grid_xpass_inv_multi(int N, int plan, int mode, const GridReq* r, int n, cudaStream_t st) {
+  dispatch_n(N, plan, [&](auto G) {
+    in_chunks(r, n, [&](const GridReq* c, int m) { decltype(G)::xpass_inv(mode, c, m, st); });
+  });
+}
+void grid_xpass_fwd_multi(int N, int plan, int mode, const GridReq* r, int n, cudaStream_t st) {
+  dispatch_n(N, plan, [&](auto G) {
+    in_chunks(r, n, [&](const GridReq* c, int m) { decltype(G)::xpass_fwd(mode, c, m, st); });
+  });
+}
+void grid_plane_h_multi(int N, int plan, int prec, const GridReq* r, int n, cudaStream_t st) {
+  dispatch_n(N, plan, [&](auto G) {
+    in_chunks(r, n, [&](const GridReq* c, int m) { decltype(G)::plane_h(prec, c, m, st); });
+  });
+}
+void grid_plane_rho_multi(int N, int plan, int prec, const GridReq* r, int n, cudaStream_t st) {
+  dispatch_n(N, plan, [&](auto G) {
+    in_chunks(r, n, [&](const GridReq* c, int m) { decltype(G)::plane_rho(prec, c, m, st); });
+  });
+}
+
+// Single-system launches: a one-segment table.
+static GridReq req_of(const GridCtx& g, int nbands, const int* kactive) {
+  GridReq r{};
+  r.g = &g;
+  r.nbands = nbands;
+  r.kactive = kactive;
+  r.scale = 1.0;
+  r.groups = 1;
+  return r;
+}
+
 void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, int nbands, const int* kactive,
                     cudaStream_t st) {
-  dispatch_n(g.N, plan_of(g, prec), [&](auto G) {
-    decltype(G)::xpass_inv(g, prec == 0 ? 0 : 1, psi, tbuf, nbands, kactive, st);
-  });
+  GridReq r = req_of(g, nbands, kactive);
+  r.in = psi;
+  r.tbuf = tbuf;
+  grid_xpass_inv_multi(g.N, plan_of(g, prec), prec == 0 ? 0 : 1, &r, 1, st);
 }
 
 void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
                     double scale, double2* out, int nbands, const int* kactive, cudaStream_t st) {
-  dispatch_n(g.N, plan_of(g, prec), [&](auto G) {
-    decltype(G)::xpass_fwd(g, prec == 0 ? 0 : 1, tbuf, psi_in, kin, scale, out, nbands, kactive, st);
-  });
+  GridReq r = req_of(g, nbands, kactive);
+  r.in = psi_in;
+  r.tbuf = const_cast<void*>(tbuf);
+  r.out = out;
+  r.kin = kin;
+  r.scale = scale;
+  grid_xpass_fwd_multi(g.N, plan_of(g, prec), prec == 0 ? 0 : 1, &r, 1, st);
 }
 
 void grid_xpass_inv32(const GridCtx& g, const float2* psi, void* tbuf, int nbands, const int* kactive,
                       cudaStream_t st) {
-  dispatch_n(g.N, g.plan32, [&](auto G) { decltype(G)::xpass_inv(g, 2, psi, tbuf, nbands, kactive, st); });
+  GridReq r = req_of(g, nbands, kactive);
+  r.in = psi;
+  r.tbuf = tbuf;
+  grid_xpass_inv_multi(g.N, g.plan32, 2, &r, 1, st);
 }
 
 void grid_xpass_fwd32(const GridCtx& g, const void* tbuf, const float2* psi_in, const double* kin, double scale,
                       float2* out, int nbands, const int* kactive, cudaStream_t st) {
-  dispatch_n(g.N, g.plan32, [&](auto G) {
-    decltype(G)::xpass_fwd(g, 2, tbuf, psi_in, kin, scale, out, nbands, kactive, st);
-  });
+  GridReq r = req_of(g, nbands, kactive);
+  r.in = psi_in;
+  r.tbuf = const_cast<void*>(tbuf);
+  r.out = out;
+  r.kin = kin;
+  r.scale = scale;
+  grid_xpass_fwd_multi(g.N, g.plan32, 2, &r, 1, st);
 }
 
 void grid_plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nbands, const int* kactive,
                   cudaStream_t st) {
-  dispatch_n(g.N, plan_of(g, prec), [&](auto G) { decltype(G)::plane_h(g, prec, tbuf, v, nbands, kactive, st); });
+  GridReq r = req_of(g, nbands, kactive);
+  r.tbuf = tbuf;
+  r.v = v;
+  grid_plane_h_multi(g.N, plan_of(g, prec), prec, &r, 1, st);
 }
 
 void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
                     double* partial, cudaStream_t st) {
-  dispatch_n(g.N, plan_of(g, prec), [&](auto G) {
-    decltype(G)::plane_rho(g, prec, tbuf, nbands, groups, bw, partial, st);
-  });
+  GridReq r = req_of(g, nbands, nullptr);
+  r.tbuf = const_cast<void*>(tbuf);
+  r.bw = bw;
+  r.partial = partial;
+  r.groups = groups;
+  grid_plane_rho_multi(g.N, plan_of(g, prec), prec, &r, 1, st);
 }
 
 void grid_fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {

@@ -30,7 +30,60 @@ struct GridCtx {
   const void* tw32;    // float2[N]
 };
 
+// One system's share of a transform launch.  A launch covers the bands of up to
+// GRID_MAX_SEGS systems of the same grid size, line plan and precision: grid row y of the
+// launch belongs to the segment with the largest y0 <= y (bands for the x passes and the
+// potential multiply, band groups for the density).  The table travels as a kernel parameter.
+struct GridSeg {
+  const void* in;        // coefficient blocks [bands][n_max] (block precision)
+  void* tbuf;            // x-pass intermediate [bands][N][ncols] (transform precision)
+  void* out;             // forward x pass: result blocks [bands][n_max]
+  const double* kin;     // forward x pass: kinetic factors [K][n_max] (may be null)
+  const void* v;         // plane kernel: potential [N^3] (transform precision)
+  const int* kactive;    // [K] or null
+  const int* nk;         // [K]
+  const int* xmap;       // [K][N][ncols]
+  const int* cmapy;      // [ny][N + 1]
+  const int* ylist;      // [ny]
+  const int* rowmask;    // [N]
+  const void* tw;        // twiddles [N] (transform precision)
+  const double* bw;      // density: weight of every band
+  double* partial;       // density: [groups][N^3]
+  double scale;          // forward x pass: factor of the transform
+  int n_max, p, ncols, ny, nbands, groups;
+  int y0;                // first grid row of the segment
+};
+constexpr int GRID_MAX_SEGS = 16;
+struct GridSegs {
+  int n;
+  GridSeg s[GRID_MAX_SEGS];
+};
+
+// A transform request of one system, the unit a multi-system launch is built from.
+struct GridReq {
+  const GridCtx* g;
+  const void* in;
+  void* tbuf;
+  void* out;
+  const double* kin;
+  double scale;
+  const void* v;
+  const int* kactive;
+  int nbands;
+  const double* bw;
+  double* partial;
+  int groups;
+};
+
 // ---- grid_kernels.cu
+// Multi-system transform launches (one kernel launch per call for up to GRID_MAX_SEGS requests
+// of the same N, line plan and mode; longer lists are split).  mode 0: FP64 transforms of FP64
+// blocks; 1: FP32 transforms of FP64 blocks; 2: FP32 transforms of FP32 blocks.  plane_h and
+// plane_rho take prec (0 FP64, 1 FP32).
+void grid_xpass_inv_multi(int N, int plan, int mode, const GridReq* r, int n, cudaStream_t st);
+void grid_xpass_fwd_multi(int N, int plan, int mode, const GridReq* r, int n, cudaStream_t st);
+void grid_plane_h_multi(int N, int plan, int prec, const GridReq* r, int n, cudaStream_t st);
+void grid_plane_rho_multi(int N, int plan, int prec, const GridReq* r, int n, cudaStream_t st);
 void grid_build_sphere(int N, int K, const double* kfrac_d, double thr, double b, int n_max_cap, int* nk, int* row_off,
                        int* m, double* kin, int* colmark, cudaStream_t st);
 // True if N has a compile-time line plan (the grid sizes this library transforms), and if it

@@ -17,16 +17,19 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import System, eacg_bytes_required, eacg_default_params, eacg_get_psi, eacg_set_psi, eacg_step
+from . import (System, eacg_bytes_required, eacg_default_params, eacg_get_psi, eacg_profile_enable,
+               eacg_profile_read, eacg_set_psi, eacg_solve_host, eacg_step)
 
 
 @dataclass
 class Request:
     rid: int
     cfg: dict
-    raw: object            # host complex128 tensor [K, p, n_max] or a callable(n_k list, n_max) -> tensor
+    raw: object            # complex128 tensor [K, p, n_max] (device, or pinned host for host-buffer
+                           # serving) or a callable(n_k list, n_max) -> tensor
     arrival: float         # seconds after the start of the run
     max_outer: int = 300
+    out: object = None     # host-buffer serving: pinned host tensor that receives the result
 
 
 @dataclass
@@ -43,19 +46,30 @@ class Outcome:
     bytes: int = 0
     psi: object = None
     steps: list = field(default_factory=list)
+    h_band_apps: int = 0
+    end_event: object = None   # CUDA event recorded on the request's stream after its last call
 
 
 class Server:
     """Admits requests by HBM budget and slot count; one worker thread per resident system."""
 
     def __init__(self, hbm_budget: int, max_resident: int = 8, precision: int = 1, keep_psi: bool = False,
-                 device: int = 0, use_cuda: bool = True):
+                 device: int = 0, use_cuda: bool = True, start_event=None, profile: bool = False,
+                 host_buffers: bool = False):
+        """start_event: a CUDA event every request stream waits on before its first call (device
+        timing from one event); profile: live kernel timing of every system, summed into
+        self.profile; host_buffers: requests carry pinned host input and output tensors and are
+        solved through eacg_solve_host (copies inside the request)."""
         self.use_cuda = use_cuda
         self.budget = int(hbm_budget)
         self.max_resident = int(max_resident)
         self.precision = precision
         self.keep_psi = keep_psi
         self.device = device
+        self.start_event = start_event
+        self.profile_on = profile
+        self.host_buffers = host_buffers
+        self.profile: dict = {}
         self._lock = threading.Lock()
         self._resident_bytes = 0
         self._resident = 0
@@ -78,20 +92,32 @@ class Server:
                 import contextlib
                 stream, ctx, handle = None, contextlib.nullcontext(), 0
             with ctx:
+                if self.start_event is not None and stream is not None:
+                    stream.wait_event(self.start_event)
                 prm = eacg_default_params(precision=self.precision, max_outer=req.max_outer)
                 s = System(req.cfg, prm, stream=handle)
+                if self.profile_on:
+                    eacg_profile_enable(s.h, 1)
                 raw = req.raw(s.nk, s.n_max) if callable(req.raw) else req.raw
-                psi = raw.to("cuda", non_blocking=False) if self.use_cuda else raw
-                eacg_set_psi(s.h, psi)
-                while True:
-                    info = eacg_step(s.h)
-                    out.steps.append((info.E, info.rnorm))
-                    if info.converged:
-                        out.converged = True
-                        break
-                out.E, out.rnorm = info.E, info.rnorm
-                out.iterations = len(out.steps)
-                out.status = "converged"
+                if self.host_buffers:
+                    r = eacg_solve_host(s.h, raw, req.out, check=False)
+                    out.E, out.rnorm, out.iterations = r.E, r.rnorm, r.iterations
+                    out.h_band_apps = r.h_band_apps
+                    out.converged = r.status == 0 and r.rnorm <= prm.res_tol
+                    out.status = "converged" if out.converged else f"status {r.status}"
+                else:
+                    psi = raw if (not self.use_cuda or raw.is_cuda) else raw.to("cuda", non_blocking=False)
+                    eacg_set_psi(s.h, psi)
+                    while True:
+                        info = eacg_step(s.h)
+                        out.steps.append((info.E, info.rnorm))
+                        if info.converged:
+                            out.converged = True
+                            break
+                    out.E, out.rnorm = info.E, info.rnorm
+                    out.iterations = len(out.steps)
+                    out.h_band_apps = getattr(info, "h_band_apps", 0)
+                    out.status = "converged"
                 if self.keep_psi:
                     phi = s.block()
                     eacg_get_psi(s.h, phi)
@@ -105,6 +131,19 @@ class Server:
                 out.iterations = len(out.steps)
         finally:
             if s is not None:
+                if self.profile_on:
+                    try:
+                        prof = eacg_profile_read(s.h)
+                    except Exception:
+                        prof = {}
+                    with self._lock:
+                        for name, st in prof.items():
+                            acc = self.profile.setdefault(name, dict.fromkeys(st, 0))
+                            for key, v in st.items():
+                                acc[key] += v
+                if stream is not None:
+                    out.end_event = torch.cuda.Event(enable_timing=True)
+                    out.end_event.record(stream)
                 s.close()
             out.done = time.perf_counter() - t0
             with self._lock:
@@ -164,17 +203,22 @@ class Server:
         return [outs[r.rid] for r in requests]
 
 
+def percentile(values, q):
+    """Nearest-rank percentile of a list (None when empty)."""
+    v = sorted(values)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(round(q * (len(v) - 1)))))
+    return v[k]
+
+
 def latency_stats(outs: list[Outcome]):
-    """solves/s over the whole run and p50/p99 of arrival-to-converged latency (converged only)."""
+    """solves/s over the whole run, p50/p99 of arrival-to-converged latency and of the solve
+    time from admission (converged requests only)."""
     ok = [o for o in outs if o.converged]
-    lat = sorted(o.done - o.arrival for o in ok)
+    lat = [o.done - o.arrival for o in ok]
+    svc = [o.done - o.admit for o in ok]
     span = max(o.done for o in outs) - min(o.arrival for o in outs) if outs else 0.0
-
-    def pct(q):
-        if not lat:
-            return None
-        k = min(len(lat) - 1, max(0, int(round(q * (len(lat) - 1)))))
-        return lat[k]
-
     return {"converged": len(ok), "requests": len(outs), "solves_per_s": len(ok) / span if span > 0 else None,
-            "p50_s": pct(0.5), "p99_s": pct(0.99)}
+            "p50_s": percentile(lat, 0.5), "p99_s": percentile(lat, 0.99),
+            "solve_p50_s": percentile(svc, 0.5), "solve_p99_s": percentile(svc, 0.99)}

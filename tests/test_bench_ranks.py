@@ -61,15 +61,26 @@ def test_reference_arm_prints_only_on_rank_zero(monkeypatch, capsys):
 
 
 def test_both_arms_share_metric_and_config():
+    """Both arms build the metric name and the config from the same helpers: the default is the
+    256-request serving stream, split into K steps that cover the stream once."""
     import synth
     import sys
     old = sys.argv
     try:
-        sys.argv = ["bench.py"]
+        sys.argv = ["bench.py", "--steps", "20"]
         args = bench.parse()
+        sys.argv = ["bench.py", "--workload", "diamond_k444"]
+        args_d = bench.parse()
     finally:
         sys.argv = old
+    assert args.workload == "serving_stream"
+    assert bench.metric_name(args) == "served eARCG solves/s (stream of 256 synthetic crystals, to ||R||<=1e-8)"
+    c = bench.config_of(args, None, 1)
+    assert c["workload"] == "serving_stream_256" and c["parallelism"] == "replicas1"
+    assert c["requests_per_step"] == 13 and 13 * 20 >= 256
+    assert bench.stream_ids(250, 8) == [250, 251, 252, 253, 254, 255, 0, 1]
+    assert bench.fp64_sample_ids() == list(range(0, 256, 16))
     cfg = synth.config_diamond(2, kgrid=(4, 4, 4))
-    assert bench.metric_name(args, cfg) == "served eARCG solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)"
-    c = bench.config_of(args, cfg, 1)
+    assert bench.metric_name(args_d, cfg) == "served eARCG solves/s (diamond8 4x4x4k 48^3 p16, to ||R||<=1e-8)"
+    c = bench.config_of(args_d, cfg, 1)
     assert c["workload"] == cfg["name"] and c["parallelism"] == "replicas1" and c["concurrent_systems"] == 4

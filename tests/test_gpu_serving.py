@@ -57,3 +57,33 @@ def test_budget_limits_residency():
     spans = sorted((o.admit, o.done) for o in outs)
     for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
         assert a1 >= d0 - 1e-3
+
+
+def _golden_serving():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_serving.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-6), (0, 1e-8)])
+def test_served_stream_requests_match_the_oracle(precision, tol):
+    """Requests of the 256-crystal serving stream, served together (continuous batching, own
+    streams), reach the energies of the oracle's own converged solves (written to
+    tests/golden/oracle_serving.json by tests/golden/make_golden.py): within 1e-6 Ha per atom in
+    mixed precision and 1e-8 Ha per atom in FP64."""
+    g = _golden_serving()
+    rows = sorted(g["solves"].values(), key=lambda r: r["oracle_seconds"])[:6]
+    reqs = []
+    for j, row in enumerate(rows):
+        cfg = synth.config_serving_request(row["request"])
+
+        def raw(nk, n_max, cfg=cfg):
+            return torch.from_numpy(synth.raw_coefficients(cfg["seed"], nk, cfg["nbands"], n_max))
+        reqs.append(serve.Request(rid=j, cfg=cfg, raw=raw, arrival=0.0))
+    outs = serve.Server(hbm_budget=1 << 40, max_resident=6, precision=precision).run(reqs)
+    for o, row in zip(outs, rows):
+        assert row["status"] == "converged"
+        assert o.converged and o.rnorm <= 1e-8, (row["request"], o.status)
+        assert abs(o.E - row["E"]) <= tol * row["natoms"], (row["request"], o.E, row["E"])
