@@ -148,7 +148,11 @@ void eacg_default_params(eacg_params* prm);
 size_t eacg_bytes_required(const eacg_model* model, const eacg_params* prm, size_t* fom_bytes_per_iter);
 
 /* Builds the basis (Sec. 5.1), local potential and projectors on the device.
- * stream: a cudaStream_t (NULL = legacy default stream).  *out owns all device state. */
+ * stream: a cudaStream_t (NULL = legacy default stream).  *out owns all device state.
+ * While a call on the system runs, nothing else may be enqueued on its stream: the FOM's
+ * block H application is captured from that stream into a CUDA graph, and work of another
+ * system on the same stream would be captured with it.  Concurrent systems therefore need
+ * streams of their own (eacg_stream_create gives such streams). */
 eacg_status eacg_create_system(const eacg_model* model, const eacg_params* prm, void* stream, eacg_system** out);
 /* Synchronises the system's stream and frees every device and pinned host buffer the system
  * owns; NULL is ignored.  Resource management only, the paper has no counterpart. */
@@ -240,6 +244,11 @@ eacg_status eacg_profile_enable(eacg_system* sys, int on);
 int eacg_profile_read(eacg_system* sys, eacg_kernel_stat* out, int max);
 /* Number of kernels this library has launched in the process so far. */
 long long eacg_launch_count(void);
+/* A new non-blocking CUDA stream on the current device (*stream, a cudaStream_t), for a system
+ * of its own; eacg_stream_destroy synchronises and destroys it.  Stream management for
+ * concurrent systems; the paper has no counterpart.  EACG_ECUDA if the runtime refuses. */
+eacg_status eacg_stream_create(void** stream);
+eacg_status eacg_stream_destroy(void* stream);
 
 /* Allocation-free block overlaps (the paper has no counterpart; this serves callers that
  * cannot allocate device memory, e.g. code running inside a memory pool or framework that

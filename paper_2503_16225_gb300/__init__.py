@@ -19,7 +19,7 @@ __all__ = [
     "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
-    "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_backproject_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
+    "eacg_stream_create", "eacg_stream_destroy", "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_backproject_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
 ]
 
 # band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
@@ -106,6 +106,8 @@ def _load():
         "eacg_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "eacg_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(EacgKernelStat), ctypes.c_int]),
         "eacg_launch_count": (ctypes.c_longlong, []),
+        "eacg_stream_create": (ctypes.c_int, [ctypes.POINTER(vp)]),
+        "eacg_stream_destroy": (ctypes.c_int, [vp]),
         "eacg_overlap_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "eacg_overlap_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                             ctypes.c_int, vp]),
@@ -311,6 +313,17 @@ def eacg_profile_read(sys):
 
 def eacg_launch_count():
     return int(lib.eacg_launch_count())
+
+
+def eacg_stream_create():
+    """Handle (int) of a new non-blocking CUDA stream owned by the caller."""
+    h = ctypes.c_void_p()
+    _check(None, lib.eacg_stream_create(ctypes.byref(h)))
+    return int(h.value)
+
+
+def eacg_stream_destroy(stream):
+    _check(None, lib.eacg_stream_destroy(ctypes.c_void_p(stream)))
 
 
 def eacg_overlap_noalloc(a, b, c, stream=None):

@@ -2244,3 +2244,27 @@ extern "C" int eacg_profile_read(eacg_system* s, eacg_kernel_stat* out, int max)
 }
 
 extern "C" long long eacg_launch_count(void) { return g_launches.load(); }
+
+extern "C" eacg_status eacg_stream_create(void** stream) {
+  if (!stream) return EACG_EINVAL;
+  *stream = nullptr;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return EACG_ECUDA;
+  }
+  *stream = st;
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_stream_destroy(void* stream) {
+  if (!stream) return EACG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const cudaError_t e1 = cudaStreamSynchronize(st);
+  const cudaError_t e2 = cudaStreamDestroy(st);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return EACG_ECUDA;
+  }
+  return EACG_OK;
+}

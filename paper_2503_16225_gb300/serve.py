@@ -18,7 +18,8 @@ from dataclasses import dataclass, field
 import torch
 
 from . import (System, eacg_bytes_required, eacg_default_params, eacg_get_psi, eacg_profile_enable,
-               eacg_profile_read, eacg_set_psi, eacg_solve_host, eacg_step)
+               eacg_profile_read, eacg_set_psi, eacg_solve_host, eacg_step, eacg_stream_create,
+               eacg_stream_destroy)
 
 
 @dataclass
@@ -80,17 +81,20 @@ class Server:
         base, per_iter = eacg_bytes_required(cfg, prm)
         return base + 16 * per_iter   # room for 16 FOM iterations of Krylov storage
 
-    def _work(self, req: Request, out: Outcome, t0: float):
+    def _work(self, req: Request, out: Outcome, t0: float, slot):
         s = None
+        stream = None
         try:
             if self.use_cuda:
+                # a stream of the resident slot's own: no two resident systems share a stream
+                # (the FOM captures its H application from the system's stream into a graph)
                 torch.cuda.set_device(self.device)
-                stream = torch.cuda.Stream()
+                stream = torch.cuda.ExternalStream(slot, device=torch.device("cuda", self.device))
                 ctx = torch.cuda.stream(stream)
-                handle = stream.cuda_stream
+                handle = slot
             else:
                 import contextlib
-                stream, ctx, handle = None, contextlib.nullcontext(), 0
+                ctx, handle = contextlib.nullcontext(), 0
             with ctx:
                 if self.start_event is not None and stream is not None:
                     stream.wait_event(self.start_event)
@@ -130,12 +134,10 @@ class Server:
                 out.E, out.rnorm = out.steps[-1]
                 out.iterations = len(out.steps)
         finally:
-            if s is not None:
-                if self.profile_on:
-                    try:
-                        prof = eacg_profile_read(s.h)
-                    except Exception:
-                        prof = {}
+            # the request leaves whatever happened: its slot and budget are always returned
+            try:
+                if s is not None and self.profile_on:
+                    prof = eacg_profile_read(s.h)
                     with self._lock:
                         for name, st in prof.items():
                             acc = self.profile.setdefault(name, dict.fromkeys(st, 0))
@@ -144,15 +146,36 @@ class Server:
                 if stream is not None:
                     out.end_event = torch.cuda.Event(enable_timing=True)
                     out.end_event.record(stream)
-                s.close()
+            except Exception as exc:
+                out.status = out.status or f"failed: {exc}"
+                out.end_event = None
+            finally:
+                if s is not None:
+                    s.close()
             out.done = time.perf_counter() - t0
             with self._lock:
                 self._resident_bytes -= out.bytes
                 self._resident -= 1
+            self._slots.put(slot)
             self._done.put(out)
 
     def run(self, requests: list[Request]) -> list[Outcome]:
         """Serve the requests (sorted by arrival); returns one Outcome per request."""
+        self._slots = queue.Queue()
+        streams = []
+        if self.use_cuda:
+            torch.cuda.set_device(self.device)
+            for _ in range(self.max_resident):
+                streams.append(eacg_stream_create())
+        for i in range(self.max_resident):
+            self._slots.put(streams[i] if streams else i)
+        try:
+            return self._run(requests)
+        finally:
+            for h in streams:
+                eacg_stream_destroy(h)
+
+    def _run(self, requests: list[Request]) -> list[Outcome]:
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting: list[tuple[Request, Outcome, int]] = []
         outs: dict[int, Outcome] = {}
@@ -182,7 +205,7 @@ class Server:
                 waiting.pop(0)
                 o.admit = time.perf_counter() - t0
                 o.bytes = need
-                th = threading.Thread(target=self._work, args=(r, o, t0), daemon=True)
+                th = threading.Thread(target=self._work, args=(r, o, t0, self._slots.get()), daemon=True)
                 th.start()
                 threads.append(th)
             try:
