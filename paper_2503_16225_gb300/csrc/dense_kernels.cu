@@ -66,13 +66,31 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // bitwise the same partial: the tile choice (dense_tune_cn, timed at system set-up and cached
 // for the process; untuned shapes use 4) changes only the speed.
 constexpr int CN_TILE = 16;
-constexpr int CN_CHUNK = 1024;  // rows per partial
+constexpr int CN_CHUNK = 1024;  // largest number of rows per partial
 constexpr int CN_SUB = 16;      // rows per stage
 constexpr int CN_LANES = 4;     // summation lanes (stages per round)
+// CTAs a small-problem GEMM launch aims at (two per SM): GB300 executes 2 FP64 FMA per
+// SM-clock, so an FP64 contraction confined to a few CTAs leaves almost all of its FP64
+// throughput unused.
+constexpr int GEMM_TARGET_CTAS = 2 * 152;
+
+// Rows per partial of A^H B: CN_CHUNK, or fewer (a multiple of CN_SUB * CN_LANES) when the
+// tiles of all k-points would not fill GEMM_TARGET_CTAS CTAs.  Depends on the shape only.
+static int cn_chunk(int K, int L, int m, int n) {
+  const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
+  const long long have = (long long)tiles * K;
+  const int want = (int)std::min<long long>(GEMM_TARGET_CTAS, (GEMM_TARGET_CTAS + have - 1) / have);
+  constexpr int R = CN_SUB * CN_LANES;
+  int chunk = (L + want - 1) / want;
+  chunk = ((chunk + R - 1) / R) * R;
+  return std::max(R, std::min(CN_CHUNK, chunk));
+}
 
 size_t dense_cn_work(int K, int L, int m, int n) {
+  // at most ceil(L / CN_CHUNK) partials per element for large tile counts; otherwise at most
+  // ceil(GEMM_TARGET_CTAS / (tiles K)) + 1 of them, with m n <= tiles * CN_TILE^2
   const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
-  return (size_t)K * nch * m * n;
+  return (size_t)K * (nch + 1) * m * n + (size_t)GEMM_TARGET_CTAS * CN_TILE * CN_TILE;
 }
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
@@ -86,7 +104,7 @@ template <typename T, int CN_GROUPS>
 __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
     k_gemm_cn_partial(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
                       const cplx<T>* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
-                      const int* __restrict__ kactive) {
+                      const int* __restrict__ kactive, int chunk) {
   using V = cplx<T>;
   constexpr int PER = CN_LANES / CN_GROUPS;  // lanes per group
   constexpr int NT = CN_TILE * CN_TILE * CN_GROUPS;
@@ -108,7 +126,7 @@ __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
   V acc[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) acc[i] = zero;
-  const int l_beg = ch * CN_CHUNK, l_end = min(L, l_beg + CN_CHUNK);
+  const int l_beg = ch * chunk, l_end = min(L, l_beg + chunk);
   for (int s0 = l_beg; s0 < l_end; s0 += CN_SUB * CN_LANES) {  // uniform trip count over the CTA
     for (int e = threadIdx.x; e < CN_LANES * CN_SUB * CN_TILE; e += NT) {
       const int v = e / (CN_SUB * CN_TILE), w = e - v * (CN_SUB * CN_TILE);
@@ -179,13 +197,15 @@ int cn_groups_for(size_t es, int m, int n, int L) {
 template <typename T>
 static void gemm_cn_partial_launch(int G, dim3 g1, int L, int m, int n, const cplx<T>* A, size_t sA, int lda,
                                    const cplx<T>* B, size_t sB, int ldb, double2* work, const int* kactive,
-                                   cudaStream_t st) {
+                                   int chunk, cudaStream_t st) {
   if (G == 1)
-    k_gemm_cn_partial<T, 1><<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+    k_gemm_cn_partial<T, 1><<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive, chunk);
   else if (G == 2)
-    k_gemm_cn_partial<T, 2><<<g1, CN_TILE * CN_TILE * 2, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+    k_gemm_cn_partial<T, 2><<<g1, CN_TILE * CN_TILE * 2, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive,
+                                                                  chunk);
   else
-    k_gemm_cn_partial<T, 4><<<g1, CN_TILE * CN_TILE * 4, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive);
+    k_gemm_cn_partial<T, 4><<<g1, CN_TILE * CN_TILE * 4, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive,
+                                                                  chunk);
   count_launch();
 }
 
@@ -202,12 +222,13 @@ static void gemm_cn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, i
                       int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
                       const int* kactive, cudaStream_t st, int G = 0) {
   if (K <= 0 || m <= 0 || n <= 0) return;
-  const int nch = (L + CN_CHUNK - 1) / CN_CHUNK;
+  const int chunk = cn_chunk(K, L, m, n);
+  const int nch = (L + chunk - 1) / chunk;
   const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
   dim3 g1(tiles, nch > 0 ? nch : 1, K);
   if (nch > 0)
     gemm_cn_partial_launch<T>(G > 0 ? G : cn_groups_for(sizeof(cplx<T>), m, n, L), g1, L, m, n, A, sA, lda, B, sB,
-                              ldb, work, kactive, st);
+                              ldb, work, kactive, chunk, st);
   dim3 g2((m * n + 255) / 256, K);
   k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
   count_launch();
@@ -295,7 +316,12 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
   const int k = blockIdx.y;
   if (kactive && !kactive[k]) return;
   __shared__ V sb[NN_ROWS][NN_COLS];
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  // blockIdx.x = row block + rowblocks * column group; group gi takes the column groups of
+  // NN_COLS columns j0 = NN_COLS (gi + ngroups i)
+  const int rowblocks = (L + blockDim.x - 1) / blockDim.x;
+  const int rb = blockIdx.x % rowblocks, gi = blockIdx.x / rowblocks;
+  const int ngroups = gridDim.x / rowblocks;
+  const int l = rb * blockDim.x + threadIdx.x;
   const V* Ak = A + k * sA;
   const double2* Bk = B + k * sB;
   VC* Ck = C + k * sC;
@@ -304,7 +330,7 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
   V zero;
   zero.x = 0;
   zero.y = 0;
-  for (int j0 = 0; j0 < n; j0 += NN_COLS) {
+  for (int j0 = NN_COLS * gi; j0 < n; j0 += NN_COLS * ngroups) {
     V acc[NN_COLS];
 #pragma unroll
     for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = zero;
@@ -343,7 +369,13 @@ static void gemm_nn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, i
                       int ldb, VC* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                       cudaStream_t st) {
   if (K <= 0 || L <= 0 || n <= 0) return;
-  dim3 g((L + 127) / 128, K);
+  // every output element is one thread's fixed-order sum whatever the split, so the column
+  // groups only spread small problems over more SMs (GB300's FP64 units are 2 FMA per SM-clock)
+  const int rowblocks = (L + 127) / 128;
+  const int colgroups = (n + NN_COLS - 1) / NN_COLS;
+  const int want = (GEMM_TARGET_CTAS + rowblocks * K - 1) / (rowblocks * K);
+  const int groups = std::max(1, std::min(colgroups, want));
+  dim3 g(rowblocks * groups, K);
   k_gemm_nn<T, VC><<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
   count_launch();
 }

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/eacg.h"
@@ -143,6 +144,7 @@ struct eacg_system {
   bool frozen = false;
   double* d_rho_in = nullptr;         // SCF input density (allocated by the first SCF call)
   bool tc_proj = false;               // FP32 projector overlaps on the tensor cores
+  cudaEvent_t ev_sync = nullptr;      // blocking-sync event of the host waits (stream_wait)
 };
 
 namespace {
@@ -271,11 +273,25 @@ static void dfree(eacg_system* s, void* p) {
   cudaFree(p);
 }
 
+// Waits for the system's stream.  A short poll (with yields) covers the usual sub-millisecond
+// waits of small problems; after it the thread blocks on an event created with
+// cudaEventBlockingSync instead of spinning, so that the host threads of many concurrent
+// systems do not keep every core busy polling the GPU.
+static cudaError_t stream_wait(eacg_system* s) {
+  if (!s->ev_sync) return cudaStreamSynchronize(s->st);
+  cudaError_t e = cudaEventRecord(s->ev_sync, s->st);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < 64; ++i) {
+    e = cudaEventQuery(s->ev_sync);
+    if (e != cudaErrorNotReady) return e;
+    std::this_thread::yield();
+  }
+  return cudaEventSynchronize(s->ev_sync);
+}
+
 static eacg_status sync_read(eacg_system* s, int ndouble) {
-
-
   CK(cudaMemcpyAsync(s->h_out, s->d_out, sizeof(double) * ndouble, cudaMemcpyDeviceToHost, s->st));
-  CK(cudaStreamSynchronize(s->st));
+  CK(stream_wait(s));
   return EACG_OK;
 }
 
@@ -704,10 +720,8 @@ static eacg_status density_and_potential(eacg_system* s, const double2* phi, int
 // Sum of the 3 * nblk strided block sums of k_vtot_energy, done on the host after one copy.
 static eacg_status fetch_grid_energies(eacg_system* s, double* eloc, double* eh, double* ex) {
   const int nblk = 256;
-
-
   CK(cudaMemcpyAsync(s->h_out, s->d_esum, sizeof(double) * 3 * nblk, cudaMemcpyDeviceToHost, s->st));
-  CK(cudaStreamSynchronize(s->st));
+  CK(stream_wait(s));
   double a = 0, b = 0, c = 0;
   for (int i = 0; i < nblk; ++i) {
     a += s->h_out[3 * i];
@@ -1125,7 +1139,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
   q = p;
   // rank of the first block
   CK(cudaMemcpyAsync(s->h_int + K, s->d_nzero, sizeof(int) * K, cudaMemcpyDeviceToHost, s->st));
-  CK(cudaStreamSynchronize(s->st));
+  CK(stream_wait(s));
   for (int k = 0; k < K; ++k)
     if (active[k] && s->h_int[K + k] >= p) active[k] = 0;  // rank 0: nothing to solve
   int j = 0;
@@ -1191,7 +1205,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     PROF_RUN(P_FOM_ORTH, 4.0 * K * q * nm * sizeof(V), 32.0 * K * nm * q * p, 0,
              TRY(orthonormalise<T>(s, t2, fV, q, (size_t)s->qcap * nm, vt, t3, s->d_kactive)));
     CK(cudaMemcpyAsync(s->h_int + K, s->d_nzero, sizeof(int) * K, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
+    CK(stream_wait(s));
     bool any2 = false;
     for (int k = 0; k < K; ++k) {
       if (active[k] && s->h_int[K + k] >= p) {
@@ -1852,6 +1866,10 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   if ((st = build_potential_and_projectors(s)) != EACG_OK) return fail(st);
   s->tc_proj = s->prm.tensor_cores && s->nproj > 0 && dense_overlap_tc_eligible(s->nproj, s->p);
   if ((st = alloc_work(s)) != EACG_OK) return fail(st);
+  if (cudaEventCreateWithFlags(&s->ev_sync, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    s->ev_sync = nullptr;  // waits fall back to cudaStreamSynchronize
+  }
   if ((st = autotune_plans(s)) != EACG_OK) return fail(st);
   if ((st = autotune_gemm(s)) != EACG_OK) return fail(st);
   if (cudaStreamSynchronize(s->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -1867,6 +1885,7 @@ extern "C" void eacg_destroy(eacg_system* s) {
   if (s->st) cudaStreamSynchronize(s->st);
   for (auto& g : s->hg) hg_release(g);
   for (cudaEvent_t e : s->evpool) cudaEventDestroy(e);
+  if (s->ev_sync) cudaEventDestroy(s->ev_sync);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_out) cudaFreeHost(s->h_out);
   if (s->h_int) cudaFreeHost(s->h_int);
