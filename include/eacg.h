@@ -114,6 +114,11 @@ typedef struct {
                        * method 1) and the back-projection of FP32-phase evaluations (nbands <= 256;
                        * eacg_backproject_c64, method 1) on the tensor cores; 0: SIMT FP32.
                        * Default 1 */
+  int df_transforms;  /* 1: the FP64-accurate transforms (FP64 mode, the FP64 phase of the mixed
+                       * mode and the density) run in double-float arithmetic, each value an
+                       * unevaluated sum of two FP32 numbers (about 48 significant bits, 1e-14
+                       * relative error on a transform), on GB300's FP32 pipe, which is 64 times
+                       * wider than its FP64 pipe; 0: plain FP64 arithmetic.  Default 1 */
 } eacg_params;
 
 typedef struct {

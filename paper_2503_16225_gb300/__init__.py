@@ -47,7 +47,8 @@ class EacgParams(ctypes.Structure):
                 ("eps", ctypes.c_double), ("warm_res", ctypes.c_double), ("switch_res", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("max_warm", ctypes.c_int), ("max_fom", ctypes.c_int),
                 ("max_ls", ctypes.c_int), ("precision", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("fft_plan", ctypes.c_int), ("method", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("fft_plan", ctypes.c_int), ("method", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("df_transforms", ctypes.c_int)]
 
 
 class EacgStepInfo(ctypes.Structure):

@@ -69,6 +69,8 @@ struct eacg_system {
   float2* d_tw32 = nullptr;
   double *d_vloc = nullptr, *d_vtot = nullptr, *d_rho = nullptr, *d_vh = nullptr, *d_partial = nullptr;
   float* d_vtot32 = nullptr;
+  float2* d_vtotdf = nullptr;         // double-float copy of V_tot (hi, lo)
+  void* d_twdf = nullptr;             // double-float twiddles
   double2* d_fft3 = nullptr;
   double2 *d_B = nullptr, *d_P = nullptr, *d_P2 = nullptr;
   float2* d_B32 = nullptr;
@@ -364,6 +366,7 @@ extern "C" void eacg_default_params(eacg_params* prm) {
   prm->fft_plan = -1;
   prm->method = 0;
   prm->tensor_cores = 1;
+  prm->df_transforms = 1;
 }
 
 static double sphere_volume_estimate(const eacg_model* m) {
@@ -455,6 +458,7 @@ static eacg_status build_potential_and_projectors(eacg_system* s) {
   TRY(dalloc(s, &s->d_vloc, sizeof(double) * N3));
   TRY(dalloc(s, &s->d_vtot, sizeof(double) * N3));
   TRY(dalloc(s, &s->d_vtot32, sizeof(float) * N3));
+  TRY(dalloc(s, &s->d_vtotdf, sizeof(float2) * N3));
   TRY(dalloc(s, &s->d_vh, sizeof(double) * N3));
   TRY(dalloc(s, &s->d_rho, sizeof(double) * N3));
   grid_vloc_g(N, s->b, s->omega, s->natoms, s->d_pos, s->d_Z, s->d_rc, s->d_fft3, s->st);
@@ -466,7 +470,7 @@ static eacg_status build_potential_and_projectors(eacg_system* s) {
   {
     double* esum = nullptr;
     TRY(dalloc(s, &esum, sizeof(double) * 3 * 256));
-    grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, 0, 0, s->d_vtot, s->d_vtot32, esum, s->st);
+    grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, 0, 0, s->d_vtot, s->d_vtot32, s->d_vtotdf, esum, s->st);
     CKL(s);
     CK(cudaStreamSynchronize(s->st));
     dfree(s, esum);
@@ -603,6 +607,13 @@ static eacg_status fom_reserve(eacg_system* s, int qneed) {
 }
 
 // ============================================================================ operators
+// The potential the plane kernels multiply by: FP32 copy for FP32 transforms, the double-float
+// copy or the FP64 grid for FP64-accurate ones.
+static const void* vpot(const eacg_system* s, int prec) {
+  if (prec) return s->d_vtot32;
+  return s->g.df64 ? (const void*)s->d_vtotdf : (const void*)s->d_vtot;
+}
+
 // P = B32^* in32 (projector overlaps of complex64 blocks): on the tensor cores (3 x TF32) when
 // the shape allows it, else the SIMT FP32 block-overlap kernel.
 static void projector_overlaps32(eacg_system* s, const float2* in32, const int* kactive) {
@@ -630,7 +641,7 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
   PROF_RUN(P_XINV + off, nb * (coef + inter), fx, nb,
            grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st));
   PROF_RUN(P_PLANE_H + off, nb * 2.0 * inter + N3 * (prec ? 4.0 : 8.0), fp, nb,
-           grid_plane_h(s->g, prec, s->d_tbuf, prec ? (const void*)s->d_vtot32 : (const void*)s->d_vtot, nb, kactive,
+           grid_plane_h(s->g, prec, s->d_tbuf, vpot(s, prec), nb, kactive,
                         s->st));
   PROF_RUN(P_XFWD + off, nb * (inter + 2.0 * coef), fx, nb,
            grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
@@ -703,8 +714,8 @@ static eacg_status potential_from_rho(eacg_system* s) {
       grid_fft3(s->g, s->d_fft3, true, s->st);
       grid_complex_real_part(s->d_fft3, s->d_vh, N3, s->st);
     }
-    nblk = grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, s->hartree, s->xc, s->d_vtot, s->d_vtot32, s->d_esum,
-                            s->st);
+    nblk = grid_vtot_energy(N3, s->d_vloc, s->d_vh, s->d_rho, s->hartree, s->xc, s->d_vtot, s->d_vtot32,
+                            s->d_vtotdf, s->d_esum, s->st);
   });
   CKL(s);
   return (nblk == 256) ? EACG_OK : EACG_ECUDA;
@@ -1701,7 +1712,7 @@ static eacg_status autotune_plans(eacg_system* s) {
   CK(cudaEventCreate(&b));
   int choice[2] = {0, 0};
   for (int prec = 0; prec < 2; ++prec) {
-    const void* v = prec == 0 ? (const void*)s->d_vtot : (const void*)s->d_vtot32;
+    const void* v = vpot(s, prec);
     const int reps = prec == 0 ? 1 : 4;
     float best = 0.f;
     for (int plan = 0; plan < 2; ++plan) {
@@ -1841,10 +1852,22 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
       tw[k] = make_double2(std::cos(ang), -std::sin(ang));
       tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
     }
+    // double-float twiddles: each component as its nearest (hi, lo) FP32 pair
+    std::vector<float> twdf(4 * (size_t)s->N);
+    for (int k = 0; k < s->N; ++k) {
+      const double c[2] = {tw[k].x, tw[k].y};
+      for (int q = 0; q < 2; ++q) {
+        const float hi = (float)c[q];
+        twdf[4 * k + 2 * q] = hi;
+        twdf[4 * k + 2 * q + 1] = (float)(c[q] - (double)hi);
+      }
+    }
     if ((st = dalloc(s, &s->d_tw64, sizeof(double2) * s->N)) != EACG_OK) return fail(st);
     if ((st = dalloc(s, &s->d_tw32, sizeof(float2) * s->N)) != EACG_OK) return fail(st);
+    if ((st = dalloc(s, &s->d_twdf, sizeof(float) * twdf.size())) != EACG_OK) return fail(st);
     cudaMemcpyAsync(s->d_tw64, tw.data(), sizeof(double2) * s->N, cudaMemcpyHostToDevice, s->st);
     cudaMemcpyAsync(s->d_tw32, tw32.data(), sizeof(float2) * s->N, cudaMemcpyHostToDevice, s->st);
+    cudaMemcpyAsync(s->d_twdf, twdf.data(), sizeof(float) * twdf.size(), cudaMemcpyHostToDevice, s->st);
     if (cudaStreamSynchronize(s->st) != cudaSuccess) {
       s->err = "stream synchronise failed during set-up";
       return fail(EACG_ECUDA);
@@ -1863,6 +1886,8 @@ extern "C" eacg_status eacg_create_system(const eacg_model* m, const eacg_params
   s->g.ylist = s->d_ylist;
   s->g.tw64 = s->d_tw64;
   s->g.tw32 = s->d_tw32;
+  s->g.twdf = s->d_twdf;
+  s->g.df64 = s->prm.df_transforms ? 1 : 0;
   if ((st = build_potential_and_projectors(s)) != EACG_OK) return fail(st);
   s->tc_proj = s->prm.tensor_cores && s->nproj > 0 && dense_overlap_tc_eligible(s->nproj, s->p);
   if ((st = alloc_work(s)) != EACG_OK) return fail(st);

@@ -68,9 +68,9 @@ __device__ __forceinline__ void dft_small(V* v) {
     v[0] = a + b;
     v[1] = a - b;
   } else if constexpr (R == 3) {
-    const T h = (T)0.86602540378443864676372317075293618;  // sin(2 pi / 3)
+    constexpr T h = T(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
     V t1 = v[1] + v[2];
-    V t2 = v[0] - cscale(t1, (T)0.5);
+    V t2 = v[0] - cscale(t1, T(0.5));
     V d = mul_mi<INV>(cscale(v[1] - v[2], h));
     v[0] = v[0] + t1;
     v[1] = t2 + d;
@@ -83,10 +83,10 @@ __device__ __forceinline__ void dft_small(V* v) {
     v[1] = t1 + t3;
     v[3] = t1 - t3;
   } else if constexpr (R == 5) {
-    const T c1 = (T)0.30901699437494742410229341718281906;   // cos(2 pi / 5)
-    const T c2 = (T)-0.80901699437494742410229341718281906;  // cos(4 pi / 5)
-    const T s1 = (T)0.95105651629515357211643933337938214;   // sin(2 pi / 5)
-    const T s2 = (T)0.58778525229247312916870595463907277;   // sin(4 pi / 5)
+    constexpr T c1 = T(0.30901699437494742410229341718281906);   // cos(2 pi / 5)
+    constexpr T c2 = T(-0.80901699437494742410229341718281906);  // cos(4 pi / 5)
+    constexpr T s1 = T(0.95105651629515357211643933337938214);   // sin(2 pi / 5)
+    constexpr T s2 = T(0.58778525229247312916870595463907277);   // sin(4 pi / 5)
     V t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
     V a1 = v[0] + cscale(t1, c1) + cscale(t2, c2);
     V a2 = v[0] + cscale(t1, c2) + cscale(t2, c1);

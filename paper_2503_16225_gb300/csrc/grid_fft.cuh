@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(XPASS_THREADS) k_xpass_inv(const __grid_consta
       nc, tw, PitchedScratch<V>{A, N + 1},
       [&](int l, int fx) {
         const int id = xm[(size_t)fx * ncols + l];
-        return id >= 0 ? cvt<V>(src[id]) : mk<V>(0, 0);
+        return id >= 0 ? cvt<V>(src[id]) : czero<V>();
       },
       [&](int l, int jx, V x, int) { dst[(size_t)jx * ncols + l] = x; });
 }
@@ -175,12 +175,12 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_h(const __gri
       ny, tw, zs,
       [&](int l, int fz) {
         const int c = cm[l * PP + fz];
-        return c >= 0 ? tb[c] : mk<V>(0, 0);
+        return c >= 0 ? tb[c] : czero<V>();
       },
       [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
   // y inverse over every jz (rows without columns are zero), times the potential
   fft_phase<N, PV, true, !PING>(
-      N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
+      N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : czero<V>(); },
       [&](int jz, int jy, V x, int) { B[jy * PP + jz] = cscale(x, vv[jy * N + jz]); });
   // y forward, keeping the rows with columns
   fft_phase<N, PV, false, !PING>(
@@ -197,8 +197,33 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_h(const __gri
       });
 }
 
-// Density of a group of bands on one x-plane: sum_b w_b |u_b|^2 in FP64 registers (each
-// grid point owned by one thread of the y pass, bands in a fixed order), written as
+// Accumulator of the density: FP64 for FP32 and FP64 transforms, double-float for
+// double-float transforms (FP64-accurate without the FP64 pipe).
+template <typename T>
+struct RhoAcc {
+  using type = double;
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double weight(double w) { return w; }
+  template <typename V>
+  static __device__ __forceinline__ double add(double acc, double w, V x) {
+    const double2 u = to_d(x);
+    return acc + w * (u.x * u.x + u.y * u.y);
+  }
+  static __device__ __forceinline__ double out(double a) { return a; }
+};
+template <>
+struct RhoAcc<dfloat> {
+  using type = dfloat;
+  static __device__ __forceinline__ dfloat zero() { return dfloat(0.0f, 0.0f); }
+  static __device__ __forceinline__ dfloat weight(double w) { return df_from(w); }
+  static __device__ __forceinline__ dfloat add(dfloat acc, dfloat w, dcomplex x) {
+    return acc + w * (x.x * x.x + x.y * x.y);
+  }
+  static __device__ __forceinline__ double out(dfloat a) { return df_to(a); }
+};
+
+// Density of a group of bands on one x-plane: sum_b w_b |u_b|^2 accumulated per grid point
+// (each point owned by one thread of the y pass, bands in a fixed order), written as FP64
 // partial[g][jx][jy][jz].  Grid rows are the band groups of the segments.
 template <typename T, int N, int PV>
 __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_rho(const __grid_constant__ GridSegs tab) {
@@ -217,9 +242,10 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_rho(const __g
   plane_setup<V, N>(tw, rows, yl, cm, static_cast<const V*>(S.tw), S.rowmask, S.ylist, S.cmapy, ny);
   const ZScratch<V, N, PING> zs{A, B, yl};
   const YScratch<V, N, PING> ys{A, B};
-  double acc[N1];
+  using Acc = RhoAcc<T>;
+  typename Acc::type acc[N1];
 #pragma unroll
-  for (int q = 0; q < N1; ++q) acc[q] = 0.0;
+  for (int q = 0; q < N1; ++q) acc[q] = Acc::zero();
   const int bpg = (nbands + S.groups - 1) / S.groups;
   const int b0 = g * bpg, b1 = min(nbands, b0 + bpg);
   const V* tbuf = static_cast<const V*>(S.tbuf);
@@ -229,16 +255,13 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_rho(const __g
         ny, tw, zs,
         [&](int l, int fz) {
           const int c = cm[l * PP + fz];
-          return c >= 0 ? tb[c] : mk<V>(0, 0);
+          return c >= 0 ? tb[c] : czero<V>();
         },
         [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
-    const double w = S.bw[band];
+    const auto w = Acc::weight(S.bw[band]);
     fft_phase<N, PV, true, false>(
-        N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : mk<V>(0, 0); },
-        [&](int, int, V x, int q) {
-          const double2 u = to_d(x);
-          acc[q] += w * (u.x * u.x + u.y * u.y);
-        });
+        N, tw, ys, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : czero<V>(); },
+        [&](int, int, V x, int q) { acc[q] = Acc::add(acc[q], w, x); });
   }
   // thread (jz, t) of the y pass owns jy = (t + N2 j) + N1 k2 at q = j N2 + k2
   const int L = blockDim.x / N2;
@@ -248,7 +271,7 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_rho(const __g
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       const int jy = (t + N2 * (q / N2)) + N1 * (q % N2);
-      out[(size_t)jy * N + jz] = acc[q];
+      out[(size_t)jy * N + jz] = Acc::out(acc[q]);
     }
   }
 }
@@ -278,6 +301,11 @@ __global__ void __launch_bounds__(XPASS_THREADS)
       [&](int l, int o, double2 x, int) { a[addr(l, o)] = x; });
 }
 
+template <typename T>
+struct TwKind {
+  static constexpr int value = std::is_same<T, float>::value ? 1 : std::is_same<T, dfloat>::value ? 2 : 0;
+};
+
 // Launchers of one grid size and line-plan variant; instantiated per supported (N, variant)
 // in the grid_fft_*.cu units.  Each launch covers the requests r[0..n) (n <= GRID_MAX_SEGS).
 template <int N, int PV>
@@ -285,7 +313,8 @@ struct GridFft {
   static constexpr int N2 = LinePlan<N, PV>::N2;
 
   // segment table of the requests; rows(i) = grid rows of request i; returns the total
-  static int table(GridSegs& t, const GridReq* r, int n, int mode_t32, bool groups_as_rows) {
+  // tw_kind: 0 FP64 twiddles, 1 FP32, 2 double-float
+  static int table(GridSegs& t, const GridReq* r, int n, int tw_kind, bool groups_as_rows) {
     int y = 0;
     t.n = n;
     for (int i = 0; i < n; ++i) {
@@ -302,7 +331,7 @@ struct GridFft {
       S.cmapy = g.cmapy;
       S.ylist = g.ylist;
       S.rowmask = g.rowmask;
-      S.tw = mode_t32 ? g.tw32 : g.tw64;
+      S.tw = tw_kind == 1 ? g.tw32 : tw_kind == 2 ? g.twdf : g.tw64;
       S.bw = r[i].bw;
       S.partial = r[i].partial;
       S.scale = r[i].scale;
@@ -331,7 +360,7 @@ struct GridFft {
   template <typename T, typename TIO>
   static void xinv(const GridReq* r, int n, cudaStream_t st) {
     GridSegs t;
-    const int rows = table(t, r, n, sizeof(T) == 4, false);
+    const int rows = table(t, r, n, TwKind<T>::value, false);
     const int cpc = XPASS_THREADS / N2;
     dim3 grid((max_cols(r, n) + cpc - 1) / cpc, rows);
     const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
@@ -343,7 +372,7 @@ struct GridFft {
   template <typename T, typename TIO>
   static void xfwd(const GridReq* r, int n, cudaStream_t st) {
     GridSegs t;
-    const int rows = table(t, r, n, sizeof(T) == 4, false);
+    const int rows = table(t, r, n, TwKind<T>::value, false);
     const int cpc = XPASS_THREADS / N2;
     dim3 grid((max_cols(r, n) + cpc - 1) / cpc, rows);
     const size_t sm = sizeof(cplx<T>) * (size_t)cpc * (N + 1);
@@ -354,57 +383,35 @@ struct GridFft {
 
   // mode 0: FP64 transforms of FP64 blocks; 1: FP32 transforms of FP64 blocks;
   // 2: FP32 transforms of FP32 blocks
-  static void xpass_inv(int mode, const GridReq* r, int n, cudaStream_t st) {
-    if (mode == 0)
-      xinv<double, double2>(r, n, st);
-    else if (mode == 1)
-      xinv<float, double2>(r, n, st);
-    else
-      xinv<float, float2>(r, n, st);
-  }
+  // mode 3: double-float transforms of FP64 blocks
+  static void xpass_inv(int mode, const GridReq* r, int n, cudaStream_t st);
 
-  static void xpass_fwd(int mode, const GridReq* r, int n, cudaStream_t st) {
-    if (mode == 0)
-      xfwd<double, double2>(r, n, st);
-    else if (mode == 1)
-      xfwd<float, double2>(r, n, st);
-    else
-      xfwd<float, float2>(r, n, st);
-  }
+  static void xpass_fwd(int mode, const GridReq* r, int n, cudaStream_t st);
 
   template <typename T>
   static void plane_h_t(const GridReq* r, int n, cudaStream_t st) {
     GridSegs t;
-    const int rows = table(t, r, n, sizeof(T) == 4, false);
+    const int rows = table(t, r, n, TwKind<T>::value, false);
     const size_t sm = PlaneCfg<T, N>::smem_bytes(max_ny(r, n));
     ensure_smem((const void*)k_plane_h<T, N, PV>, sm);
     k_plane_h<T, N, PV><<<dim3(N, rows), N * N2, sm, st>>>(t);
     count_launch();
   }
 
-  static void plane_h(int prec, const GridReq* r, int n, cudaStream_t st) {
-    if (prec == 0)
-      plane_h_t<double>(r, n, st);
-    else
-      plane_h_t<float>(r, n, st);
-  }
+  // prec 0: FP64, 1: FP32, 2: double-float
+  static void plane_h(int prec, const GridReq* r, int n, cudaStream_t st);
 
   template <typename T>
   static void plane_rho_t(const GridReq* r, int n, cudaStream_t st) {
     GridSegs t;
-    const int rows = table(t, r, n, sizeof(T) == 4, true);
+    const int rows = table(t, r, n, TwKind<T>::value, true);
     const size_t sm = PlaneCfg<T, N>::smem_bytes(max_ny(r, n));
     ensure_smem((const void*)k_plane_rho<T, N, PV>, sm);
     k_plane_rho<T, N, PV><<<dim3(N, rows), N * N2, sm, st>>>(t);
     count_launch();
   }
 
-  static void plane_rho(int prec, const GridReq* r, int n, cudaStream_t st) {
-    if (prec == 0)
-      plane_rho_t<double>(r, n, st);
-    else
-      plane_rho_t<float>(r, n, st);
-  }
+  static void plane_rho(int prec, const GridReq* r, int n, cudaStream_t st);
 
   template <bool INV>
   static void fft3_axis(const GridCtx& g, double2* a, int axis, cudaStream_t st) {
@@ -415,14 +422,64 @@ struct GridFft {
     count_launch();
   }
 
-  static void fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
-    for (int axis = 2; axis >= 0; --axis) {
-      if (inverse)
-        fft3_axis<true>(g, a, axis, st);
-      else
-        fft3_axis<false>(g, a, axis, st);
-    }
-  }
+  static void fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st);
 };
+
+// Dispatchers defined outside the class, so that they are not inline: the explicit
+// instantiations in the grid_fft_*.cu units are then the only ones, and other translation
+// units see only their declarations (extern template).
+template <int N, int PV>
+void GridFft<N, PV>::xpass_inv(int mode, const GridReq* r, int n, cudaStream_t st) {
+  if (mode == 0)
+    xinv<double, double2>(r, n, st);
+  else if (mode == 1)
+    xinv<float, double2>(r, n, st);
+  else if (mode == 2)
+    xinv<float, float2>(r, n, st);
+  else
+    xinv<dfloat, double2>(r, n, st);
+}
+
+template <int N, int PV>
+void GridFft<N, PV>::xpass_fwd(int mode, const GridReq* r, int n, cudaStream_t st) {
+  if (mode == 0)
+    xfwd<double, double2>(r, n, st);
+  else if (mode == 1)
+    xfwd<float, double2>(r, n, st);
+  else if (mode == 2)
+    xfwd<float, float2>(r, n, st);
+  else
+    xfwd<dfloat, double2>(r, n, st);
+}
+
+template <int N, int PV>
+void GridFft<N, PV>::plane_h(int prec, const GridReq* r, int n, cudaStream_t st) {
+  if (prec == 0)
+    plane_h_t<double>(r, n, st);
+  else if (prec == 1)
+    plane_h_t<float>(r, n, st);
+  else
+    plane_h_t<dfloat>(r, n, st);
+}
+
+template <int N, int PV>
+void GridFft<N, PV>::plane_rho(int prec, const GridReq* r, int n, cudaStream_t st) {
+  if (prec == 0)
+    plane_rho_t<double>(r, n, st);
+  else if (prec == 1)
+    plane_rho_t<float>(r, n, st);
+  else
+    plane_rho_t<dfloat>(r, n, st);
+}
+
+template <int N, int PV>
+void GridFft<N, PV>::fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
+  for (int axis = 2; axis >= 0; --axis) {
+    if (inverse)
+      fft3_axis<true>(g, a, axis, st);
+    else
+      fft3_axis<false>(g, a, axis, st);
+  }
+}
 
 }  // namespace eacg

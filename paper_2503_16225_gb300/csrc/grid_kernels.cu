@@ -208,7 +208,8 @@ __device__ __forceinline__ double pw92_correlation(double rho, double* vc) {
 // block; xc: 0 none, 1 Slater exchange, 2 Slater exchange + PW92 correlation.
 __global__ void k_vtot_energy(size_t n, const double* __restrict__ vloc, const double* __restrict__ vh,
                               const double* __restrict__ rho, int hartree, int xc, double* __restrict__ vtot,
-                              float* __restrict__ vtot32, double* __restrict__ blocksums /*[gridDim][3]*/) {
+                              float* __restrict__ vtot32, float2* __restrict__ vtotdf,
+                              double* __restrict__ blocksums /*[gridDim][3]*/) {
   __shared__ double sh[3][256];
   double el = 0.0, eh = 0.0, ex = 0.0;
   const double cx = -0.75 * cbrt(3.0 / M_PI);
@@ -233,6 +234,10 @@ __global__ void k_vtot_energy(size_t n, const double* __restrict__ vloc, const d
     }
     vtot[i] = v;
     if (vtot32) vtot32[i] = (float)v;
+    if (vtotdf) {
+      const dfloat d = df_from(v);  // double-float copy for the double-float transforms
+      vtotdf[i] = make_float2(d.hi, d.lo);
+    }
   }
   sh[0][threadIdx.x] = el;
   sh[1][threadIdx.x] = eh;
@@ -341,8 +346,13 @@ static void dispatch_n(int N, int plan, const F& f) {
   }
 }
 
-// line-plan variant of the transforms in this precision (0: FP64, else FP32)
+// line-plan variant of the transforms in this precision (0: FP64-accurate, else FP32)
 static int plan_of(const GridCtx& g, int prec) { return prec == 0 ? g.plan64 : g.plan32; }
+// launch mode of the x passes of FP64 blocks and precision of the plane kernels: the
+// FP64-accurate transforms run on the FP64 pipe (mode 0 / prec 0) or in double-float
+// arithmetic (mode 3 / prec 2)
+static int xmode_of(const GridCtx& g, int prec) { return prec != 0 ? 1 : g.df64 ? 3 : 0; }
+static int pprec_of(const GridCtx& g, int prec) { return prec != 0 ? 1 : g.df64 ? 2 : 0; }
 
 // Launches f over chunks of at most GRID_MAX_SEGS requests.
 template <typename F>
@@ -387,7 +397,7 @@ void grid_xpass_inv(const GridCtx& g, int prec, const double2* psi, void* tbuf, 
   GridReq r = req_of(g, nbands, kactive);
   r.in = psi;
   r.tbuf = tbuf;
-  grid_xpass_inv_multi(g.N, plan_of(g, prec), prec == 0 ? 0 : 1, &r, 1, st);
+  grid_xpass_inv_multi(g.N, plan_of(g, prec), xmode_of(g, prec), &r, 1, st);
 }
 
 void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2* psi_in, const double* kin,
@@ -398,7 +408,7 @@ void grid_xpass_fwd(const GridCtx& g, int prec, const void* tbuf, const double2*
   r.out = out;
   r.kin = kin;
   r.scale = scale;
-  grid_xpass_fwd_multi(g.N, plan_of(g, prec), prec == 0 ? 0 : 1, &r, 1, st);
+  grid_xpass_fwd_multi(g.N, plan_of(g, prec), xmode_of(g, prec), &r, 1, st);
 }
 
 void grid_xpass_inv32(const GridCtx& g, const float2* psi, void* tbuf, int nbands, const int* kactive,
@@ -425,7 +435,7 @@ void grid_plane_h(const GridCtx& g, int prec, void* tbuf, const void* v, int nba
   GridReq r = req_of(g, nbands, kactive);
   r.tbuf = tbuf;
   r.v = v;
-  grid_plane_h_multi(g.N, plan_of(g, prec), prec, &r, 1, st);
+  grid_plane_h_multi(g.N, plan_of(g, prec), pprec_of(g, prec), &r, 1, st);
 }
 
 void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, int groups, const double* bw,
@@ -435,7 +445,7 @@ void grid_plane_rho(const GridCtx& g, int prec, const void* tbuf, int nbands, in
   r.bw = bw;
   r.partial = partial;
   r.groups = groups;
-  grid_plane_rho_multi(g.N, plan_of(g, prec), prec, &r, 1, st);
+  grid_plane_rho_multi(g.N, plan_of(g, prec), pprec_of(g, prec), &r, 1, st);
 }
 
 void grid_fft3(const GridCtx& g, double2* a, bool inverse, cudaStream_t st) {
@@ -481,9 +491,9 @@ void grid_complex_real_part(const double2* c, double* r, size_t n, cudaStream_t 
   count_launch();
 }
 int grid_vtot_energy(size_t n, const double* vloc, const double* vh, const double* rho, int hartree, int xc,
-                     double* vtot, float* vtot32, double* blocksums, cudaStream_t st) {
+                     double* vtot, float* vtot32, float2* vtotdf, double* blocksums, cudaStream_t st) {
   const int blocks = 256;
-  k_vtot_energy<<<blocks, 256, 0, st>>>(n, vloc, vh, rho, hartree, xc, vtot, vtot32, blocksums);
+  k_vtot_energy<<<blocks, 256, 0, st>>>(n, vloc, vh, rho, hartree, xc, vtot, vtot32, vtotdf, blocksums);
   count_launch();
   return blocks;
 }

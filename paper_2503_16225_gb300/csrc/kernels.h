@@ -28,6 +28,8 @@ struct GridCtx {
   const int* ylist;    // [ny]: the rows fy that hold columns
   const void* tw64;    // double2[N]
   const void* tw32;    // float2[N]
+  const void* twdf;    // dcomplex[N]
+  int df64;            // 1: the FP64-accurate transforms run in double-float arithmetic
 };
 
 // One system's share of a transform launch.  A launch covers the bands of up to
@@ -115,7 +117,7 @@ void grid_hartree_scale(double2* a, int N, double b, cudaStream_t st);
 void grid_real_to_complex(const double* r, double2* c, size_t n, cudaStream_t st);
 void grid_complex_real_part(const double2* c, double* r, size_t n, cudaStream_t st);
 int grid_vtot_energy(size_t n, const double* vloc, const double* vh, const double* rho, int hartree, int xc,
-                     double* vtot, float* vtot32, double* blocksums, cudaStream_t st);
+                     double* vtot, float* vtot32, float2* vtotdf, double* blocksums, cudaStream_t st);
 void grid_projectors(int K, int n_max, const int* nk, const int* m, const double* kfrac, double b, double omega,
                      int natoms, const double* pos, int npa, double w, double2* B, cudaStream_t st);
 

@@ -3,9 +3,11 @@
 Each supported N gets a small two-atom crystal (two bands, s/p projectors, a shifted
 k-point) whose cutoff sphere reaches about a quarter of the grid, so that every
 transform phase (x columns, z rows, y lines, the potential multiply, the density) runs
-on several lines with a partial disk.  Density and potential (FP64 transforms, including
-the full 3D FFT of the Hartree term) to relative 1e-11; H psi to 1e-11 with FP64
-transforms and 5e-6 with FP32 transforms (the tolerances of the main parity suite)."""
+on several lines with a partial disk.  Density and potential (FP64-accurate transforms,
+including the full 3D FFT of the Hartree term) to relative 1e-11; H psi to 1e-11 with
+FP64-accurate transforms and 5e-6 with FP32 transforms (the tolerances of the main parity
+suite).  The FP64-accurate transforms run both ways: in double-float arithmetic (pairs of
+FP32 numbers, the default) and in plain FP64."""
 import math
 
 import numpy as np
@@ -25,7 +27,7 @@ import paper_2503_16225_gb300 as E  # noqa: E402
 
 GRID_N = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96)
 PLAN1_N = (16, 32, 36, 48, 64, 72)   # sizes with a second line plan
-CASES = [(n, 0) for n in GRID_N] + [(n, 1) for n in PLAN1_N]
+CASES = [(n, 0, 1) for n in GRID_N] + [(n, 1, 1) for n in PLAN1_N] + [(n, 0, 0) for n in GRID_N]
 
 
 def grid_model(N):
@@ -40,11 +42,11 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
 
 
-@pytest.mark.parametrize("N,plan", CASES)
-def test_grid_size(N, plan):
+@pytest.mark.parametrize("N,plan,df", CASES)
+def test_grid_size(N, plan, df):
     cfg = grid_model(N)
     model = Model(cfg)
-    s = E.System(cfg, E.eacg_default_params(fft_plan=plan))
+    s = E.System(cfg, E.eacg_default_params(fft_plan=plan, df_transforms=df))
     try:
         assert E.eacg_get_plans(s.h) == (plan, plan)
         assert s.nk == model.nk

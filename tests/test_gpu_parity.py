@@ -111,6 +111,36 @@ def test_apply_H(pair, prec, tol):
         assert np.all(h[k, :, model.nk[k]:] == 0)
 
 
+def test_fp64_transforms_in_double_float_and_plain_fp64(pair):
+    """The FP64-accurate transforms in double-float arithmetic (default) and on the FP64 pipe
+    give the oracle's density and H psi to 1e-11, and each other's to 1e-13 (the double-float
+    pairs carry about 48 significant bits, so both are rounding-level copies of the exact
+    transform)."""
+    name, cfg, model, s = pair
+    _, Phi = start_blocks(model, cfg, s.n_max)
+    rng = np.random.default_rng(8)
+    C = [rng.standard_normal(P.shape) + 1j * rng.standard_normal(P.shape) for P in Phi]
+    rho_o = model.density(Phi)
+    vtot = model.potentials(rho_o)[0]
+    got = {}
+    for df in (1, 0):
+        s2 = E.System(cfg, E.eacg_default_params(df_transforms=df))
+        try:
+            rho = s2.grid()
+            E.eacg_density(s2.h, to_dev(s2, Phi), rho, 0)
+            out = s2.block()
+            E.eacg_apply_H(s2.h, to_dev(s2, C), out, 0)
+            got[df] = (rho.cpu().numpy(), from_dev(out, model))
+        finally:
+            s2.close()
+        assert rel(got[df][0], rho_o) < 1e-11, df
+        for k in range(model.K):
+            assert rel(got[df][1][k], model.apply_H(k, C[k], vtot)) < 1e-11, (df, k)
+    assert rel(got[1][0], got[0][0]) < 1e-13
+    for k in range(model.K):
+        assert rel(got[1][1][k], got[0][1][k]) < 1e-13
+
+
 def test_energy_lambda_residual(pair):
     name, cfg, model, s = pair
     _, Phi = start_blocks(model, cfg, s.n_max)
