@@ -81,6 +81,12 @@ def parse():
     ap.add_argument("--concurrent", type=int, default=4,
                     help="one-workload solves: resident systems solved concurrently (own stream and host "
                          "thread each)")
+    ap.add_argument("--batch-window", type=int, default=-1,
+                    help="serving: batch the transforms of concurrently stepping systems, each waiting at most "
+                         "this many microseconds (eacg_batching); -1: off")
+    ap.add_argument("--step-many", action="store_true",
+                    help="one-workload solves: step the concurrent systems together with eacg_step_many "
+                         "(batched transform launches) instead of one host thread per system")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed region (short runs under a profiler): no e2e, FP64 sample, Poisson "
                          "latency runs or CPU baseline")
@@ -143,10 +149,11 @@ def config_of(args, cfg, world):
                             "1/8/27 k, N 20-64, p 1-23",
                 "arrivals": "all queued at t=0 (saturating load)", "precision": args.precision,
                 "method": args.method, "parallelism": f"replicas{world}", "max_resident": args.resident,
-                "l2": "inputs of the stream (GBs) exceed L2; no flush"}
+                "batch_window_us": args.batch_window, "l2": "inputs of the stream (GBs) exceed L2; no flush"}
     return {"workload": cfg["name"], "kpoints": len(cfg["kweight"]), "bands": cfg["nbands"], "grid": cfg["N"],
             "ecut": cfg["ecut"], "precision": args.precision, "method": args.method,
             "parallelism": f"replicas{world}", "concurrent_systems": max(1, args.concurrent),
+            "stepping": "eacg_step_many" if args.step_many else "one host thread per system",
             "l2": "flushed between rounds of concurrent solves (256 MiB write)"}
 
 
@@ -505,6 +512,7 @@ def run_serving(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = 1 if args.precision == "mixed" else 0
+    E.eacg_batching(args.batch_window)
     M = per_step(args.steps)
     timed = stream_ids(0, args.steps * M)
     warm = stream_ids(0, args.warmup * M)
@@ -647,6 +655,30 @@ def run_solve(args):
             res[i] = exc
         ends[i].record(st_i)
 
+    def many_on(res, ends):
+        """All systems stepped together by eacg_step_many until every one has converged."""
+        for sy, _ in systems:
+            E.eacg_set_psi(sy.h, psi0)
+        live = list(range(C))
+        iters = [0] * C
+        apps = [0] * C
+        while live:
+            infos, sts = E.eacg_step_many([systems[i][0].h for i in live], window_us=2000)
+            nxt = []
+            for j, i in enumerate(live):
+                iters[i] += 1
+                apps[i] = infos[j].h_band_apps
+                if infos[j].converged:
+                    res[i] = E.EacgResult(E=infos[j].E, rnorm=infos[j].rnorm, iterations=iters[i] - 1,
+                                          warm_iterations=0, status=0, ls_trials=0, h_band_apps=apps[i])
+                    ends[i].record(systems[i][1])
+                elif iters[i] > params.max_outer + 1:
+                    res[i] = RuntimeError("step_many: iteration cap")
+                    ends[i].record(systems[i][1])
+                else:
+                    nxt.append(i)
+            live = nxt
+
     def one_round():
         start = torch.cuda.Event(enable_timing=True)
         start.record(stream)
@@ -654,7 +686,10 @@ def run_solve(args):
             st_i.wait_event(start)
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(C)]
         res = [None] * C
-        ths = [threading.Thread(target=solve_on, args=(i, res, ends)) for i in range(C)]
+        if args.step_many:
+            ths = [threading.Thread(target=many_on, args=(res, ends))]
+        else:
+            ths = [threading.Thread(target=solve_on, args=(i, res, ends)) for i in range(C)]
         for t in ths:
             t.start()
         for t in ths:

@@ -313,6 +313,29 @@ eacg_status eacg_scf_guess(eacg_system* sys, const double* psi0_dev, double drho
 
 /* One outer iteration of Algorithm 3 (warm-up iterations first, see eacg_params). */
 eacg_status eacg_step(eacg_system* sys, eacg_step_info* info);
+/* One outer iteration of Algorithm 3 on each of nsys distinct systems, taken together (the
+ * serving form of eacg_step; Algorithm 3 itself is per system and unchanged).  Every system
+ * steps in a host thread of its own on its own stream; the plane-wave transforms of the H
+ * applications and densities that several systems reach at the same time are launched
+ * together, one launch per transform kernel over a table of (system, band) work items, for the
+ * systems that share the grid size, line plan and transform precision.  A system that reaches
+ * a transform waits at most window_us microseconds for the others to reach one.  Each band's
+ * arithmetic is that of an unbatched launch, so every result equals the one of eacg_step bit
+ * for bit.  infos (nsys entries) and statuses (nsys entries, each system's own eacg_status) may
+ * be NULL.  Returns EACG_OK when every step succeeded, else the first failing system's status;
+ * EACG_EINVAL for a NULL or repeated system or a negative window, EACG_EUNSUPPORTED for
+ * p > EACG_MAX_BANDS_DENSE.  The FOM's graph replay is not used inside batched steps. */
+eacg_status eacg_step_many(eacg_system* const* sys, int nsys, eacg_step_info* infos, int* statuses, int window_us);
+/* Process-wide batching of eacg_step: with window_us >= 0, concurrent eacg_step calls from
+ * different host threads (e.g. a serving loop with one thread per resident system) batch their
+ * transforms as eacg_step_many does, each waiting at most window_us microseconds; window_us = -1
+ * turns it off (the default).  Steps already running keep the setting they started with.
+ * EACG_EINVAL for window_us < -1.  Serving utility; the paper has no counterpart. */
+eacg_status eacg_batching(int window_us);
+/* Process-wide counts since start: batched transform groups launched by eacg_step_many and
+ * batched eacg_step calls (*groups) and the system requests they covered (*members; a group of
+ * one is a system that found no partner within the window).  Either pointer may be NULL. */
+eacg_status eacg_batch_counts(long long* groups, long long* members);
 /* Algorithm 3 to convergence: iterates eacg_step from the current iterate until the
  * residual ||R||_F of Sec. 5.3 is <= res_tol (status EACG_OK) or max_outer iterations
  * (EACG_ENOTCONV); E, ||R||_F and the counts in *out (out may not be NULL).  Errors of a step

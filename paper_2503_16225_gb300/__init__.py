@@ -19,7 +19,7 @@ __all__ = [
     "eacg_get_dims", "eacg_get_plans", "eacg_graph_launches", "eacg_gemm_tile", "eacg_force_gemm_tile", "eacg_get_basis", "eacg_set_psi", "eacg_get_psi", "eacg_density", "eacg_get_potential",
     "eacg_apply_H", "eacg_energy", "eacg_ea_gradient", "eacg_retract", "eacg_step", "eacg_solve",
     "eacg_solve_host", "eacg_profile_enable", "eacg_profile_read", "eacg_launch_count", "EacgKernelStat",
-    "eacg_stream_create", "eacg_stream_destroy", "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_backproject_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
+    "eacg_stream_create", "eacg_stream_destroy", "eacg_step_many", "eacg_batching", "eacg_batch_counts", "eacg_overlap_noalloc", "eacg_overlap_c64", "eacg_backproject_c64", "eacg_scf_guess", "System", "STATUS", "EACG_MAX_BANDS", "EACG_MAX_BANDS_DENSE",
 ]
 
 # band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
@@ -102,6 +102,10 @@ def _load():
         "eacg_ea_gradient": (ctypes.c_int, [vp, vp, vp, _ip, ctypes.c_int]),
         "eacg_retract": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, vp, vp]),
         "eacg_step": (ctypes.c_int, [vp, ctypes.POINTER(EacgStepInfo)]),
+        "eacg_step_many": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(EacgStepInfo), _ip,
+                                          ctypes.c_int]),
+        "eacg_batching": (ctypes.c_int, [ctypes.c_int]),
+        "eacg_batch_counts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "eacg_solve": (ctypes.c_int, [vp, ctypes.POINTER(EacgResult)]),
         "eacg_solve_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(EacgResult)]),
         "eacg_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -279,6 +283,32 @@ def eacg_step(sys):
     code = lib.eacg_step(sys, ctypes.byref(info))
     _check(sys, code)
     return info
+
+
+def eacg_step_many(systems, window_us=200, check=True):
+    """One step of each system (handles), taken together with batched transform launches;
+    returns (step infos, per-system status codes)."""
+    n = len(systems)
+    arr = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in systems])
+    infos = (EacgStepInfo * n)()
+    sts = (ctypes.c_int * n)()
+    code = lib.eacg_step_many(arr, n, infos, sts, int(window_us))
+    if check and code != 0:
+        bad = next(i for i in range(n) if sts[i] != 0) if any(sts[i] for i in range(n)) else 0
+        _check(systems[bad], code)
+    return list(infos), list(sts)
+
+
+def eacg_batching(window_us):
+    """Process-wide batching of concurrent eacg_step calls (window_us >= 0), or off (-1)."""
+    _check(None, lib.eacg_batching(int(window_us)))
+
+
+def eacg_batch_counts():
+    """(batched transform groups, system requests covered) since the process started."""
+    g, m = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(None, lib.eacg_batch_counts(ctypes.byref(g), ctypes.byref(m)))
+    return g.value, m.value
 
 
 def eacg_solve(sys, check=True):

@@ -9,7 +9,9 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <map>
 #include <mutex>
 #include <cstdio>
@@ -614,6 +616,177 @@ static const void* vpot(const eacg_system* s, int prec) {
   return s->g.df64 ? (const void*)s->d_vtotdf : (const void*)s->d_vtot;
 }
 
+// ---- cross-system batching of the transforms
+// Systems stepped together (eacg_step_many, or eacg_step with eacg_batching on) run in their
+// own host threads on their own streams.  When a system reaches the plane-wave transforms of
+// an H application or a density it hands them to the batcher and waits; the first system to
+// arrive leads: it waits until every stepping system is waiting, or the window has passed,
+// then launches the transforms of all waiting systems that share the grid size, line plan and
+// precision as one launch per kernel over a table of (system, band) work items (the segment
+// tables of the transform kernels) on the leader's stream, ordered against every member's
+// stream by events.  Each band is transformed by the same arithmetic as in a launch of its own,
+// so batched results equal unbatched ones bit for bit.
+struct XformOp {
+  eacg_system* s = nullptr;
+  int kind = 0;                 // 0: H application transforms, 1: density transforms
+  int plan = 0, xmode = 0, pprec = 0;
+  GridReq req{};
+  bool done = false;
+  eacg_status status = EACG_OK;
+};
+
+// process-wide counts of batched transform groups and of the system requests they covered
+std::atomic<long long> g_batch_groups{0}, g_batch_members{0};
+
+class Batcher {
+ public:
+  explicit Batcher(int window_us) : window_us_(window_us) {}
+  void enter() {
+    std::lock_guard<std::mutex> lk(mu_);
+    ++live_;
+  }
+  void leave() {
+    std::lock_guard<std::mutex> lk(mu_);
+    --live_;
+    cv_.notify_all();
+  }
+  int window_us() const { return window_us_; }
+  long long launches() const { return batched_launches_.load(); }
+
+  eacg_status submit(XformOp* op) {
+    std::unique_lock<std::mutex> lk(mu_);
+    pending_.push_back(op);
+    ++waiting_;
+    cv_.notify_all();
+    if (!leading_) {
+      leading_ = true;
+      const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(window_us_);
+      cv_.wait_until(lk, deadline, [&] { return waiting_ >= live_; });
+      std::vector<XformOp*> batch;
+      batch.swap(pending_);
+      leading_ = false;
+      lk.unlock();
+      execute(batch);
+      lk.lock();
+      waiting_ -= (int)batch.size();
+      for (XformOp* o : batch) o->done = true;
+      cv_.notify_all();
+    }
+    cv_.wait(lk, [&] { return op->done; });
+    return op->status;
+  }
+
+ private:
+  void execute(std::vector<XformOp*>& batch) {
+    std::vector<bool> used(batch.size(), false);
+    for (size_t i = 0; i < batch.size(); ++i) {
+      if (used[i]) continue;
+      std::vector<XformOp*> grp;
+      for (size_t j = i; j < batch.size(); ++j) {
+        XformOp* a = batch[i];
+        XformOp* b = batch[j];
+        if (!used[j] && a->kind == b->kind && a->s->N == b->s->N && a->plan == b->plan && a->xmode == b->xmode &&
+            a->pprec == b->pprec) {
+          used[j] = true;
+          grp.push_back(b);
+        }
+      }
+      launch_group(grp);
+    }
+  }
+
+  void launch_group(std::vector<XformOp*>& grp) {
+    cudaStream_t ls = grp[0]->s->st;
+    std::vector<GridReq> reqs;
+    std::vector<cudaEvent_t> evs;
+    cudaError_t err = cudaSuccess;
+    for (XformOp* o : grp) {
+      reqs.push_back(o->req);
+      if (o->s->st != ls) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+          err = cudaErrorUnknown;
+          break;
+        }
+        evs.push_back(e);
+        cudaEventRecord(e, o->s->st);
+        cudaStreamWaitEvent(ls, e, 0);
+      }
+    }
+    const int N = grp[0]->s->N, n = (int)reqs.size();
+    const XformOp& k0 = *grp[0];
+    if (err == cudaSuccess) {
+      grid_xpass_inv_multi(N, k0.plan, k0.xmode, reqs.data(), n, ls);
+      if (k0.kind == 0) {
+        grid_plane_h_multi(N, k0.plan, k0.pprec, reqs.data(), n, ls);
+        grid_xpass_fwd_multi(N, k0.plan, k0.xmode, reqs.data(), n, ls);
+      } else {
+        grid_plane_rho_multi(N, k0.plan, k0.pprec, reqs.data(), n, ls);
+      }
+      batched_launches_ += (k0.kind == 0 ? 3 : 2) * ((n + GRID_MAX_SEGS - 1) / GRID_MAX_SEGS);
+      g_batch_groups += 1;
+      g_batch_members += n;
+      err = cudaGetLastError();
+    }
+    cudaEvent_t done = nullptr;
+    if (err == cudaSuccess && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(done, ls);
+      for (XformOp* o : grp)
+        if (o->s->st != ls) cudaStreamWaitEvent(o->s->st, done, 0);
+      cudaEventDestroy(done);
+    } else if (err == cudaSuccess) {
+      err = cudaErrorUnknown;
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    for (XformOp* o : grp) {
+      if (err != cudaSuccess) {
+        o->status = EACG_ECUDA;
+        o->s->err = std::string("batched transform launch: ") + cudaGetErrorString(err);
+      }
+    }
+  }
+
+  std::mutex mu_;
+  std::condition_variable cv_;
+  int live_ = 0, waiting_ = 0;
+  bool leading_ = false;
+  std::vector<XformOp*> pending_;
+  int window_us_;
+  std::atomic<long long> batched_launches_{0};
+};
+
+// the batcher of the calling thread's step (set by eacg_step_many and by eacg_step when
+// batching is on), and the process-wide batcher of eacg_batching
+thread_local Batcher* tl_batch = nullptr;
+std::mutex g_batch_mu;
+Batcher* g_batch = nullptr;
+
+// The transforms of an H application (kind 0) or of a density (kind 1) of the bands of one
+// system through the batcher.
+static eacg_status batched_xform(eacg_system* s, int kind, int prec32_blocks, int prec, const void* in, void* out,
+                                 const double* kin, double scale, const void* v, const int* kactive) {
+  XformOp op;
+  op.s = s;
+  op.kind = kind;
+  op.plan = prec ? s->g.plan32 : s->g.plan64;
+  op.xmode = prec32_blocks ? 2 : prec ? 1 : (s->g.df64 ? 3 : 0);
+  op.pprec = prec ? 1 : (s->g.df64 ? 2 : 0);
+  GridReq& r = op.req;
+  r.g = &s->g;
+  r.in = in;
+  r.tbuf = s->d_tbuf;
+  r.out = out;
+  r.kin = kin;
+  r.scale = scale;
+  r.v = v;
+  r.kactive = kactive;
+  r.nbands = s->K * s->p;
+  r.bw = s->d_bw;
+  r.partial = s->d_partial;
+  r.groups = s->rho_groups;
+  return tl_batch->submit(&op);
+}
+
 // P = B32^* in32 (projector overlaps of complex64 blocks): on the tensor cores (3 x TF32) when
 // the shape allows it, else the SIMT FP32 block-overlap kernel.
 static void projector_overlaps32(eacg_system* s, const float2* in32, const int* kactive) {
@@ -638,13 +811,16 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
   const int off = prec ? P_F32 : 0;
   const double fx = nb * s->ncols * fft_flops(s->N);
   const double fp = nb * 2.0 * s->N * (s->ny + s->N) * fft_flops(s->N);
-  PROF_RUN(P_XINV + off, nb * (coef + inter), fx, nb,
-           grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st));
-  PROF_RUN(P_PLANE_H + off, nb * 2.0 * inter + N3 * (prec ? 4.0 : 8.0), fp, nb,
-           grid_plane_h(s->g, prec, s->d_tbuf, vpot(s, prec), nb, kactive,
-                        s->st));
-  PROF_RUN(P_XFWD + off, nb * (inter + 2.0 * coef), fx, nb,
-           grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
+  if (tl_batch) {
+    TRY(batched_xform(s, 0, 0, prec, in, out, s->d_kin, 1.0 / N3, vpot(s, prec), kactive));
+  } else {
+    PROF_RUN(P_XINV + off, nb * (coef + inter), fx, nb,
+             grid_xpass_inv(s->g, prec, in, s->d_tbuf, nb, kactive, s->st));
+    PROF_RUN(P_PLANE_H + off, nb * 2.0 * inter + N3 * (prec ? 4.0 : 8.0), fp, nb,
+             grid_plane_h(s->g, prec, s->d_tbuf, vpot(s, prec), nb, kactive, s->st));
+    PROF_RUN(P_XFWD + off, nb * (inter + 2.0 * coef), fx, nb,
+             grid_xpass_fwd(s->g, prec, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
+  }
   CKL(s);
   if (s->nproj > 0 && prec == 0) {
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
@@ -689,13 +865,18 @@ static eacg_status density_only(eacg_system* s, const double2* phi, int prec) {
   const double tv = prec ? 8.0 : 16.0;
   const double inter = (double)s->N * s->ncols * tv;
   const int off = prec ? P_F32 : 0;
-  PROF_RUN(P_XINV_RHO + off, nb * ((double)s->n_max * 16.0 + inter), nb * s->ncols * fft_flops(s->N), nb,
-           grid_xpass_inv(s->g, prec, phi, s->d_tbuf, nb, nullptr, s->st));
-  PROF_RUN(P_PLANE_RHO + off, nb * inter + (double)s->rho_groups * N3 * 8.0,
-           nb * (double)s->N * (s->ny + s->N) * fft_flops(s->N), nb, {
-    grid_plane_rho(s->g, prec, s->d_tbuf, nb, s->rho_groups, s->d_bw, s->d_partial, s->st);
+  if (tl_batch) {
+    TRY(batched_xform(s, 1, 0, prec, phi, nullptr, nullptr, 1.0, nullptr, nullptr));
     grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
-  });
+  } else {
+    PROF_RUN(P_XINV_RHO + off, nb * ((double)s->n_max * 16.0 + inter), nb * s->ncols * fft_flops(s->N), nb,
+             grid_xpass_inv(s->g, prec, phi, s->d_tbuf, nb, nullptr, s->st));
+    PROF_RUN(P_PLANE_RHO + off, nb * inter + (double)s->rho_groups * N3 * 8.0,
+             nb * (double)s->N * (s->ny + s->N) * fft_flops(s->N), nb, {
+      grid_plane_rho(s->g, prec, s->d_tbuf, nb, s->rho_groups, s->d_bw, s->d_partial, s->st);
+      grid_reduce_groups(s->d_partial, s->rho_groups, N3, s->d_rho, s->st);
+    });
+  }
   CKL(s);
   return EACG_OK;
 }
@@ -902,12 +1083,16 @@ static eacg_status apply_H_block32(eacg_system* s, const float2* in, float2* out
   const double N3 = (double)s->N * s->N * s->N;
   const double fx = nb * s->ncols * fft_flops(s->N);
   const double fp = nb * 2.0 * s->N * (s->ny + s->N) * fft_flops(s->N);
-  PROF_RUN(P_XINV + P_F32, nb * (coef + inter), fx, nb,
-           grid_xpass_inv32(s->g, in, s->d_tbuf, nb, kactive, s->st));
-  PROF_RUN(P_PLANE_H + P_F32, nb * 2.0 * inter + N3 * 4.0, fp, nb,
-           grid_plane_h(s->g, 1, s->d_tbuf, s->d_vtot32, nb, kactive, s->st));
-  PROF_RUN(P_XFWD + P_F32, nb * (inter + 2.0 * coef), fx, nb,
-           grid_xpass_fwd32(s->g, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
+  if (tl_batch) {
+    TRY(batched_xform(s, 0, 1, 1, in, out, s->d_kin, 1.0 / N3, s->d_vtot32, kactive));
+  } else {
+    PROF_RUN(P_XINV + P_F32, nb * (coef + inter), fx, nb,
+             grid_xpass_inv32(s->g, in, s->d_tbuf, nb, kactive, s->st));
+    PROF_RUN(P_PLANE_H + P_F32, nb * 2.0 * inter + N3 * 4.0, fp, nb,
+             grid_plane_h(s->g, 1, s->d_tbuf, s->d_vtot32, nb, kactive, s->st));
+    PROF_RUN(P_XFWD + P_F32, nb * (inter + 2.0 * coef), fx, nb,
+             grid_xpass_fwd32(s->g, s->d_tbuf, in, s->d_kin, 1.0 / N3, out, nb, kactive, s->st));
+  }
   CKL(s);
   if (s->nproj > 0) {
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
@@ -964,7 +1149,8 @@ static void hg_resolve(eacg_system* s, eacg_system::HGraph& g) {
 template <typename V>
 static eacg_status apply_H_fom(eacg_system* s, const V* in, V* out, const int* ka) {
   auto& g = s->hg[sizeof(V) == sizeof(float2) ? 1 : 0];
-  if (!s->prm.graphs || s->graphs_off) return apply_H_t(s, in, out, ka);
+  // batched steps launch the transforms together with other systems: no per-system graph
+  if (!s->prm.graphs || s->graphs_off || tl_batch) return apply_H_t(s, in, out, ka);
   const bool same = g.in == in && g.out == out && g.ka == ka && g.cnw == s->cn_work;
   if (!same) {
     hg_resolve(s, g);  // keep the last replay's profile records
@@ -2185,10 +2371,17 @@ extern "C" eacg_status eacg_backproject_c64(int K, int L, int m, int n, const fl
   return e == cudaSuccess ? EACG_OK : EACG_ECUDA;
 }
 
-extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {
-  SYS_CHECK(s);
-  DENSE_CHECK(s);
+// One step of one system, inside the batcher b when it is not null.
+static eacg_status step_in(eacg_system* s, eacg_step_info* info, Batcher* b) {
+  if (b) {
+    b->enter();
+    tl_batch = b;
+  }
   eacg_status st = do_step(s, info);
+  if (b) {
+    tl_batch = nullptr;
+    b->leave();
+  }
   if (st == EACG_OK) {
     cudaError_t e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) {
@@ -2197,6 +2390,63 @@ extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {
     }
   }
   return st;
+}
+
+extern "C" eacg_status eacg_step(eacg_system* s, eacg_step_info* info) {
+  SYS_CHECK(s);
+  DENSE_CHECK(s);
+  Batcher* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    b = g_batch;
+  }
+  return step_in(s, info, b);
+}
+
+extern "C" eacg_status eacg_step_many(eacg_system* const* sys, int nsys, eacg_step_info* infos, int* statuses,
+                                      int window_us) {
+  if (nsys < 0 || (nsys > 0 && !sys) || window_us < 0) return EACG_EINVAL;
+  for (int i = 0; i < nsys; ++i) {
+    if (!sys[i]) return EACG_EINVAL;
+    if (sys[i]->p > EACG_MAX_BANDS_DENSE) {
+      sys[i]->err = "this call needs the p x p dense kernels, which support at most 64 bands";
+      return EACG_EUNSUPPORTED;
+    }
+    for (int j = 0; j < i; ++j)
+      if (sys[j] == sys[i]) return EACG_EINVAL;  // a system steps once per call
+  }
+  Batcher b(window_us);
+  std::vector<eacg_status> st(nsys, EACG_OK);
+  std::vector<std::thread> th;
+  th.reserve(nsys);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < nsys; ++i)
+    th.emplace_back([&, i] {
+      cudaSetDevice(dev);  // the worker threads use the caller's device
+      st[i] = step_in(sys[i], infos ? infos + i : nullptr, &b);
+    });
+  for (auto& t : th) t.join();
+  eacg_status first = EACG_OK;
+  for (int i = 0; i < nsys; ++i) {
+    if (statuses) statuses[i] = st[i];
+    if (first == EACG_OK && st[i] != EACG_OK) first = st[i];
+  }
+  return first;
+}
+
+extern "C" eacg_status eacg_batch_counts(long long* groups, long long* members) {
+  if (groups) *groups = g_batch_groups.load();
+  if (members) *members = g_batch_members.load();
+  return EACG_OK;
+}
+
+extern "C" eacg_status eacg_batching(int window_us) {
+  if (window_us < -1) return EACG_EINVAL;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  // the old batcher may still be in use by steps in flight: it is kept until process exit
+  g_batch = window_us < 0 ? nullptr : new Batcher(window_us);
+  return EACG_OK;
 }
 
 extern "C" eacg_status eacg_solve(eacg_system* s, eacg_result* out) {
