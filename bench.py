@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--step-many", action="store_true",
                     help="one-workload solves: step the concurrent systems together with eacg_step_many "
                          "(batched transform launches) instead of one host thread per system")
+    ap.add_argument("--stream-len", type=int, default=256,
+                    help="serving: requests of the stream that the K steps cover (256; fewer only for short "
+                         "profiler runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed region (short runs under a profiler): no e2e, FP64 sample, Poisson "
                          "latency runs or CPU baseline")
@@ -116,9 +119,9 @@ def whole_job_rate(world, units_per_rank, ms):
     return world * units_per_rank / (ms / 1e3)
 
 
-def per_step(steps):
-    """Requests per step: the K steps cover the 256-request stream once."""
-    return int(math.ceil(STREAM / max(1, steps)))
+def per_step(steps, length=STREAM):
+    """Requests per step: the K steps cover the stream (256 requests) once."""
+    return int(math.ceil(length / max(1, steps)))
 
 
 def stream_ids(start, count):
@@ -144,7 +147,8 @@ def metric_name(args, cfg=None):
 def config_of(args, cfg, world):
     """The workload description, shared by this arm and the reference arm."""
     if args.workload == "serving_stream":
-        return {"workload": f"serving_stream_{STREAM}", "requests_per_step": per_step(args.steps),
+        return {"workload": f"serving_stream_{STREAM}" if args.stream_len == STREAM else
+                f"serving_stream_first_{args.stream_len}", "requests_per_step": per_step(args.steps, args.stream_len),
                 "requests": "synth.config_serving_request(i), i < 256: a 6-14, 1-16 atoms, Z 1-4, Ecut 8-20, "
                             "1/8/27 k, N 20-64, p 1-23",
                 "arrivals": "all queued at t=0 (saturating load)", "precision": args.precision,
@@ -194,7 +198,10 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+        import resource
+        self.ru0 = resource.getrusage(resource.RUSAGE_SELF)
+        self.t0 = time.perf_counter()
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
@@ -212,7 +219,7 @@ class Clocks:
         self.f.flush()
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, util = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
@@ -221,8 +228,16 @@ class Clocks:
                 for n, v in zip(names, r[5:9]):
                     if v.strip().lower() == "active":
                         reasons.add(n)
+                util.append(float(r[9]))
             except (ValueError, IndexError):
                 continue
+        import resource
+        ru = resource.getrusage(resource.RUSAGE_SELF)
+        wall = time.perf_counter() - self.t0
+        cpu = (ru.ru_utime - self.ru0.ru_utime) + (ru.ru_stime - self.ru0.ru_stime)
+        # kernel-active share of the samples and the host cores kept busy (context for the number)
+        self.busy = {"gpu_util_pct_median": statistics.median(util) if util else None,
+                     "host_cores_busy": round(cpu / wall, 2) if wall > 0 else None}
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
 
@@ -513,7 +528,7 @@ def run_serving(args):
     dev = torch.device("cuda", local)
     prec = 1 if args.precision == "mixed" else 0
     E.eacg_batching(args.batch_window)
-    M = per_step(args.steps)
+    M = per_step(args.steps, args.stream_len)
     timed = stream_ids(0, args.steps * M)
     warm = stream_ids(0, args.warmup * M)
     sample = fp64_sample_ids()
@@ -536,6 +551,7 @@ def run_serving(args):
         dist.barrier()
     launches = E.eacg_launch_count() - launches0
     clk = clocks.stop()
+    log["busy"] = getattr(clocks, "busy", None)
     conv = sum(1 for o in outs if o.converged)
     total_ms = max_over_ranks(ms, world, dev)
     value = whole_job_rate(world, conv, total_ms)
@@ -552,7 +568,7 @@ def run_serving(args):
         "converged": conv, "requests": len(outs), "failed": failed[:4],
         "latency_s": {"saturated": {"solve_p50": r4(st["solve_p50_s"]), "solve_p99": r4(st["solve_p99_s"])}},
         "hpsi_gbs": r4(hpsi_bytes / (ms / 1e3) / 1e9),
-        "gpu_launches": launches, "clocks": clk,
+        "gpu_launches": launches, "clocks": clk, "busy": log["busy"],
     }
     acc = accuracy_vs_oracle(outs, timed)
     if acc:
