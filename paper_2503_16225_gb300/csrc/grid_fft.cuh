@@ -121,9 +121,14 @@ __device__ __forceinline__ void plane_setup(V* tw, int* rows, int* yl, int* cm, 
 // Plane buffers: B = the plane [jy][jz] (pitch N + 1) and, where two planes fit in shared
 // memory, A = step-1 scratch (ping-pong: one barrier per step).  Otherwise the step-1
 // values stay in B in place and the phases that store into B add a barrier.
+// Double-float transforms are latency-bound (long dependent chains of error-free operations):
+// they keep two planes only where four CTAs still fit an SM (N <= 41), and otherwise work in
+// place with twice the CTAs per SM.
 template <typename T, int N>
 struct PlaneCfg {
-  static constexpr bool pingpong = 2 * sizeof(cplx<T>) * N * (N + 1) <= 200 * 1024;
+  static constexpr bool pingpong = std::is_same<T, dfloat>::value
+                                       ? 2 * sizeof(cplx<T>) * N * (N + 1) <= 56 * 1024
+                                       : 2 * sizeof(cplx<T>) * N * (N + 1) <= 200 * 1024;
   static size_t smem_bytes(int ny) {
     return (pingpong ? 2 : 1) * sizeof(cplx<T>) * (size_t)N * (N + 1) + sizeof(int) * (size_t)ny * (N + 1);
   }
