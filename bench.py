@@ -57,6 +57,7 @@ SINGLE_KERNEL_SLOTS = ("plane_h", "plane_rho", "xpass_inv", "xpass_fwd", "xpass_
 # profile slots of the H application and density (algorithmic H-psi bytes)
 HPSI_SLOTS = ("xpass_inv", "plane_h", "xpass_fwd", "nonlocal", "xpass_rho", "plane_rho", "nonlocal_eval")
 GOLDEN_SERVING = os.path.join(ROOT, "tests", "golden", "oracle_serving.json")
+SERVE_PARAMS: dict = {}   # eacg_params overrides of the served requests (set from the flags)
 
 
 def parse():
@@ -87,6 +88,9 @@ def parse():
     ap.add_argument("--step-many", action="store_true",
                     help="one-workload solves: step the concurrent systems together with eacg_step_many "
                          "(batched transform launches) instead of one host thread per system")
+    ap.add_argument("--switch-res", type=float, default=None,
+                    help="mixed precision: residual below which the evaluations switch to FP64-accurate "
+                         "transforms (library default if not given)")
     ap.add_argument("--stream-len", type=int, default=256,
                     help="serving: requests of the stream that the K steps cover (256; fewer only for short "
                          "profiler runs)")
@@ -454,7 +458,7 @@ def serve_run(inputs, ids, precision, resident, profile=False, host=False, arriv
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     free, _ = torch.cuda.mem_get_info()
     srv = serve.Server(hbm_budget=int(0.8 * free), max_resident=resident, precision=precision,
-                       start_event=start, profile=profile, host_buffers=host)
+                       start_event=start, profile=profile, host_buffers=host, params=SERVE_PARAMS)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     start.record(main)
@@ -477,7 +481,8 @@ def one_at_a_time(inputs, ids, precision, profile=False):
     for i in ids:
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
-            s = E.System(inputs.cfg[i], E.eacg_default_params(precision=precision), stream=st.cuda_stream)
+            s = E.System(inputs.cfg[i], E.eacg_default_params(precision=precision, **SERVE_PARAMS),
+                     stream=st.cuda_stream)
             if profile:
                 E.eacg_profile_enable(s.h, 1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -528,6 +533,8 @@ def run_serving(args):
     dev = torch.device("cuda", local)
     prec = 1 if args.precision == "mixed" else 0
     E.eacg_batching(args.batch_window)
+    if args.switch_res is not None:
+        SERVE_PARAMS["switch_res"] = args.switch_res
     M = per_step(args.steps, args.stream_len)
     timed = stream_ids(0, args.steps * M)
     warm = stream_ids(0, args.warmup * M)

@@ -56,11 +56,13 @@ class Server:
 
     def __init__(self, hbm_budget: int, max_resident: int = 8, precision: int = 1, keep_psi: bool = False,
                  device: int = 0, use_cuda: bool = True, start_event=None, profile: bool = False,
-                 host_buffers: bool = False):
+                 host_buffers: bool = False, params: dict | None = None):
         """start_event: a CUDA event every request stream waits on before its first call (device
         timing from one event); profile: live kernel timing of every system, summed into
         self.profile; host_buffers: requests carry pinned host input and output tensors and are
-        solved through eacg_solve_host (copies inside the request)."""
+        solved through eacg_solve_host (copies inside the request); params: eacg_params fields
+        that replace the defaults for every request."""
+        self.params = dict(params or {})
         self.use_cuda = use_cuda
         self.budget = int(hbm_budget)
         self.max_resident = int(max_resident)
@@ -98,7 +100,7 @@ class Server:
             with ctx:
                 if self.start_event is not None and stream is not None:
                     stream.wait_event(self.start_event)
-                prm = eacg_default_params(precision=self.precision, max_outer=req.max_outer)
+                prm = eacg_default_params(precision=self.precision, max_outer=req.max_outer, **self.params)
                 s = System(req.cfg, prm, stream=handle)
                 if self.profile_on:
                     eacg_profile_enable(s.h, 1)
