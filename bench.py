@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--switch-res", type=float, default=None,
                     help="mixed precision: residual below which the evaluations switch to FP64-accurate "
                          "transforms (library default if not given)")
+    ap.add_argument("--stream-start", type=int, default=0,
+                    help="serving: first request of the timed stream (0; another value only for short profiler runs)")
     ap.add_argument("--stream-len", type=int, default=256,
                     help="serving: requests of the stream that the K steps cover (256; fewer only for short "
                          "profiler runs)")
@@ -152,7 +154,8 @@ def config_of(args, cfg, world):
     """The workload description, shared by this arm and the reference arm."""
     if args.workload == "serving_stream":
         return {"workload": f"serving_stream_{STREAM}" if args.stream_len == STREAM else
-                f"serving_stream_first_{args.stream_len}", "requests_per_step": per_step(args.steps, args.stream_len),
+                f"serving_stream_requests_{args.stream_start}_to_{args.stream_start + args.stream_len - 1}",
+                "requests_per_step": per_step(args.steps, args.stream_len),
                 "requests": "synth.config_serving_request(i), i < 256: a 6-14, 1-16 atoms, Z 1-4, Ecut 8-20, "
                             "1/8/27 k, N 20-64, p 1-23",
                 "arrivals": "all queued at t=0 (saturating load)", "precision": args.precision,
@@ -536,7 +539,7 @@ def run_serving(args):
     if args.switch_res is not None:
         SERVE_PARAMS["switch_res"] = args.switch_res
     M = per_step(args.steps, args.stream_len)
-    timed = stream_ids(0, args.steps * M)
+    timed = stream_ids(args.stream_start, args.steps * M)
     warm = stream_ids(0, args.warmup * M)
     sample = fp64_sample_ids()
     inputs = StreamInputs(timed + warm + sample, dev)
