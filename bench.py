@@ -50,8 +50,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of single-kernel
 # slots, from the ncu captures summarised in profiles/ (diamond 4x4x4 workload, 1024 bands per
-# launch); a kernel changed since its capture must be removed from this table.
-NCU_TRAFFIC_BYTES = {"plane_h_f64": 393.6e6, "plane_h_f32": 170.0e6}
+# launch); a kernel changed since its capture must be removed from this table.  The FP64-accurate
+# slots (_f64) run in double-float arithmetic by default.
+NCU_TRAFFIC_BYTES = {"plane_h_f64": 395.6e6, "plane_rho_f64": 240.2e6, "plane_h_f32": 170.0e6}
+# FP32 instructions (FADD + FMUL + FFMA, thread level) per algorithmic FLOP (5 N log2 N per line)
+# of the double-float kernels, from the same captures: their roofline is the FP32 pipe's
+# instruction rate (152 SMs x 128 lanes x clock) divided by this ratio.
+NCU_DF_INSTR_PER_FLOP = {"plane_h_f64": 11.54, "plane_rho_f64": 12.99}
+FP32_INSTR_PEAK = 152 * 128 * 2.07e9
 # profile slots that time exactly one kernel (the roofline is reported for the top one)
 SINGLE_KERNEL_SLOTS = ("plane_h", "plane_rho", "xpass_inv", "xpass_fwd", "xpass_rho", "fom_solve")
 # profile slots of the H application and density (algorithmic H-psi bytes)
@@ -263,7 +269,7 @@ def profile_summary(prof, total_ms=None):
     return out
 
 
-def roofline_of(prof, traffic_table=None):
+def roofline_of(prof, traffic_table=None, df=True):
     """Roofline of the single-kernel profile slot with the largest summed time: achieved
     algorithmic FLOP/s per launch against the derived FP64 / FP32 ALU peak."""
     single = {k: v for k, v in (prof or {}).items()
@@ -275,7 +281,12 @@ def roofline_of(prof, traffic_table=None):
     n = st["launches"]
     avg_ms = st["ms"] / n
     achieved = (st["flops"] / n) / (avg_ms / 1e3) / 1e12
-    if top.endswith("_f64"):
+    if top.endswith("_f64") and df and top in NCU_DF_INSTR_PER_FLOP:
+        ratio = NCU_DF_INSTR_PER_FLOP[top]
+        peak = FP32_INSTR_PEAK / ratio / 1e12
+        pk = (f"double-float on the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz FP32 instructions / {ratio} "
+              f"instructions per FLOP (ncu)")
+    elif top.endswith("_f64"):
         peak, pk = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz"
     else:
         peak, pk = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
@@ -542,7 +553,7 @@ def run_serving(args):
     timed = stream_ids(args.stream_start, args.steps * M)
     warm = stream_ids(0, args.warmup * M)
     sample = fp64_sample_ids()
-    inputs = StreamInputs(timed + warm + sample, dev)
+    inputs = StreamInputs(timed + warm + ([] if args.no_extras else sample), dev)
     log = {}
 
     # ---- warm-up: W steps of the stream (set-up caches: FFT plans, GEMM tiles per shape)
