@@ -1032,17 +1032,18 @@ __device__ __forceinline__ V warp_sum(V v) {
   return v;
 }
 
-// Sum over the CTA of one value per thread in a fixed order; every thread gets the result.
+// Sum over the CTA of one value per thread in a fixed order (a shuffle tree per warp, then one
+// over the warp sums); every thread gets the result.
 template <typename V>
 __device__ __forceinline__ V block_sum(V v, V* red) {
   v = warp_sum(v);
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) red[w] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    V t = red[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = t + red[i];
-    red[32] = t;
+  if (w == 0) {
+    V t = threadIdx.x < nw ? red[threadIdx.x] : V{};
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[32] = t;
   }
   __syncthreads();
   const V r = red[32];
@@ -1122,19 +1123,15 @@ __global__ void __launch_bounds__(HS_THREADS)
     }
     __syncthreads();
     if (t.x == (T)0 && t.y == (T)0) continue;
-    // x = A22 v: the lower part by rows (thread per row), the upper part by columns (warp per column)
-    for (int i = j + 1 + tid; i < q; i += blockDim.x) {
-      V acc = zero;
-      for (int l = j + 1; l <= i; ++l) acc = acc + cmul(P[poff(l, q) + (i - l)], vv[l]);
-      xv[i] = acc;
-    }
-    __syncthreads();
+    // x = tau A22 v, warp per row i: the lower part A_il (l <= i) along row i of the packed
+    // columns, the upper part conj(A_li) (l > i) down column i, lanes striding over l
     for (int i = j + 1 + warp; i < q; i += nw) {
       const size_t ci = poff(i, q) - i;
       V acc = zero;
+      for (int l = j + 1 + lane; l <= i; l += 32) acc = acc + cmul(P[poff(l, q) + (i - l)], vv[l]);
       for (int l = i + 1 + lane; l < q; l += 32) acc = acc + cmulc(P[ci + l], vv[l]);
       acc = warp_sum(acc);
-      if (lane == 0) xv[i] = cmul(t, xv[i] + acc);  // x = tau A22 v
+      if (lane == 0) xv[i] = cmul(t, acc);
     }
     __syncthreads();
     V dp = zero;
