@@ -99,13 +99,20 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
 }
+// double-float complex multiply-adds (FP64-accurate products and sums on the FP32 pipe)
+__device__ __forceinline__ dcomplex cfma(dcomplex a, dcomplex b, dcomplex c) {  // c + a * b
+  return {c.x + (a.x * b.x - a.y * b.y), c.y + (a.x * b.y + a.y * b.x)};
+}
+__device__ __forceinline__ dcomplex cfmac(dcomplex a, dcomplex b, dcomplex c) {  // c + conj(a) * b
+  return {c.x + (a.x * b.x + a.y * b.y), c.y + (a.x * b.y - a.y * b.x)};
+}
 
-template <typename T, int CN_GROUPS>
+template <typename T, typename TM, int CN_GROUPS>
 __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
     k_gemm_cn_partial(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
                       const cplx<T>* __restrict__ B, size_t sB, int ldb, double2* __restrict__ part,
                       const int* __restrict__ kactive, int chunk) {
-  using V = cplx<T>;
+  using V = cplx<TM>;  // arithmetic type (the storage type T, or double-float for FP64 storage)
   constexpr int PER = CN_LANES / CN_GROUPS;  // lanes per group
   constexpr int NT = CN_TILE * CN_TILE * CN_GROUPS;
   const int k = blockIdx.z;
@@ -118,11 +125,9 @@ __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
   const int i0 = tm * CN_TILE, j0 = tn * CN_TILE;
   __shared__ V sa[CN_LANES][CN_SUB][CN_TILE + 1];
   __shared__ V sb[CN_LANES][CN_SUB][CN_TILE + 1];
-  const V* Ak = A + k * sA;
-  const V* Bk = B + k * sB;
-  V zero;
-  zero.x = 0;
-  zero.y = 0;
+  const cplx<T>* Ak = A + k * sA;
+  const cplx<T>* Bk = B + k * sB;
+  const V zero = czero<V>();
   V acc[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) acc[i] = zero;
@@ -132,8 +137,8 @@ __global__ void __launch_bounds__(CN_TILE * CN_TILE * CN_GROUPS)
       const int v = e / (CN_SUB * CN_TILE), w = e - v * (CN_SUB * CN_TILE);
       const int c = w / CN_SUB, r = w - c * CN_SUB;
       const int l = s0 + v * CN_SUB + r;
-      sa[v][r][c] = (l < l_end && i0 + c < m) ? Ak[(size_t)(i0 + c) * lda + l] : zero;
-      sb[v][r][c] = (l < l_end && j0 + c < n) ? Bk[(size_t)(j0 + c) * ldb + l] : zero;
+      sa[v][r][c] = (l < l_end && i0 + c < m) ? cvt<V>(Ak[(size_t)(i0 + c) * lda + l]) : zero;
+      sb[v][r][c] = (l < l_end && j0 + c < n) ? cvt<V>(Bk[(size_t)(j0 + c) * ldb + l]) : zero;
     }
     __syncthreads();
 #pragma unroll
@@ -194,18 +199,19 @@ int cn_groups_for(size_t es, int m, int n, int L) {
 }
 }  // namespace
 
-template <typename T>
+template <typename T, typename TM>
 static void gemm_cn_partial_launch(int G, dim3 g1, int L, int m, int n, const cplx<T>* A, size_t sA, int lda,
                                    const cplx<T>* B, size_t sB, int ldb, double2* work, const int* kactive,
                                    int chunk, cudaStream_t st) {
   if (G == 1)
-    k_gemm_cn_partial<T, 1><<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive, chunk);
+    k_gemm_cn_partial<T, TM, 1><<<g1, CN_TILE * CN_TILE, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive,
+                                                                   chunk);
   else if (G == 2)
-    k_gemm_cn_partial<T, 2><<<g1, CN_TILE * CN_TILE * 2, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive,
-                                                                  chunk);
+    k_gemm_cn_partial<T, TM, 2><<<g1, CN_TILE * CN_TILE * 2, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work,
+                                                                       kactive, chunk);
   else
-    k_gemm_cn_partial<T, 4><<<g1, CN_TILE * CN_TILE * 4, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work, kactive,
-                                                                  chunk);
+    k_gemm_cn_partial<T, TM, 4><<<g1, CN_TILE * CN_TILE * 4, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, work,
+                                                                       kactive, chunk);
   count_launch();
 }
 
@@ -217,7 +223,7 @@ void dense_cn_reduce(int K, int m, int n, int nch, const double2* work, double2*
   count_launch();
 }
 
-template <typename T>
+template <typename T, typename TM = T>
 static void gemm_cn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const cplx<T>* B, size_t sB,
                       int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
                       const int* kactive, cudaStream_t st, int G = 0) {
@@ -227,8 +233,8 @@ static void gemm_cn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, i
   const int tiles = ((m + CN_TILE - 1) / CN_TILE) * ((n + CN_TILE - 1) / CN_TILE);
   dim3 g1(tiles, nch > 0 ? nch : 1, K);
   if (nch > 0)
-    gemm_cn_partial_launch<T>(G > 0 ? G : cn_groups_for(sizeof(cplx<T>), m, n, L), g1, L, m, n, A, sA, lda, B, sB,
-                              ldb, work, kactive, chunk, st);
+    gemm_cn_partial_launch<T, TM>(G > 0 ? G : cn_groups_for(sizeof(cplx<T>), m, n, L), g1, L, m, n, A, sA, lda, B,
+                                  sB, ldb, work, kactive, chunk, st);
   dim3 g2((m * n + 255) / 256, K);
   k_gemm_cn_reduce<<<g2, 256, 0, st>>>(m, n, nch, work, C, sC, ldc, alpha, beta, kactive);
   count_launch();
@@ -292,8 +298,11 @@ int dense_cn_force(int groups) {
 
 void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
-                   const int* kactive, cudaStream_t st) {
-  gemm_cn_t<double>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, work, kactive, st);
+                   const int* kactive, cudaStream_t st, int df) {
+  if (df)
+    gemm_cn_t<double, dfloat>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, work, kactive, st);
+  else
+    gemm_cn_t<double>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, work, kactive, st);
 }
 void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const float2* B, size_t sB,
                      int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
@@ -307,11 +316,11 @@ void dense_gemm_cn32(int K, int L, int m, int n, const float2* A, size_t sA, int
 // for FP32 operands added into an FP64 block).
 constexpr int NN_COLS = 8;
 constexpr int NN_ROWS = 64;
-template <typename T, typename VC>
+template <typename T, typename TM, typename VC>
 __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, size_t sA, int lda,
                           const double2* __restrict__ B, size_t sB, int ldb, VC* __restrict__ C, size_t sC,
                           int ldc, double2 alpha, double2 beta, const int* __restrict__ kactive) {
-  using V = cplx<T>;
+  using V = cplx<TM>;  // arithmetic type (the storage type T, or double-float for FP64 storage)
   using TC = decltype(C[0].x);
   const int k = blockIdx.y;
   if (kactive && !kactive[k]) return;
@@ -322,14 +331,12 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
   const int rb = blockIdx.x % rowblocks, gi = blockIdx.x / rowblocks;
   const int ngroups = gridDim.x / rowblocks;
   const int l = rb * blockDim.x + threadIdx.x;
-  const V* Ak = A + k * sA;
+  const cplx<T>* Ak = A + k * sA;
   const double2* Bk = B + k * sB;
   VC* Ck = C + k * sC;
   const bool bz = (beta.x == 0.0 && beta.y == 0.0);
   const VC al = to_c<TC>(alpha), be = to_c<TC>(beta);
-  V zero;
-  zero.x = 0;
-  zero.y = 0;
+  const V zero = czero<V>();
   for (int j0 = NN_COLS * gi; j0 < n; j0 += NN_COLS * ngroups) {
     V acc[NN_COLS];
 #pragma unroll
@@ -338,13 +345,13 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
       __syncthreads();
       for (int e = threadIdx.x; e < NN_ROWS * NN_COLS; e += blockDim.x) {
         const int r = e / NN_COLS, c = e - r * NN_COLS;
-        sb[r][c] = (i0 + r < m && j0 + c < n) ? to_c<T>(Bk[(size_t)(j0 + c) * ldb + i0 + r]) : zero;
+        sb[r][c] = (i0 + r < m && j0 + c < n) ? cvt<V>(Bk[(size_t)(j0 + c) * ldb + i0 + r]) : zero;
       }
       __syncthreads();
       if (l < L) {
         const int iend = min(NN_ROWS, m - i0);
         for (int r = 0; r < iend; ++r) {
-          const V a = Ak[(size_t)(i0 + r) * lda + l];
+          const V a = cvt<V>(Ak[(size_t)(i0 + r) * lda + l]);
 #pragma unroll
           for (int jj = 0; jj < NN_COLS; ++jj) acc[jj] = cfma(a, sb[r][jj], acc[jj]);
         }
@@ -364,7 +371,7 @@ __global__ void k_gemm_nn(int L, int m, int n, const cplx<T>* __restrict__ A, si
   }
 }
 
-template <typename T, typename VC>
+template <typename T, typename VC, typename TM = T>
 static void gemm_nn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, int lda, const double2* B, size_t sB,
                       int ldb, VC* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
                       cudaStream_t st) {
@@ -376,14 +383,17 @@ static void gemm_nn_t(int K, int L, int m, int n, const cplx<T>* A, size_t sA, i
   const int want = (GEMM_TARGET_CTAS + rowblocks * K - 1) / (rowblocks * K);
   const int groups = std::max(1, std::min(colgroups, want));
   dim3 g(rowblocks * groups, K);
-  k_gemm_nn<T, VC><<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
+  k_gemm_nn<T, TM, VC><<<g, 128, 0, st>>>(L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive);
   count_launch();
 }
 
 void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
-                   cudaStream_t st) {
-  gemm_nn_t<double>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
+                   cudaStream_t st, int df) {
+  if (df)
+    gemm_nn_t<double, double2, dfloat>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
+  else
+    gemm_nn_t<double, double2>(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, alpha, beta, kactive, st);
 }
 void dense_gemm_nn32(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* B, size_t sB,
                      int ldb, float2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,

@@ -826,11 +826,11 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
     const int K = s->K, p = s->p, np = s->nproj, nm = s->n_max;
     PROF_RUN(P_NONLOCAL, (double)K * np * nm * 16.0 * 2 + 3.0 * nb * coef, 16.0 * K * np * nm * p, nb, {
       dense_gemm_cn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, in, (size_t)p * nm, nm, s->d_P, (size_t)np * p, np,
-                    ONE, ZERO, s->cn_work, kactive, s->st);
+                    ONE, ZERO, s->cn_work, kactive, s->st, s->g.df64);
       dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
       dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
       dense_gemm_nn(K, nm, np, p, s->d_B, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np, out, (size_t)p * nm, nm,
-                    ONE, ONE, kactive, s->st);
+                    ONE, ONE, kactive, s->st, s->g.df64);
     });
     CKL(s);
   } else if (s->nproj > 0) {
@@ -946,12 +946,12 @@ static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, d
   TRY(apply_H_block(s, phi, hphi, prec, nullptr));
   // Lambda = herm(Phi^* H Phi)
   dense_gemm_cn(K, nm, p, p, phi, (size_t)p * nm, nm, hphi, (size_t)p * nm, nm, lam, (size_t)p * p, p, ONE, ZERO,
-                s->cn_work, nullptr, s->st);
+                s->cn_work, nullptr, s->st, s->g.df64);
   dense_herm(K, p, lam, s->st);
   // R = H Phi - Phi Lambda
   dense_copy(res, hphi, s->blk, s->st);
   dense_gemm_nn(K, nm, p, p, phi, (size_t)p * nm, nm, lam, (size_t)p * p, p, res, (size_t)p * nm, nm, MONE, ONE,
-                nullptr, s->st);
+                nullptr, s->st, s->g.df64);
   CKL(s);
   if (s->frozen) {
     // band energy of the fixed Hamiltonian: f <Phi, H Phi> in the weighted pairing
@@ -1005,11 +1005,11 @@ static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, d
 static eacg_status polar(eacg_system* s, const double2* psi, double2* out, double* ev, double2* evv, double2* sinv) {
   const int K = s->K, p = s->p, nm = s->n_max;
   dense_gemm_cn(K, nm, p, p, psi, (size_t)p * nm, nm, psi, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, ONE, ZERO,
-                s->cn_work, nullptr, s->st);
+                s->cn_work, nullptr, s->st, s->g.df64);
   dense_heig(K, p, s->sm1, (size_t)p * p, ev, evv, nullptr, s->st);
   dense_eig_func(K, p, evv, ev, -0.5, 0.0, sinv, nullptr, s->st);
   dense_gemm_nn(K, nm, p, p, psi, (size_t)p * nm, nm, sinv, (size_t)p * p, p, out, (size_t)p * nm, nm, ONE, ZERO,
-                nullptr, s->st);
+                nullptr, s->st, s->g.df64);
   CKL(s);
   return EACG_OK;
 }
@@ -1021,11 +1021,11 @@ static eacg_status precond_gradient(eacg_system* s, const double2* phi, const do
   dense_kinetic_alpha(K, p, nm, s->d_kin, phi, s->alpha, s->st);
   dense_tpa(K, p, nm, s->d_kin, s->alpha, res, s->tmp1, true, s->st);
   dense_gemm_cn(K, nm, p, p, phi, (size_t)p * nm, nm, s->tmp1, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, ONE,
-                ZERO, s->cn_work, nullptr, s->st);
+                ZERO, s->cn_work, nullptr, s->st, s->g.df64);
   dense_herm(K, p, s->sm1, s->st);
   dense_copy(g, s->tmp1, s->blk, s->st);
   dense_gemm_nn(K, nm, p, p, phi, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, g, (size_t)p * nm, nm, MONE, ONE,
-                nullptr, s->st);
+                nullptr, s->st, s->g.df64);
   CKL(s);
   return EACG_OK;
 }
@@ -1039,12 +1039,13 @@ struct FomOps<double> {
   using V = double2;
   static constexpr double drop_tol = 1e-12;
   static void cn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const V* B, size_t sB, int ldb,
-                 double2* C, size_t sC, int ldc, double2 al, double2 be, double2* w, const int* ka, cudaStream_t st) {
-    dense_gemm_cn(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, w, ka, st);
+                 double2* C, size_t sC, int ldc, double2 al, double2 be, double2* w, const int* ka, cudaStream_t st,
+                 int df) {
+    dense_gemm_cn(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, w, ka, st, df);
   }
   static void nn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const double2* B, size_t sB, int ldb,
-                 V* C, size_t sC, int ldc, double2 al, double2 be, const int* ka, cudaStream_t st) {
-    dense_gemm_nn(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, ka, st);
+                 V* C, size_t sC, int ldc, double2 al, double2 be, const int* ka, cudaStream_t st, int df) {
+    dense_gemm_nn(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, ka, st, df);
   }
   static void axpby(size_t n, double2 a, const V* x, double2 b, const V* y, V* o, cudaStream_t st) {
     dense_axpby(n, a, x, b, y, o, st);
@@ -1059,11 +1060,12 @@ struct FomOps<float> {
   using V = float2;
   static constexpr double drop_tol = 1e-6;
   static void cn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const V* B, size_t sB, int ldb,
-                 double2* C, size_t sC, int ldc, double2 al, double2 be, double2* w, const int* ka, cudaStream_t st) {
+                 double2* C, size_t sC, int ldc, double2 al, double2 be, double2* w, const int* ka, cudaStream_t st,
+                 int) {
     dense_gemm_cn32(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, w, ka, st);
   }
   static void nn(int K, int L, int m, int n, const V* A, size_t sA, int lda, const double2* B, size_t sB, int ldb,
-                 V* C, size_t sC, int ldc, double2 al, double2 be, const int* ka, cudaStream_t st) {
+                 V* C, size_t sC, int ldc, double2 al, double2 be, const int* ka, cudaStream_t st, int) {
     dense_gemm_nn32(K, L, m, n, A, sA, lda, B, sB, ldb, C, sC, ldc, al, be, ka, st);
   }
   static void axpby(size_t n, double2 a, const V* x, double2 b, const V* y, V* o, cudaStream_t st) {
@@ -1220,24 +1222,24 @@ static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, 
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
   // reference: largest squared column norm before projection
-  O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
+  O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st, s->g.df64);
   small_max_diag(K, p, s->sm1, s->lref, s->st);
   if (q > 0) {
     for (int pass = 0; pass < 2; ++pass) {
       O::cn(K, nm, q, p, V, sV, nm, R, sb, nm, s->fYt, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work, kactive,
-            s->st);
-      O::nn(K, nm, q, p, V, sV, nm, s->fYt, (size_t)s->qcap * p, s->qcap, R, sb, nm, MONE, ONE, kactive, s->st);
+            s->st, s->g.df64);
+      O::nn(K, nm, q, p, V, sV, nm, s->fYt, (size_t)s->qcap * p, s->qcap, R, sb, nm, MONE, ONE, kactive, s->st, s->g.df64);
     }
   }
   // first (rank-revealing) pass
-  O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st);
+  O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st, s->g.df64);
   small_pivchol(K, p, s->sm1, s->lref, O::drop_tol, s->sm3, s->d_nzero, kactive, s->st);
-  O::nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, scratch, sb, nm, ONE, ZERO, kactive, s->st);
+  O::nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, scratch, sb, nm, ONE, ZERO, kactive, s->st, s->g.df64);
   // second pass on the kept block (reference: its own largest column norm)
   O::cn(K, nm, p, p, scratch, sb, nm, scratch, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive,
-        s->st);
+        s->st, s->g.df64);
   small_pivchol(K, p, s->sm1, nullptr, O::drop_tol, s->sm3, s->d_info, kactive, s->st);
-  O::nn(K, nm, p, p, scratch, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st);
+  O::nn(K, nm, p, p, scratch, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st, s->g.df64);
   CKL(s);
   return EACG_OK;
 }
@@ -1275,7 +1277,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
   dense_kinetic_alpha(K, p, nm, s->d_kin, phi, s->alpha, s->st);
   // C = Phi - (H X0 - X0 Sigma), X0 = Phi / mu, H X0 = H Phi / mu  (FP64, then in T)
   dense_copy(s->Cb, hphi, s->blk, s->st);
-  dense_gemm_nn(K, nm, p, p, phi, sb, nm, s->sig, (size_t)p * p, p, s->Cb, sb, nm, MONE, ONE, nullptr, s->st);
+  dense_gemm_nn(K, nm, p, p, phi, sb, nm, s->sig, (size_t)p * p, p, s->Cb, sb, nm, MONE, ONE, nullptr, s->st, s->g.df64);
   dense_axpby(s->blk, ONE, phi, cr(-1.0 / mu), s->Cb, s->Cb, s->st);
   dense_norms2(K, sb, s->Cb, s->d_out + 64, s->st);
   V* C = reinterpret_cast<V*>(s->Cb);
@@ -1321,14 +1323,14 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     V* Wn = reinterpret_cast<V*>(s->fW) + (size_t)q0 * nm;
     if (q0 > 0) {
       O::cn(K, nm, q0, p, fV, sV, nm, Wn, sV, nm, s->fA + (size_t)q0 * s->qcap, sA, s->qcap, ONE, ZERO, s->cn_work,
-            s->d_kactive, s->st);
+            s->d_kactive, s->st, s->g.df64);
       fom_mirror(K, q0, p, s->fA, s->qcap, sA, s->d_kactive, s->st);
     }
-    O::cn(K, nm, p, p, Vn, sV, nm, Wn, sV, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, s->d_kactive, s->st);
+    O::cn(K, nm, p, p, Vn, sV, nm, Wn, sV, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, s->d_kactive, s->st, s->g.df64);
     small_put_herm_block(K, p, s->sm1, s->fA, s->qcap, sA, q0, s->st);
     fom_pad_diag(K, q0, p, s->fA, s->qcap, sA, s->d_nzero, s->eval, s->st);
     O::cn(K, nm, p, p, Vn, sV, nm, C, sb, nm, s->fC + q0, (size_t)s->qcap * p, s->qcap, ONE, ZERO, s->cn_work,
-          s->d_kactive, s->st);
+          s->d_kactive, s->st, s->g.df64);
     CKL(s);
     return EACG_OK;
   };
@@ -1350,7 +1352,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     TRY(upload_active());
     // Y = solve(A Y - Y Sigma = C_j) via C~ = C Q, (A - s_m) y~_m = c~_m, Y = Y~ Q^H
     dense_gemm_nn(K, q, p, p, s->fC, sC, s->qcap, s->sigv, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
-                  s->d_kactive, s->st);
+                  s->d_kactive, s->st, s->g.df64);
     // algorithmic: A, C read and Y written once per k; (16/3) q^3 for the Householder reduction
     // plus two reflector transforms of 8 q^2 per shift
     PROF_RUN(P_FOMSOLVE + (f32 ? P_F32 : 0), (double)K * ((double)q * q + 2.0 * q * p) * 16.0,
@@ -1359,12 +1361,12 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
                                s->d_kactive, nullptr, f32 ? 1 : 0, s->st));
     PROF_RUN(P_FOM_RES, 2.0 * K * q * nm * sizeof(V) + 2.0 * s->blk * sizeof(V), 16.0 * K * nm * q * p, 0, {
       dense_gemm_nn(K, q, p, p, s->fY, sC, s->qcap, s->sigvh, (size_t)p * p, p, s->fYt, sC, s->qcap, ONE, ZERO,
-                    s->d_kactive, s->st);
+                    s->d_kactive, s->st, s->g.df64);
       // fYt now holds Y.  Res = C - (W Y - V Y Sigma)
-      O::nn(K, nm, q, p, fW, sV, nm, s->fYt, sC, s->qcap, t1, sb, nm, ONE, ZERO, s->d_kactive, s->st);
+      O::nn(K, nm, q, p, fW, sV, nm, s->fYt, sC, s->qcap, t1, sb, nm, ONE, ZERO, s->d_kactive, s->st, s->g.df64);
       dense_gemm_nn(K, q, p, p, s->fYt, sC, s->qcap, s->sig, (size_t)p * p, p, s->fY, sC, s->qcap, ONE, ZERO,
-                    s->d_kactive, s->st);
-      O::nn(K, nm, q, p, fV, sV, nm, s->fY, sC, s->qcap, t1, sb, nm, MONE, ONE, s->d_kactive, s->st);
+                    s->d_kactive, s->st, s->g.df64);
+      O::nn(K, nm, q, p, fV, sV, nm, s->fY, sC, s->qcap, t1, sb, nm, MONE, ONE, s->d_kactive, s->st, s->g.df64);
       O::axpby(s->blk, ONE, C, MONE, t1, t1, s->st);
       O::norms2(K, sb, t1, s->d_out + 64, s->st);
     });
@@ -1435,18 +1437,18 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     dense_axpby(s->blk, cr(1.0 / mu), phi, ZERO, nullptr, s->Xb, s->st);
     if (!f32) {
       dense_gemm_nn(K, nm, q, p, s->fV, (size_t)s->qcap * nm, nm, s->fYf, sC, s->qcap, s->Xb, sb, nm, ONE, ONE,
-                    nullptr, s->st);
+                    nullptr, s->st, s->g.df64);
     } else {
       O::nn(K, nm, q, p, reinterpret_cast<V*>(s->fV), (size_t)s->qcap * nm, nm, s->fYf, sC, s->qcap, t1, sb, nm, ONE,
-            ZERO, nullptr, s->st);
+            ZERO, nullptr, s->st, s->g.df64);
       dense_to64(s->blk, reinterpret_cast<float2*>(s->tmp1), s->tmp3, s->st);
       dense_axpby(s->blk, ONE, s->Xb, ONE, s->tmp3, s->Xb, s->st);
     }
     dense_gemm_cn(K, nm, p, p, phi, sb, nm, s->Xb, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
-                  s->st);
+                  s->st, s->g.df64);
     dense_inverse(K, p, s->sm1, s->sm2, nullptr, s->st);
     dense_copy(g, phi, s->blk, s->st);
-    dense_gemm_nn(K, nm, p, p, s->Xb, sb, nm, s->sm2, (size_t)p * p, p, g, sb, nm, MONE, ONE, nullptr, s->st);
+    dense_gemm_nn(K, nm, p, p, s->Xb, sb, nm, s->sm2, (size_t)p * p, p, g, sb, nm, MONE, ONE, nullptr, s->st, s->g.df64);
   });
   CKL(s);
   int mx = 0;
@@ -1480,11 +1482,11 @@ static eacg_status trial(eacg_system* s, double t, int prec, TrialOut* out) {
     TRY(polar(s, s->psi_t, s->phi_t, s->eval_t, s->evec_t, s->sinv_t));
     // T(eta) = eta S^{-1} - t Phi+ [[eta S^{-1}, eta S^{-1}]]
     dense_gemm_nn(K, nm, p, p, s->eta, sb, nm, s->sinv_t, (size_t)p * p, p, s->teta_t, sb, nm, ONE, ZERO, nullptr,
-                  s->st);
+                  s->st, s->g.df64);
     dense_gemm_cn(K, nm, p, p, s->teta_t, sb, nm, s->teta_t, sb, nm, s->sm2, (size_t)p * p, p, ONE, ZERO,
-                  s->cn_work, nullptr, s->st);
+                  s->cn_work, nullptr, s->st, s->g.df64);
     dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm2, (size_t)p * p, p, s->teta_t, sb, nm, cr(-t), ONE, nullptr,
-                  s->st);
+                  s->st, s->g.df64);
   });
   CKL(s);
   TRY(evaluate(s, s->phi_t, s->hphi_t, s->res_t, s->lam_t, prec, &out->ev));
@@ -1608,13 +1610,13 @@ static eacg_status transport_g(eacg_system* s, double tau) {
   const int K = s->K, p = s->p, nm = s->n_max;
   const size_t sb = (size_t)p * nm;
   dense_gemm_cn(K, nm, p, p, s->eta, sb, nm, s->gv, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
-                s->st);
+                s->st, s->g.df64);
   small_add_herm(K, p, s->sm1, tau, s->sm2, s->st);  // sm2 = tau (M + M^H)
   small_sqrt_vals(K, p, s->eval_t, s->sqd, s->st);
   dense_lyapunov(K, p, s->evec_t, s->sqd, s->sm2, s->sm3, s->st);
   dense_copy(s->tmp1, s->gv, s->blk, s->st);
-  dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm3, (size_t)p * p, p, s->tmp1, sb, nm, MONE, ONE, nullptr, s->st);
-  dense_gemm_nn(K, nm, p, p, s->tmp1, sb, nm, s->sinv_t, (size_t)p * p, p, s->tg, sb, nm, ONE, ZERO, nullptr, s->st);
+  dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm3, (size_t)p * p, p, s->tmp1, sb, nm, MONE, ONE, nullptr, s->st, s->g.df64);
+  dense_gemm_nn(K, nm, p, p, s->tmp1, sb, nm, s->sinv_t, (size_t)p * p, p, s->tg, sb, nm, ONE, ZERO, nullptr, s->st, s->g.df64);
   CKL(s);
   return EACG_OK;
 }
@@ -2238,11 +2240,11 @@ extern "C" eacg_status eacg_retract(eacg_system* s, const double* phi_dev, const
   TRY(polar(s, s->psi_t, s->tmp1, s->eval_t, s->evec_t, s->sinv_t));
   if (teta_out_dev) {
     dense_gemm_nn(K, nm, p, p, reinterpret_cast<const double2*>(eta_dev), sb, nm, s->sinv_t, (size_t)p * p, p,
-                  s->tmp2, sb, nm, ONE, ZERO, nullptr, s->st);
+                  s->tmp2, sb, nm, ONE, ZERO, nullptr, s->st, s->g.df64);
     dense_gemm_cn(K, nm, p, p, s->tmp2, sb, nm, s->tmp2, sb, nm, s->sm2, (size_t)p * p, p, ONE, ZERO, s->cn_work,
-                  nullptr, s->st);
+                  nullptr, s->st, s->g.df64);
     dense_gemm_nn(K, nm, p, p, s->tmp1, sb, nm, s->sm2, (size_t)p * p, p, s->tmp2, sb, nm, cr(-tau), ONE, nullptr,
-                  s->st);
+                  s->st, s->g.df64);
     CK(cudaMemcpyAsync(teta_out_dev, s->tmp2, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));
   }
   CK(cudaMemcpyAsync(phi_out_dev, s->tmp1, sizeof(double2) * s->blk, cudaMemcpyDeviceToDevice, s->st));

@@ -144,13 +144,14 @@ bool dense_backproject_tc_eligible(int m, int n);
 void dense_backproject_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* Q,
                               size_t sQ, int ldq, double2* C, size_t sC, int ldc, const int* kactive,
                               cudaStream_t st);
+// df = 1: the products and sums in double-float arithmetic (FP64-accurate, on the FP32 pipe).
 void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,
-                   const int* kactive, cudaStream_t st);
+                   const int* kactive, cudaStream_t st, int df = 0);
 // C[k](L x n, ldc) = alpha * A[k](L x m, lda) * B[k](m x n, ldb) + beta * C[k].
 void dense_gemm_nn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, const int* kactive,
-                   cudaStream_t st);
+                   cudaStream_t st, int df = 0);
 // Tile autotune of the A^H B kernel: times its row-group variants on these operands (Kt
 // k-points, prec 0 complex128 / 1 complex64 A and B) and records the fastest for the shape bucket
 // of (m, n, L) for the whole process (kept if already tuned).  C: Kt * m * n, work:
