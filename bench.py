@@ -269,14 +269,16 @@ def profile_summary(prof, total_ms=None):
     return out
 
 
-def roofline_of(prof, traffic_table=None, df=True):
-    """Roofline of the single-kernel profile slot with the largest summed time: achieved
-    algorithmic FLOP/s per launch against the derived FP64 / FP32 ALU peak."""
+def roofline_of(prof, traffic_table=None, df=True, slot=None):
+    """Roofline of one single-kernel profile slot (default: the one with the largest summed
+    time): achieved algorithmic FLOP/s per launch against the derived FP64 / FP32 ALU peak, or
+    for the double-float kernels against the FP32 instruction peak over their measured
+    instructions per FLOP."""
     single = {k: v for k, v in (prof or {}).items()
               if k.rsplit("_", 1)[0] in SINGLE_KERNEL_SLOTS and v["ms"] > 0 and v["launches"] > 0}
-    if not single:
+    if not single or (slot is not None and slot not in single):
         return None
-    top = max(single, key=lambda k: single[k]["ms"])
+    top = slot if slot is not None else max(single, key=lambda k: single[k]["ms"])
     st = prof[top]
     n = st["launches"]
     avg_ms = st["ms"] / n
@@ -619,6 +621,13 @@ def run_serving(args):
         line["roofline"] = roofline_of(m_prof)
         if line["roofline"]:
             line["roofline"]["timed"] = "sample requests solved one at a time in mixed precision"
+        # the transform kernels of the H application (FP64-accurate and FP32) on the same sample
+        line["roofline_transforms"] = {}
+        for slot in ("plane_h_f64", "plane_h_f32"):
+            r = roofline_of(m_prof, slot=slot)
+            if r:
+                line["roofline_transforms"][slot] = {k: r[k] for k in ("achieved", "peak", "unit", "frac",
+                                                                        "avg_launch_ms", "launches")}
         log["mixed_alone_profile"] = profile_summary(m_prof, sum(m_ms))
 
         # ---- Poisson streams at 0.5x and 2x the FP64 one-at-a-time rate (arrival -> converged)
