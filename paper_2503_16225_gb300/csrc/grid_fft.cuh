@@ -136,54 +136,14 @@ struct PlaneCfg {
 
 // FP32 plane kernels whose lines fit a warp exchange the two FFT steps by shuffles
 // (fft_phase_shfl): no scratch plane, one plane of shared memory per CTA.
-// Largest number of lanes of one shared-memory wavefront on one bank slot when lane
-// (line l, slot t) of `lanes` lanes (n2 slots per line) touches element l * a + t * b
-// (`slots` distinct element slots per wavefront: 16 for 8-byte, 32 for 4-byte elements).
-__host__ __device__ constexpr int bank_multiplicity(int a, int b, int n2, int lanes, int slots) {
-  int worst = 0;
-  for (int r = 0; r < slots; ++r) {
-    int c = 0;
-    for (int i = 0; i < lanes; ++i) {
-      const int l = i / n2, t = i % n2;
-      if ((l * a + t * b) % slots == r) ++c;
-    }
-    worst = c > worst ? c : worst;
-  }
-  return worst;
-}
-// Pitch >= lo with the fewest conflicts of the two access patterns (a, b) and (b, a) (the y
-// phases walk a plane column, the z phases a plane row); the first of equals.
-__host__ __device__ constexpr int best_pitch(int lo, int n2, int lanes, int slots, bool both) {
-  int best = lo, cost = 1 << 30;
-  for (int p = lo; p < lo + slots; ++p) {
-    const int c = bank_multiplicity(1, p, n2, lanes, slots) + (both ? bank_multiplicity(p, 1, n2, lanes, slots) : 0);
-    if (c < cost) {
-      cost = c;
-      best = p;
-    }
-  }
-  return best;
-}
-
 template <typename T, int N, int PV>
 struct PlaneShfl {
   static constexpr bool value = std::is_same<T, float>::value && (32 % LinePlan<N, PV>::N2 == 0);
-  // With the slot of a line fastest across lanes, a 64-bit shared-memory wavefront is
-  // 16 / N2 lines x N2 slots: the plane pitch PB is chosen for the fewest bank conflicts of
-  // both the column walks (y phases, element t PB + l) and the row walks (z phases, element
-  // l PB + t); the int column map (32-lane reads, element l PC + t) gets its own pitch PC.
-  static constexpr int N2 = LinePlan<N, PV>::N2;
-  static constexpr int PB = best_pitch(N, N2, 16, 16, true);
-  static constexpr int PC = best_pitch(N + 1, N2, 32, 32, false);
 };
-// planes of shared memory of the potential kernel, and their element pitch
+// planes of shared memory of the potential kernel
 template <typename T, int N, int PV>
 __host__ __device__ constexpr int plane_h_planes() {
   return PlaneShfl<T, N, PV>::value ? 1 : (PlaneCfg<T, N>::pingpong ? 2 : 1);
-}
-template <typename T, int N, int PV>
-__host__ __device__ constexpr int plane_h_pitch() {
-  return PlaneShfl<T, N, PV>::value ? PlaneShfl<T, N, PV>::PB : N + 1;
 }
 
 // Step-1 scratch of the z phases (line l = row ylist[l]) and of the y phases (line = jz).
@@ -218,52 +178,39 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_h(const __gri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* B = reinterpret_cast<V*>(smem_raw);
   V* A = PING ? B + (size_t)N * PP : B;
-  constexpr int PB = plane_h_pitch<T, N, PV>();
-  int* cm = reinterpret_cast<int*>(B + (size_t)plane_h_planes<T, N, PV>() * N * PB);
+  int* cm = reinterpret_cast<int*>(B + (size_t)plane_h_planes<T, N, PV>() * N * PP);
   const GridSeg& S = tab.s[seg_of(tab, blockIdx.y)];
   const int jx = blockIdx.x, band = blockIdx.y - S.y0;
   if (S.kactive && !S.kactive[band / S.p]) return;
   const int ny = S.ny;
+  plane_setup<V, N>(tw, rows, yl, cm, static_cast<const V*>(S.tw), S.rowmask, S.ylist, S.cmapy, ny);
   V* tb = static_cast<V*>(S.tbuf) + ((size_t)band * N + jx) * S.ncols;
   const T* vv = static_cast<const T*>(S.v) + (size_t)jx * N * N;
   if constexpr (SH) {
-    constexpr int PC = PlaneShfl<T, N, PV>::PC;
-    const V* tw_g = static_cast<const V*>(S.tw);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      tw[i] = tw_g[i];
-      rows[i] = S.rowmask[i];
-    }
-    for (int i = threadIdx.x; i < ny; i += blockDim.x) yl[i] = S.ylist[i];
-    for (int i = threadIdx.x; i < ny * (N + 1); i += blockDim.x) {
-      const int r = i / (N + 1), c = i - r * (N + 1);
-      cm[r * PC + c] = S.cmapy[i];
-    }
-    __syncthreads();
     // every load-store hazard of a phase lies within its line: a row (z) or a column jz (y)
     fft_phase_shfl<N, PV, true>(
         ny, tw,
         [&](int l, int fz) {
-          const int c = cm[l * PC + fz];
+          const int c = cm[l * PP + fz];
           return c >= 0 ? tb[c] : czero<V>();
         },
-        [&](int l, int jz, V x, int) { B[yl[l] * PB + jz] = x; });
+        [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
     fft_phase_shfl<N, PV, true>(
-        N, tw, [&](int jz, int fy) { return rows[fy] ? B[fy * PB + jz] : czero<V>(); },
-        [&](int jz, int jy, V x, int) { B[jy * PB + jz] = cscale(x, vv[jy * N + jz]); });
+        N, tw, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : czero<V>(); },
+        [&](int jz, int jy, V x, int) { B[jy * PP + jz] = cscale(x, vv[jy * N + jz]); });
     fft_phase_shfl<N, PV, false>(
-        N, tw, [&](int jz, int jy) { return B[jy * PB + jz]; },
+        N, tw, [&](int jz, int jy) { return B[jy * PP + jz]; },
         [&](int jz, int fy, V x, int) {
-          if (rows[fy]) B[fy * PB + jz] = x;
+          if (rows[fy]) B[fy * PP + jz] = x;
         });
     fft_phase_shfl<N, PV, false>(
-        ny, tw, [&](int l, int jz) { return B[yl[l] * PB + jz]; },
+        ny, tw, [&](int l, int jz) { return B[yl[l] * PP + jz]; },
         [&](int l, int fz, V x, int) {
-          const int c = cm[l * PC + fz];
+          const int c = cm[l * PP + fz];
           if (c >= 0) tb[c] = x;
         });
     return;
   }
-  plane_setup<V, N>(tw, rows, yl, cm, static_cast<const V*>(S.tw), S.rowmask, S.ylist, S.cmapy, ny);
   const ZScratch<V, N, PING> zs{A, B, yl};
   const YScratch<V, N, PING> ys{A, B};
   // z inverse over the rows with columns, straight from the column buffer
@@ -488,9 +435,8 @@ struct GridFft {
   static void plane_h_t(const GridReq* r, int n, cudaStream_t st) {
     GridSegs t;
     const int rows = table(t, r, n, TwKind<T>::value, false);
-    constexpr int PC = PlaneShfl<T, N, PV>::value ? PlaneShfl<T, N, PV>::PC : N + 1;
-    const size_t sm = plane_h_planes<T, N, PV>() * sizeof(cplx<T>) * (size_t)N * plane_h_pitch<T, N, PV>() +
-                      sizeof(int) * (size_t)max_ny(r, n) * PC;
+    const size_t sm = plane_h_planes<T, N, PV>() * sizeof(cplx<T>) * (size_t)N * (N + 1) +
+                      sizeof(int) * (size_t)max_ny(r, n) * (N + 1);
     ensure_smem((const void*)k_plane_h<T, N, PV>, sm);
     k_plane_h<T, N, PV><<<dim3(N, rows), N * N2, sm, st>>>(t);
     count_launch();
