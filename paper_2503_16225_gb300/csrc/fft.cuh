@@ -261,61 +261,6 @@ __device__ __forceinline__ void fft_phase(int nlines, const V* tw, const Scratch
   __syncthreads();
 }
 
-// The same transform phase with the step-1 to step-2 exchange done by warp shuffles: thread
-// slot fastest (thread i works on line i / N2 at slot i % N2), so the N2 threads of a line are
-// adjacent lanes of one warp (N2 divides 32).  In round r thread t sends its step-1 value at
-// position ((t + r) mod N2) + N2 j to the lane of slot (t + r) mod N2 and receives from the lane
-// of slot (t - r) mod N2 its value at position t + N2 j, so after N2 rounds it holds the step-2
-// inputs of columns t + N2 j.  The register indices that depend on t are resolved by unrolled
-// selects.  Inputs come from load(l, i), outputs go to store(l, o, X[o], q) as in fft_phase.
-// Every hazard between the phase's loads and stores must lie within one line (the caller's
-// guarantee): a warp barrier separates them; the CTA synchronises after the phase.  Every
-// thread must call it.
-template <int N, int PV, bool INV, typename V, typename Load, typename Store>
-__device__ __forceinline__ void fft_phase_shfl(int nlines, const V* tw, const Load& load, const Store& store) {
-  constexpr int N1 = LinePlan<N, PV>::N1, N2 = LinePlan<N, PV>::N2;
-  static_assert(32 % N2 == 0, "the threads of a line must share a warp");
-  const int t = threadIdx.x % N2, l = threadIdx.x / N2;
-  const bool act = l < nlines;
-  const int base = (threadIdx.x & 31) - t;  // lane of slot 0 of this line
-  V a[N1], b[N1];
-  if (act) {
-#pragma unroll
-    for (int m = 0; m < N1; ++m) a[m] = load(l, t + N2 * m);
-    line_step1<N, PV, INV>(a, t, tw);
-  } else {
-#pragma unroll
-    for (int m = 0; m < N1; ++m) a[m] = czero<V>();
-  }
-#pragma unroll
-  for (int r = 0; r < N2; ++r) {
-    const int send_pos = (t + r) % N2, src = (t + N2 - r) % N2;
-#pragma unroll
-    for (int j = 0; j < N1 / N2; ++j) {
-      V v = a[N2 * j];
-#pragma unroll
-      for (int c = 1; c < N2; ++c)
-        if (send_pos == c) v = a[c + N2 * j];
-      if (r != 0) {
-        v.x = __shfl_sync(0xffffffffu, v.x, base + src);
-        v.y = __shfl_sync(0xffffffffu, v.y, base + src);
-      }
-#pragma unroll
-      for (int c = 0; c < N2; ++c)
-        if (src == c) b[j * N2 + c] = v;
-    }
-  }
-  if (act) line_step2<N, PV, INV>(b, tw);
-  __syncwarp();
-  if (act) {
-#pragma unroll
-    for (int j = 0; j < N1 / N2; ++j)
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) store(l, (t + N2 * j) + N1 * k2, b[j * N2 + k2], j * N2 + k2);
-  }
-  __syncthreads();
-}
-
 // Scratch lines A[l * AP + position] (AP odd) distinct from the phase's inputs and outputs.
 template <typename V>
 struct PitchedScratch {

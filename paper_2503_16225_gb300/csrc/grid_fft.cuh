@@ -134,18 +134,6 @@ struct PlaneCfg {
   }
 };
 
-// FP32 plane kernels whose lines fit a warp exchange the two FFT steps by shuffles
-// (fft_phase_shfl): no scratch plane, one plane of shared memory per CTA.
-template <typename T, int N, int PV>
-struct PlaneShfl {
-  static constexpr bool value = std::is_same<T, float>::value && (32 % LinePlan<N, PV>::N2 == 0);
-};
-// planes of shared memory of the potential kernel
-template <typename T, int N, int PV>
-__host__ __device__ constexpr int plane_h_planes() {
-  return PlaneShfl<T, N, PV>::value ? 1 : (PlaneCfg<T, N>::pingpong ? 2 : 1);
-}
-
 // Step-1 scratch of the z phases (line l = row ylist[l]) and of the y phases (line = jz).
 template <typename V, int N, bool PING>
 struct ZScratch {
@@ -171,14 +159,13 @@ template <typename T, int N, int PV>
 __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_h(const __grid_constant__ GridSegs tab) {
   using V = cplx<T>;
   constexpr int PP = N + 1;
-  constexpr bool SH = PlaneShfl<T, N, PV>::value;
-  constexpr bool PING = !SH && PlaneCfg<T, N>::pingpong;
+  constexpr bool PING = PlaneCfg<T, N>::pingpong;
   __shared__ V tw[N];
   __shared__ int rows[N], yl[N];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* B = reinterpret_cast<V*>(smem_raw);
   V* A = PING ? B + (size_t)N * PP : B;
-  int* cm = reinterpret_cast<int*>(B + (size_t)plane_h_planes<T, N, PV>() * N * PP);
+  int* cm = reinterpret_cast<int*>(B + (size_t)(PING ? 2 : 1) * N * PP);
   const GridSeg& S = tab.s[seg_of(tab, blockIdx.y)];
   const int jx = blockIdx.x, band = blockIdx.y - S.y0;
   if (S.kactive && !S.kactive[band / S.p]) return;
@@ -186,31 +173,6 @@ __global__ void __launch_bounds__(N * LinePlan<N, PV>::N2) k_plane_h(const __gri
   plane_setup<V, N>(tw, rows, yl, cm, static_cast<const V*>(S.tw), S.rowmask, S.ylist, S.cmapy, ny);
   V* tb = static_cast<V*>(S.tbuf) + ((size_t)band * N + jx) * S.ncols;
   const T* vv = static_cast<const T*>(S.v) + (size_t)jx * N * N;
-  if constexpr (SH) {
-    // every load-store hazard of a phase lies within its line: a row (z) or a column jz (y)
-    fft_phase_shfl<N, PV, true>(
-        ny, tw,
-        [&](int l, int fz) {
-          const int c = cm[l * PP + fz];
-          return c >= 0 ? tb[c] : czero<V>();
-        },
-        [&](int l, int jz, V x, int) { B[yl[l] * PP + jz] = x; });
-    fft_phase_shfl<N, PV, true>(
-        N, tw, [&](int jz, int fy) { return rows[fy] ? B[fy * PP + jz] : czero<V>(); },
-        [&](int jz, int jy, V x, int) { B[jy * PP + jz] = cscale(x, vv[jy * N + jz]); });
-    fft_phase_shfl<N, PV, false>(
-        N, tw, [&](int jz, int jy) { return B[jy * PP + jz]; },
-        [&](int jz, int fy, V x, int) {
-          if (rows[fy]) B[fy * PP + jz] = x;
-        });
-    fft_phase_shfl<N, PV, false>(
-        ny, tw, [&](int l, int jz) { return B[yl[l] * PP + jz]; },
-        [&](int l, int fz, V x, int) {
-          const int c = cm[l * PP + fz];
-          if (c >= 0) tb[c] = x;
-        });
-    return;
-  }
   const ZScratch<V, N, PING> zs{A, B, yl};
   const YScratch<V, N, PING> ys{A, B};
   // z inverse over the rows with columns, straight from the column buffer
@@ -435,8 +397,7 @@ struct GridFft {
   static void plane_h_t(const GridReq* r, int n, cudaStream_t st) {
     GridSegs t;
     const int rows = table(t, r, n, TwKind<T>::value, false);
-    const size_t sm = plane_h_planes<T, N, PV>() * sizeof(cplx<T>) * (size_t)N * (N + 1) +
-                      sizeof(int) * (size_t)max_ny(r, n) * (N + 1);
+    const size_t sm = PlaneCfg<T, N>::smem_bytes(max_ny(r, n));
     ensure_smem((const void*)k_plane_h<T, N, PV>, sm);
     k_plane_h<T, N, PV><<<dim3(N, rows), N * N2, sm, st>>>(t);
     count_launch();
