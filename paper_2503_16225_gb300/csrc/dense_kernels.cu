@@ -1086,7 +1086,6 @@ __global__ void __launch_bounds__(HS_THREADS)
   V* P = pack_in_smem ? reinterpret_cast<V*>(area) : Pg;
   V* vv = pack_in_smem ? P + poff(q, q) : reinterpret_cast<V*>(area);
   V* xv = vv + q;
-  __shared__ V s_tau, s_a2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const double2* Ak = A + k * sA;
   for (int j = 0; j < q; ++j)
@@ -1095,70 +1094,97 @@ __global__ void __launch_bounds__(HS_THREADS)
   V zero;
   zero.x = 0;
   zero.y = 0;
-  // ---- 1. reduction to tridiagonal form
-  for (int j = 0; j + 1 < q; ++j) {
-    const size_t cj = poff(j, q) - j;  // P(i, j) = P[cj + i]
+  // ---- 1. reduction to tridiagonal form.  Four CTA barriers per column: every thread forms
+  // the reflector from the same shared values; v^* x is summed per warp during the product
+  // x = tau A22 v; w = x + a2 v is formed inside the rank-2 update; warp 0 updates the next
+  // column first and sums its squared tail for the next reflector.
+  __shared__ T s_ss;
+  {
     V part = zero;
-    for (int i = j + 2 + tid; i < q; i += blockDim.x) {
-      const V x = P[cj + i];
+    for (int i = 2 + tid; i < q; i += blockDim.x) {
+      const V x = P[i];  // column 0: P(i, 0) = P[i]
       part.x += x.x * x.x + x.y * x.y;
     }
-    const T ss = block_sum(part, red).x;
+    const T ss0 = block_sum(part, red).x;
+    if (tid == 0) s_ss = ss0;
+    __syncthreads();
+  }
+  for (int j = 0; j + 1 < q; ++j) {
+    const size_t cj = poff(j, q) - j;  // P(i, j) = P[cj + i]
+    const T ss = s_ss;
+    const V alpha = P[cj + j + 1];
+    V t = zero, scale = mk<V>((T)1, (T)0);
+    T beta = alpha.x;
+    if (ss > (T)0 || alpha.y != (T)0) {
+      beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + ss), alpha.x);
+      t.x = (beta - alpha.x) / beta;
+      t.y = -alpha.y / beta;
+      const V am = mk<V>(alpha.x - beta, alpha.y);  // scale = 1 / (alpha - beta)
+      const T den = am.x * am.x + am.y * am.y;
+      scale = mk<V>(am.x / den, -am.y / den);
+    }
     if (tid == 0) {
-      const V alpha = P[cj + j + 1];
-      V t = zero;
-      T beta = alpha.x;
-      if (ss > (T)0 || alpha.y != (T)0) {
-        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + ss), alpha.x);
-        t.x = (beta - alpha.x) / beta;
-        t.y = -alpha.y / beta;
-        // scale = 1 / (alpha - beta)
-        const V am = mk<V>(alpha.x - beta, alpha.y);
-        const T den = am.x * am.x + am.y * am.y;
-        s_a2 = mk<V>(am.x / den, -am.y / den);
-      } else {
-        s_a2 = mk<V>((T)1, (T)0);
-      }
-      s_tau = t;
       tau[j] = t;
       eg[j] = beta;
       dg[j] = P[cj + j].x;
     }
-    __syncthreads();
-    const V t = s_tau, scale = s_a2;
     for (int i = j + 1 + tid; i < q; i += blockDim.x) {
       const V v = (i == j + 1) ? mk<V>((T)1, (T)0) : cmul(P[cj + i], scale);
       vv[i] = v;
       P[cj + i] = v;
     }
     __syncthreads();
-    if (t.x == (T)0 && t.y == (T)0) continue;
-    // x = tau A22 v, warp per row i: the lower part A_il (l <= i) along row i of the packed
-    // columns, the upper part conj(A_li) (l > i) down column i, lanes striding over l
+    if (t.x == (T)0 && t.y == (T)0) {
+      // no reflection: the next column's tail norm by a CTA sum
+      V part = zero;
+      const size_t cn = poff(j + 1, q) - (j + 1);
+      for (int i = j + 3 + tid; i < q; i += blockDim.x) {
+        const V x = P[cn + i];
+        part.x += x.x * x.x + x.y * x.y;
+      }
+      const T nss = block_sum(part, red).x;
+      if (tid == 0) s_ss = nss;
+      __syncthreads();
+      continue;
+    }
+    // x = tau A22 v, warp per row i (lower part along the row, upper part down column i), and
+    // the warp's share of v^* x
+    V dpart = zero;
     for (int i = j + 1 + warp; i < q; i += nw) {
       const size_t ci = poff(i, q) - i;
       V acc = zero;
       for (int l = j + 1 + lane; l <= i; l += 32) acc = acc + cmul(P[poff(l, q) + (i - l)], vv[l]);
       for (int l = i + 1 + lane; l < q; l += 32) acc = acc + cmulc(P[ci + l], vv[l]);
       acc = warp_sum(acc);
-      if (lane == 0) xv[i] = cmul(t, acc);
+      const V xi = cmul(t, acc);
+      if (lane == 0) xv[i] = xi;
+      dpart = dpart + cmulc(vv[i], xi);
+    }
+    if (lane == 0) red[warp] = dpart;
+    __syncthreads();
+    if (warp == 0) {
+      V d = lane < nw ? red[lane] : zero;
+      d = warp_sum(d);
+      if (lane == 0) red[32] = d;
     }
     __syncthreads();
-    V dp = zero;
-    for (int i = j + 1 + tid; i < q; i += blockDim.x) dp = dp + cmulc(vv[i], xv[i]);
-    const V dot = block_sum(dp, red);  // v^* x
-    if (tid == 0) s_a2 = cscale(cmul(t, cconj(dot)), (T)-0.5);
-    __syncthreads();
-    const V a2 = s_a2;
-    for (int i = j + 1 + tid; i < q; i += blockDim.x) xv[i] = xv[i] + cmul(a2, vv[i]);  // w
-    __syncthreads();
-    // A22 -= v w^* + w v^* on the lower triangle: warp per column, lanes down the rows
+    // a2 = -(tau / 2) conj(v^* x); A22 -= v w^* + w v^* with w = x + a2 v, warp per column, lanes
+    // down the rows; warp 0 takes column j + 1 first and sums the next reflector's tail norm
+    const V a2 = cscale(cmul(t, cconj(red[32])), (T)-0.5);
     for (int l = j + 1 + warp; l < q; l += nw) {
       const size_t cl = poff(l, q) - l;
-      const V vl = vv[l], wl = xv[l];
+      const V vl = vv[l], wl = xv[l] + cmul(a2, vl);
+      V tail = zero;
       for (int i = l + lane; i < q; i += 32) {
-        const V d = cmul(vv[i], cconj(wl)) + cmul(xv[i], cconj(vl));
-        P[cl + i] = P[cl + i] - d;
+        const V vi = vv[i], wi = xv[i] + cmul(a2, vi);
+        const V d = cmul(vi, cconj(wl)) + cmul(wi, cconj(vl));
+        const V nv = P[cl + i] - d;
+        P[cl + i] = nv;
+        if (l == j + 1 && i >= j + 3) tail.x += nv.x * nv.x + nv.y * nv.y;
+      }
+      if (l == j + 1) {
+        tail = warp_sum(tail);
+        if (lane == 0) s_ss = tail.x;
       }
     }
     __syncthreads();
