@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="serving_stream",
                     choices=["serving_stream", "diamond_k444", "diamond_k222", "two_atom", "diamond64_gamma",
-                             "diamond64_k222"],
+                             "diamond64_k222", "diamond216_gamma"],
                     help="serving_stream: the 256-request stream (headline); the others: concurrent solves "
                          "of one workload; diamond64_*: the 64-atom supercell (96^3 grid, 128 bands, 256 "
                          "projectors), --op runs only (its p x p dense steps exceed the 64-band limit)")
@@ -180,7 +180,8 @@ def workload(name):
             "diamond_k222": lambda: synth.config_diamond(2, kgrid=(2, 2, 2)),
             "two_atom": lambda: synth.config_two_atom(1),
             "diamond64_gamma": lambda: synth.config_diamond_supercell(2),
-            "diamond64_k222": lambda: synth.config_diamond_supercell(2, kgrid=(2, 2, 2))}[name]()
+            "diamond64_k222": lambda: synth.config_diamond_supercell(2, kgrid=(2, 2, 2)),
+            "diamond216_gamma": lambda: synth.config_diamond_supercell(3)}[name]()
 
 
 def measured_peaks():
@@ -902,7 +903,7 @@ def run_op(args):
         for k, n in enumerate(sysm.nk):
             q = np.linalg.qr(raw[k, :, :n].T)[0]
             phi[k, :, :n] = torch.from_numpy(np.ascontiguousarray(q.T))
-    E.eacg_density(sysm.h, phi, None, 0)
+    E.eacg_density(sysm.h, phi, None, 0 if sysm.N <= 96 else 1)   # N = 128: FP32 transforms only
     out = sysm.block()
     if args.op == "apply_h":
         call = lambda: E.eacg_apply_H(sysm.h, phi, out, prec)  # noqa: E731

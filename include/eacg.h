@@ -71,7 +71,10 @@ typedef struct {
   double proj_width;       /* bohr                                             */
   const double* D;         /* host, natoms x 2 (Ha)                            */
   double ecut;             /* basis: 1/2 |k+G|^2 <= ecut (Ha)                  */
-  int N;                   /* FFT grid edge: 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80 or 96 */
+  int N;                   /* FFT grid edge: 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96 or
+                            * 128; at N = 128 only FP32 transforms exist (precision 1 of
+                            * eacg_density, eacg_apply_H, eacg_energy); FP64-accurate ones return
+                            * EACG_EUNSUPPORTED */
   int nbands;              /* p: occupied orbitals per k-point, <= EACG_MAX_BANDS */
   int nk;                  /* K: number of k-points                            */
   const double* kfrac;     /* host, K x 3 fractional coordinates (units of 2 pi / a) */

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeacg.so")
 SOURCES = [
-    "grid_fft_xl.cu", "grid_fft_large.cu", "grid_fft_mid.cu", "grid_fft_48.cu", "grid_fft_small.cu",
+    "grid_fft_128.cu", "grid_fft_xl.cu", "grid_fft_large.cu", "grid_fft_mid.cu", "grid_fft_48.cu", "grid_fft_small.cu",
     "grid_kernels.cu", "dense_kernels.cu", "eacg.cu", "noalloc.cu", "tc_kernels.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -305,7 +305,7 @@ static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::st
     *why = "model is NULL";
     return EACG_EINVAL;
   }
-  if (!(m->a > 0) || m->N < 8 || m->N > 96 || m->nbands < 1 || m->nk < 1 || !(m->ecut > 0) || m->natoms < 0) {
+  if (!(m->a > 0) || m->N < 8 || m->N > 128 || m->nbands < 1 || m->nk < 1 || !(m->ecut > 0) || m->natoms < 0) {
     *why = "invalid cell, grid, band, k-point or cutoff";
     return EACG_EINVAL;
   }
@@ -338,7 +338,7 @@ static eacg_status validate(const eacg_model* m, const eacg_params* prm, std::st
     return EACG_EUNSUPPORTED;
   }
   if (!grid_supported(m->N)) {
-    *why = "grid size N must be one of 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96";
+    *why = "grid size N must be one of 8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96, 128";
     return EACG_EUNSUPPORTED;
   }
   if (prm && (!(prm->mu > 0) || prm->max_ls < 1 || prm->max_fom < 1 || prm->method < 0 || prm->method > 1)) {
@@ -799,8 +799,20 @@ static void projector_overlaps32(eacg_system* s, const float2* in32, const int* 
                     np, ONE, ZERO, s->cn_work, kactive, s->st);
 }
 
+// FP64-accurate transforms hold a plane of 16-byte values in one CTA's shared memory: grids up
+// to N = 96.  Larger grids (N = 128) have the FP32 transforms only.
+constexpr int MAX_N_FP64_TRANSFORMS = 96;
+static eacg_status check_fp64_grid(eacg_system* s, int prec) {
+  if (prec == 0 && s->N > MAX_N_FP64_TRANSFORMS) {
+    s->err = "FP64-accurate transforms support grids up to N = 96; N = 128 has FP32 transforms (precision 1)";
+    return EACG_EUNSUPPORTED;
+  }
+  return EACG_OK;
+}
+
 // out = H in with the current potential (prec 0: FP64 transforms, 1: FP32).
 static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out, int prec, const int* kactive) {
+  TRY(check_fp64_grid(s, prec));
   const int nb = s->K * s->p;
   // algorithmic bytes per band: coefficients read/written in FP64, the x-pass
   // intermediate (N * ncols values of the transform precision) written, read, written, read
@@ -859,6 +871,7 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
 
 // rho of an orthonormal block into d_rho.
 static eacg_status density_only(eacg_system* s, const double2* phi, int prec) {
+  TRY(check_fp64_grid(s, prec));
   const int nb = s->K * s->p;
   const int N = s->N;
   const size_t N3 = (size_t)N * N * N;

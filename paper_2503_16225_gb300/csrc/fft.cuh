@@ -47,6 +47,7 @@ EACG_LINE_PLAN(64, 0, 16, 4)
 EACG_LINE_PLAN(72, 0, 12, 6)
 EACG_LINE_PLAN(80, 0, 20, 4)
 EACG_LINE_PLAN(96, 0, 24, 4)
+EACG_LINE_PLAN(128, 0, 16, 8)
 EACG_LINE_PLAN(16, 1, 8, 2)
 EACG_LINE_PLAN(32, 1, 16, 2)
 EACG_LINE_PLAN(36, 1, 6, 6)
@@ -57,7 +58,7 @@ EACG_LINE_PLAN(72, 1, 24, 3)
 
 // The supported line lengths (every N with a LinePlan), for host-side checks and dispatch,
 // and those with a second plan variant.
-#define EACG_FOR_EACH_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(64) X(72) X(80) X(96)
+#define EACG_FOR_EACH_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(64) X(72) X(80) X(96) X(128)
 #define EACG_FOR_EACH_N_PLAN1(X) X(16) X(32) X(36) X(48) X(64) X(72)
 
 template <int R, bool INV, typename V>

@@ -433,48 +433,64 @@ struct GridFft {
 // Dispatchers defined outside the class, so that they are not inline: the explicit
 // instantiations in the grid_fft_*.cu units are then the only ones, and other translation
 // units see only their declarations (extern template).
+// The FP64-accurate plane kernels hold a plane of 16-byte values in shared memory, which fits
+// up to N = 96; larger grids have the FP32 transforms only (the driver refuses the others
+// before any launch, so those branches are not instantiated).
+template <int N>
+struct Fp64Planes {
+  static constexpr bool value = N <= 96;
+};
+
 template <int N, int PV>
 void GridFft<N, PV>::xpass_inv(int mode, const GridReq* r, int n, cudaStream_t st) {
-  if (mode == 0)
-    xinv<double, double2>(r, n, st);
-  else if (mode == 1)
+  if (mode == 1)
     xinv<float, double2>(r, n, st);
   else if (mode == 2)
     xinv<float, float2>(r, n, st);
-  else
-    xinv<dfloat, double2>(r, n, st);
+  else if constexpr (Fp64Planes<N>::value) {
+    if (mode == 0)
+      xinv<double, double2>(r, n, st);
+    else
+      xinv<dfloat, double2>(r, n, st);
+  }
 }
 
 template <int N, int PV>
 void GridFft<N, PV>::xpass_fwd(int mode, const GridReq* r, int n, cudaStream_t st) {
-  if (mode == 0)
-    xfwd<double, double2>(r, n, st);
-  else if (mode == 1)
+  if (mode == 1)
     xfwd<float, double2>(r, n, st);
   else if (mode == 2)
     xfwd<float, float2>(r, n, st);
-  else
-    xfwd<dfloat, double2>(r, n, st);
+  else if constexpr (Fp64Planes<N>::value) {
+    if (mode == 0)
+      xfwd<double, double2>(r, n, st);
+    else
+      xfwd<dfloat, double2>(r, n, st);
+  }
 }
 
 template <int N, int PV>
 void GridFft<N, PV>::plane_h(int prec, const GridReq* r, int n, cudaStream_t st) {
-  if (prec == 0)
-    plane_h_t<double>(r, n, st);
-  else if (prec == 1)
+  if (prec == 1)
     plane_h_t<float>(r, n, st);
-  else
-    plane_h_t<dfloat>(r, n, st);
+  else if constexpr (Fp64Planes<N>::value) {
+    if (prec == 0)
+      plane_h_t<double>(r, n, st);
+    else
+      plane_h_t<dfloat>(r, n, st);
+  }
 }
 
 template <int N, int PV>
 void GridFft<N, PV>::plane_rho(int prec, const GridReq* r, int n, cudaStream_t st) {
-  if (prec == 0)
-    plane_rho_t<double>(r, n, st);
-  else if (prec == 1)
+  if (prec == 1)
     plane_rho_t<float>(r, n, st);
-  else
-    plane_rho_t<dfloat>(r, n, st);
+  else if constexpr (Fp64Planes<N>::value) {
+    if (prec == 0)
+      plane_rho_t<double>(r, n, st);
+    else
+      plane_rho_t<dfloat>(r, n, st);
+  }
 }
 
 template <int N, int PV>

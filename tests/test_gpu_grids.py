@@ -95,3 +95,48 @@ def test_autotune_picks_a_compiled_plan(N):
     finally:
         a.close()
         b.close()
+
+
+def test_grid_128_fp32_transforms():
+    """N = 128 (the 216-atom supercell's grid): the FP32 transforms (one in-place plane of
+    128 x 129 complex64 values per CTA) give the oracle's density, potential and H psi to the
+    FP32 bound 5e-6; the FP64-accurate transforms, whose plane would not fit a CTA's shared
+    memory, are refused with EACG_EUNSUPPORTED before any launch."""
+    N = 128
+    cfg = grid_model(N)
+    model = Model(cfg)
+    s = E.System(cfg)
+    try:
+        assert s.nk == model.nk
+        rng = np.random.default_rng(N)
+        Phi = [np.linalg.qr(rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2)))[0] for n in model.nk]
+        t = torch.zeros((s.K, s.p, s.n_max), dtype=torch.complex128)
+        for k, P in enumerate(Phi):
+            t[k, :, :P.shape[0]] = torch.from_numpy(np.ascontiguousarray(P.T))
+        phi = t.cuda()
+        with pytest.raises(E.EacgError) as err:
+            E.eacg_density(s.h, phi, None, 0)
+        assert err.value.code == 9
+        rho = s.grid()
+        E.eacg_density(s.h, phi, rho, 1)
+        rho_o = model.density(Phi)
+        assert rel(rho.cpu().numpy(), rho_o) < 5e-6
+        v = s.grid()
+        E.eacg_get_potential(s.h, v)
+        vtot = model.potentials(rho_o)[0]
+        assert rel(v.cpu().numpy(), vtot) < 5e-6
+        C = [rng.standard_normal(P.shape) + 1j * rng.standard_normal(P.shape) for P in Phi]
+        t.zero_()
+        for k, Ck in enumerate(C):
+            t[k, :, :Ck.shape[0]] = torch.from_numpy(np.ascontiguousarray(Ck.T))
+        out = s.block()
+        E.eacg_apply_H(s.h, t.cuda(), out, 1)
+        h = out.cpu().numpy()
+        for k in range(model.K):
+            got = h[k, :, :model.nk[k]].T
+            assert rel(got, model.apply_H(k, C[k], vtot)) < 5e-6, k
+            assert np.all(h[k, :, model.nk[k]:] == 0)
+        with pytest.raises(E.EacgError):
+            E.eacg_apply_H(s.h, t.cuda(), out, 0)
+    finally:
+        s.close()
