@@ -114,8 +114,9 @@ typedef struct {
                        * Default 0 */
   int tensor_cores;   /* 1: where nproj >= 128 and nbands is a multiple of 16, the projector
                        * overlaps of complex64 blocks (FP32 phase, FP32 FOM; eacg_overlap_c64,
-                       * method 1) and the back-projection of FP32-phase evaluations (nbands <= 256;
-                       * eacg_backproject_c64, method 1) on the tensor cores; 0: SIMT FP32.
+                       * method 1) and the back-projection of FP32-phase evaluations (in column
+                       * blocks of at most 256 bands; eacg_backproject_c64, method 1) on the
+                       * tensor cores; 0: SIMT FP32.
                        * Default 1 */
   int df_transforms;  /* 1: the FP64-accurate transforms (FP64 mode, the FP64 phase of the mixed
                        * mode and the density) run in double-float arithmetic, each value an

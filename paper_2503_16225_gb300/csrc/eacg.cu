@@ -856,10 +856,15 @@ static eacg_status apply_H_block(eacg_system* s, const double2* in, double2* out
                projector_overlaps32(s, in32, kactive);
                dense_copy(s->d_P2, s->d_P, (size_t)K * np * p, s->st);
                dense_scale_rows(K, np, p, s->d_P, s->d_dvec, s->st);
-               if (s->tc_proj && dense_backproject_tc_eligible(np, p))
-                 dense_backproject_tf32x3(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np,
-                                          out, (size_t)p * nm, nm, kactive, s->st);
-               else
+               if (s->tc_proj && p % 16 == 0) {
+                 // tensor-core back-projection in column blocks of at most 256 bands (one MMA N)
+                 for (int j0 = 0; j0 < p; j0 += 256) {
+                   const int nc = std::min(256, p - j0);
+                   dense_backproject_tf32x3(K, nm, np, nc, s->d_B32, (size_t)np * nm, nm, s->d_P + (size_t)j0 * np,
+                                            (size_t)np * p, np, out + (size_t)j0 * nm, (size_t)p * nm, nm, kactive,
+                                            s->st);
+                 }
+               } else
                  dense_gemm_nn32_into64(K, nm, np, p, s->d_B32, (size_t)np * nm, nm, s->d_P, (size_t)np * p, np,
                                         out, (size_t)p * nm, nm, ONE, ONE, kactive, s->st);
              });
