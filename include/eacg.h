@@ -284,7 +284,10 @@ eacg_status eacg_overlap_noalloc(int K, int n, int p, const double* a_dev, const
  * TF32 parts, three TF32 products per product), for m >= 128 and n a multiple of 16, else
  * EACG_EUNSUPPORTED.  Both accumulate in FP32 within chunks of 1024 rows and sum the chunks in
  * FP64 in a fixed order.  Allocates and frees its own scratch; stream: cudaStream_t or NULL;
- * returns after synchronising it.  EACG_EINVAL for negative sizes or null buffers. */
+ * returns after synchronising it.  EACG_EINVAL for negative sizes or null buffers.
+ * The tensor-core kernel waits on its MMAs with bounded polls; a CTA whose wait gives up
+ * writes NaN for its tile and counts itself in a per-device counter, and the call then returns
+ * EACG_ECUDA (also when a tensor-core call running beside it on the same device gave up). */
 eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, const float* b_dev, double* c_dev,
                              int method, void* stream);
 
@@ -295,7 +298,9 @@ eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float* a_dev, con
  * 1: tensor cores (tcgen05, 3 x TF32 split, accumulation runs of 48 MMAs summed with
  * round-to-nearest FP32 adds) for 16 <= n <= 256 with n a multiple of 16, else
  * EACG_EUNSUPPORTED.  stream: cudaStream_t or NULL; returns after synchronising it.
- * EACG_EINVAL for negative sizes or null buffers. */
+ * EACG_EINVAL for negative sizes or null buffers.
+ * A tensor-core wait that gives up is reported as in eacg_overlap_c64 (NaN added to the
+ * CTA's rows, EACG_ECUDA). */
 eacg_status eacg_backproject_c64(int K, int L, int m, int n, const float* a_dev, const double* q_dev, double* c_dev,
                                  int method, void* stream);
 

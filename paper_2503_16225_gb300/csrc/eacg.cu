@@ -957,6 +957,17 @@ struct EvalOut {
 };
 
 // Density, potential, H phi, Lambda, R and the energy at an orthonormal phi.
+// A non-finite energy or residual; names a tensor-core wait that gave up (its tile is NaN) when
+// the device's give-up count is not zero.
+static eacg_status nan_status(eacg_system* s, const char* what) {
+  s->err = what;
+  if (s->prm.tensor_cores) {
+    const unsigned int n = dense_tc_gaveup_count(s->st);
+    if (n != 0u && n != ~0u) s->err += " (a tensor-core MMA wait gave up on this device)";
+  }
+  return EACG_ENAN;
+}
+
 static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, double2* res, double2* lam, int prec,
                             EvalOut* out) {
   const int K = s->K, p = s->p, nm = s->n_max;
@@ -980,10 +991,7 @@ static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, d
     for (double& t : out->terms) t = 0.0;
     out->E = s->occ * s->h_out[0];
     out->rnorm = std::sqrt(std::max(s->h_out[1], 0.0));
-    if (!std::isfinite(out->E) || !std::isfinite(out->rnorm)) {
-      s->err = "non-finite band energy or residual";
-      return EACG_ENAN;
-    }
+    if (!std::isfinite(out->E) || !std::isfinite(out->rnorm)) return nan_status(s, "non-finite band energy or residual");
     return EACG_OK;
   }
   // kinetic energy partials -> d_red[0..K*p), summed into d_out[0]
@@ -1012,10 +1020,7 @@ static eacg_status evaluate(eacg_system* s, const double2* phi, double2* hphi, d
   out->terms[4] = enl;
   out->E = ekin + eloc + out->terms[2] + out->terms[3] + enl;
   out->rnorm = std::sqrt(std::max(r2, 0.0));
-  if (!std::isfinite(out->E) || !std::isfinite(out->rnorm)) {
-    s->err = "non-finite energy or residual";
-    return EACG_ENAN;
-  }
+  if (!std::isfinite(out->E) || !std::isfinite(out->rnorm)) return nan_status(s, "non-finite energy or residual");
   return EACG_OK;
 }
 
@@ -2356,6 +2361,7 @@ extern "C" eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float*
   const float2* A = reinterpret_cast<const float2*>(a_dev);
   const float2* B = reinterpret_cast<const float2*>(b_dev);
   double2* C = reinterpret_cast<double2*>(c_dev);
+  const unsigned int gaveup0 = method ? dense_tc_gaveup_count(st) : 0u;
   if (method)
     dense_overlap_tf32x3(K, L, m, n, A, (size_t)m * L, L, B, (size_t)n * L, L, C, (size_t)m * n, m, ONE, ZERO, work,
                          nullptr, st);
@@ -2365,6 +2371,7 @@ extern "C" eacg_status eacg_overlap_c64(int K, int L, int m, int n, const float*
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaFree(work);
+  if (e == cudaSuccess && method && dense_tc_gaveup_count(st) != gaveup0) return EACG_ECUDA;
   return e == cudaSuccess ? EACG_OK : EACG_ECUDA;
 }
 
@@ -2378,6 +2385,7 @@ extern "C" eacg_status eacg_backproject_c64(int K, int L, int m, int n, const fl
   const float2* A = reinterpret_cast<const float2*>(a_dev);
   const double2* Q = reinterpret_cast<const double2*>(q_dev);
   double2* C = reinterpret_cast<double2*>(c_dev);
+  const unsigned int gaveup0 = (method && m > 0) ? dense_tc_gaveup_count(st) : 0u;
   if (m > 0) {
     if (method)
       dense_backproject_tf32x3(K, L, m, n, A, (size_t)m * L, L, Q, (size_t)n * m, m, C, (size_t)n * L, L, nullptr,
@@ -2388,6 +2396,7 @@ extern "C" eacg_status eacg_backproject_c64(int K, int L, int m, int n, const fl
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && method && m > 0 && dense_tc_gaveup_count(st) != gaveup0) return EACG_ECUDA;
   return e == cudaSuccess ? EACG_OK : EACG_ECUDA;
 }
 

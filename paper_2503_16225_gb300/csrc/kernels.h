@@ -144,6 +144,10 @@ bool dense_backproject_tc_eligible(int m, int n);
 void dense_backproject_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA, int lda, const double2* Q,
                               size_t sQ, int ldq, double2* C, size_t sC, int ldc, const int* kactive,
                               cudaStream_t st);
+// Number of tensor-core CTAs on the current device whose bounded mbarrier waits gave up (their
+// outputs hold NaN) since the library was loaded; read on st after synchronising it (~0u when
+// the read fails).  A change across a call marks that call, or one running beside it, failed.
+unsigned int dense_tc_gaveup_count(cudaStream_t st);
 // df = 1: the products and sums in double-float arithmetic (FP64-accurate, on the FP32 pipe).
 void dense_gemm_cn(int K, int L, int m, int n, const double2* A, size_t sA, int lda, const double2* B, size_t sB,
                    int ldb, double2* C, size_t sC, int ldc, double2 alpha, double2 beta, double2* work,

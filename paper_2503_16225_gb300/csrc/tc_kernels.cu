@@ -48,6 +48,10 @@ constexpr int TC_THREADS = 256;
 constexpr int TC_CHUNK = 1024;            // complex rows per partial (the SIMT kernel's chunk)
 constexpr int TC_FLUSH = 4;              // stages per tensor-memory accumulation run
 constexpr long long TC_SPIN = 4000000;    // try_wait polls before a wait gives up
+constexpr long long TC_SPIN_DRAIN = 8 * TC_SPIN;  // polls of the final wait before tensor memory is released
+
+// CTAs whose bounded waits gave up since the library was loaded (per device, never reset)
+__device__ unsigned int g_tc_gaveup = 0;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -74,8 +78,8 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
 // bounded wait for the completion of the mbarrier phase with the given parity
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < TC_SPIN; ++it) {
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, long long spin = TC_SPIN) {
+  for (long long it = 0; it < spin; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -250,16 +254,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   }
   // completion of the last issued stage of each buffer (also after a wait that gave up, so that
-  // no MMA still writes the tensor memory when it is released)
+  // no MMA still writes the tensor memory when it is released; this wait polls 8 times longer)
   {
     bool ok = true;
     for (int b = 0; b < 2; ++b) {
       if (issued > b) {
         const int sb = ((issued - 1 - b) >> 1) * 2 + b;  // last issued stage on buffer b
-        ok = tc_wait(b ? mb1 : mb0, (uint32_t)((sb >> 1) & 1)) && ok;
+        ok = tc_wait(b ? mb1 : mb0, (uint32_t)((sb >> 1) & 1), TC_SPIN_DRAIN) && ok;
       }
     }
     failed = __syncthreads_or(!ok) || failed;
+    if (failed && tid == 0) atomicAdd(&g_tc_gaveup, 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   // epilogue: thread (warp w, lane t) owns row 32 (w % 4) + t of Re (w < 4) or Im (w >= 4)
@@ -443,10 +448,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       if (issued > b) {
         const int sb = ((issued - 1 - b) >> 1) * 2 + b;
-        ok = tc_wait(b ? mb1 : mb0, (uint32_t)((sb >> 1) & 1)) && ok;
+        ok = tc_wait(b ? mb1 : mb0, (uint32_t)((sb >> 1) & 1), TC_SPIN_DRAIN) && ok;
       }
     }
     failed = __syncthreads_or(!ok) || failed;
+    if (failed && tid == 0) atomicAdd(&g_tc_gaveup, 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   // epilogue: interleaved row 32 w + lane -> row l of C, part re/im; C += the sums (FP64)
@@ -497,6 +503,14 @@ void dense_overlap_tf32x3(int K, int L, int m, int n, const float2* A, size_t sA
     count_launch();
   }
   dense_cn_reduce(K, m, n, nch, work, C, sC, ldc, alpha, beta, kactive, st);
+}
+
+unsigned int dense_tc_gaveup_count(cudaStream_t st) {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbolAsync(&v, g_tc_gaveup, sizeof(v), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ~0u;
+  return v;
 }
 
 bool dense_backproject_tc_eligible(int m, int n) { return m >= 1 && n >= 16 && n <= 256 && n % 16 == 0; }
