@@ -899,7 +899,7 @@ def run_op(args):
     if sysm.p <= E.EACG_MAX_BANDS_DENSE:
         E.eacg_set_psi(sysm.h, torch.from_numpy(raw).cuda())
         E.eacg_get_psi(sysm.h, phi)
-    else:  # orthonormal start by host QR (the library's polar factor needs p <= 64)
+    else:  # orthonormal start by host QR (p above the library's dense-kernel limit)
         for k, n in enumerate(sysm.nk):
             q = np.linalg.qr(raw[k, :, :n].T)[0]
             phi[k, :, :n] = torch.from_numpy(np.ascontiguousarray(q.T))

@@ -38,11 +38,12 @@ typedef struct eacg_system eacg_system;
 /* Band limits.  The transforms, the density, the potential, H application and the energy
  * evaluation take up to EACG_MAX_BANDS bands per k-point.  The calls that decompose p x p
  * matrices (eacg_set_psi, eacg_step, eacg_solve, eacg_solve_host, eacg_ea_gradient,
- * eacg_retract, eacg_scf_guess: polar factor, inverse, Lyapunov solve, rank-revealing QR, projected FOM
- * solves) hold a p x p block in one CTA's shared memory and return EACG_EUNSUPPORTED for
- * p > EACG_MAX_BANDS_DENSE. */
+ * eacg_retract, eacg_scf_guess: polar factor, inverse, Lyapunov solve, rank-revealing QR,
+ * projected FOM solves) run one CTA per k-point; up to 64 bands (80 for some of them) the p x p
+ * blocks sit in shared memory, above that in a global scratch owned by the system.  They
+ * return EACG_EUNSUPPORTED for p > EACG_MAX_BANDS_DENSE. */
 #define EACG_MAX_BANDS 1024
-#define EACG_MAX_BANDS_DENSE 64
+#define EACG_MAX_BANDS_DENSE 512
 
 typedef enum {
   EACG_OK = 0,

@@ -24,7 +24,7 @@ __all__ = [
 
 # band limits of include/eacg.h: transforms / H / density / energy, and the p x p dense calls
 EACG_MAX_BANDS = 1024
-EACG_MAX_BANDS_DENSE = 64
+EACG_MAX_BANDS_DENSE = 512
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBREAKDOWN", 5: "ENONCOERCIVE",
           6: "ELINESEARCH", 7: "ENAN", 8: "ENOTCONV", 9: "EUNSUPPORTED"}

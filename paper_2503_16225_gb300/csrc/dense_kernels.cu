@@ -488,16 +488,18 @@ struct JacobiMath<double> {
 };
 template <typename T>
 __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double* __restrict__ w,
-                       double2* __restrict__ Vg, const int* __restrict__ kactive) {
+                       double2* __restrict__ Vg, const int* __restrict__ kactive, unsigned char* gscr,
+                       size_t gstride) {
   using V2 = cplx<T>;
   using M = JacobiMath<T>;
   const int k = blockIdx.x;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int pe = p + (p & 1);  // even number of slots (a dummy index when p is odd)
-  V2* A = reinterpret_cast<V2*>(smem_raw);
+  // A and V in shared memory, or (gscr set, large p) in this k's global scratch
+  V2* A = reinterpret_cast<V2*>(gscr ? gscr + (size_t)k * gstride : smem_raw);
   V2* V = A + p * p;
-  T* rot = reinterpret_cast<T*>(V + p * p);  // [pe/2][4]: c, s, cos phi, sin phi
+  T* rot = reinterpret_cast<T*>(gscr ? smem_raw : reinterpret_cast<unsigned char*>(V + p * p));  // [pe/2][4]
   T* red = rot + 2 * pe;                     // [2 + 2 * warps]
   const double2* Ak = Ag + k * sA;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -653,20 +655,38 @@ __global__ void k_heig(int p, const double2* __restrict__ Ag, size_t sA, double*
   }
 }
 
+// Matrices of the p x p kernels live in shared memory up to this size, else in global scratch.
+constexpr size_t PP_SMEM_MAX = 200 * 1024;
+constexpr int PP_GLOBAL_THREADS = 1024;  // threads of a p x p kernel working from global scratch
+
+static size_t heig_big(int p) { return sizeof(double2) * 2 * (size_t)p * p; }
+static size_t inverse_big(int p) { return sizeof(double2) * 2 * (size_t)p * p; }
+static size_t lyap_big(int p) { return sizeof(double2) * 3 * (size_t)p * p; }
+static size_t pivchol_big(int p) { return sizeof(double2) * 2 * (size_t)p * p + sizeof(int) * (size_t)p + 16; }
+static size_t pp_stride(int p) {
+  auto g = [](size_t b) { return b > PP_SMEM_MAX ? ((b + 255) & ~(size_t)255) : (size_t)0; };
+  return std::max(std::max(g(heig_big(p)), g(inverse_big(p))), std::max(g(lyap_big(p)), g(pivchol_big(p))));
+}
+size_t dense_pp_scratch(int K, int p) { return (size_t)K * pp_stride(p); }
+
 template <typename T>
 static void heig_t(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
-                   cudaStream_t st) {
+                   void* scratch, cudaStream_t st) {
   const int pe = p + (p & 1);
-  const size_t sm = sizeof(cplx<T>) * 2 * p * p + sizeof(T) * (2 * pe + 2 + 16) + 16;
+  const bool big = heig_big(p) > PP_SMEM_MAX;
+  if (big && !scratch) return;  // callers size the scratch with dense_pp_scratch
+  const int threads = big ? PP_GLOBAL_THREADS : (p <= 16 ? 64 : 256);
+  const size_t small = sizeof(T) * (2 * pe + 2 + 2 * (threads / 32)) + 16;
+  const size_t sm = (big ? 0 : sizeof(cplx<T>) * 2 * p * p) + small;
   ensure_smem((const void*)k_heig<T>, sm);
-  const int threads = p <= 16 ? 64 : 256;
-  k_heig<T><<<K, threads, sm, st>>>(p, A, sA, w, V, kactive);
+  k_heig<T><<<K, threads, sm, st>>>(p, A, sA, w, V, kactive, big ? (unsigned char*)scratch : nullptr,
+                                    pp_stride(p));
   count_launch();
 }
 
 void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive,
-                cudaStream_t st) {
-  heig_t<double>(K, p, A, sA, w, V, kactive, st);
+                cudaStream_t st, void* scratch) {
+  heig_t<double>(K, p, A, sA, w, V, kactive, scratch, st);
 }
 // out = V diag(f(w)) V^H, f(x) = x^expo for x > cut_rel * max(w, 0), else 0
 __global__ void k_eig_func(int p, const double2* __restrict__ V, const double* __restrict__ w, double expo,
@@ -700,15 +720,30 @@ __global__ void k_eig_func(int p, const double2* __restrict__ V, const double* _
 
 void dense_eig_func(int K, int p, const double2* V, const double* w, double expo, double cut_rel, double2* out,
                     const int* kactive, cudaStream_t st) {
-  k_eig_func<<<K, 128, sizeof(double) * (p + 1), st>>>(p, V, w, expo, cut_rel, out, kactive);
+  k_eig_func<<<K, p > 64 ? 512 : 128, sizeof(double) * (p + 1), st>>>(p, V, w, expo, cut_rel, out, kactive);
   count_launch();
 }
 
-// Gauss-Jordan inverse with partial pivoting, one CTA per matrix (p <= 64).
-__global__ void k_inverse(int p, const double2* __restrict__ A, double2* __restrict__ Ainv, int* __restrict__ info) {
+// Largest value over the warp with its index, the smallest index on ties (every lane gets it).
+__device__ __forceinline__ void warp_argmax(double& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+
+// Gauss-Jordan inverse with partial pivoting, one CTA per matrix; the augmented matrix in
+// shared memory, or (gscr set, large p) in this k's global scratch.
+__global__ void k_inverse(int p, const double2* __restrict__ A, double2* __restrict__ Ainv, int* __restrict__ info,
+                          unsigned char* gscr, size_t gstride) {
   const int k = blockIdx.x;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* M = reinterpret_cast<double2*>(smem_raw);  // [2p][p] column-major augmented
+  double2* M = reinterpret_cast<double2*>(gscr ? gscr + (size_t)k * gstride : smem_raw);  // [2p][p] augmented
   __shared__ int piv;
   const double2* Ak = A + (size_t)k * p * p;
   for (int e = threadIdx.x; e < 2 * p * p; e += blockDim.x) {
@@ -717,18 +752,21 @@ __global__ void k_inverse(int p, const double2* __restrict__ A, double2* __restr
   }
   __syncthreads();
   for (int c = 0; c < p; ++c) {
-    if (threadIdx.x == 0) {
-      int best = c;
-      double bv = cabs2(M[c * p + c]);
-      for (int i = c + 1; i < p; ++i) {
+    if (threadIdx.x < 32) {  // pivot: the first row of largest modulus in column c
+      double bv = -1.0;
+      int best = p;
+      for (int i = c + (int)threadIdx.x; i < p; i += 32) {
         const double v = cabs2(M[c * p + i]);
         if (v > bv) {
           bv = v;
           best = i;
         }
       }
-      piv = best;
-      if (bv == 0.0 && info) info[k] = c + 1;
+      warp_argmax(bv, best);
+      if (threadIdx.x == 0) {
+        piv = best;
+        if (bv == 0.0 && info) info[k] = c + 1;
+      }
     }
     __syncthreads();
     const int r = piv;
@@ -762,19 +800,23 @@ __global__ void k_inverse(int p, const double2* __restrict__ A, double2* __restr
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ainv[(size_t)k * p * p + e] = M[p * p + e];
 }
 
-void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st) {
-  const size_t sm = sizeof(double2) * 2 * p * p;
+void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st, void* scratch) {
+  const bool big = inverse_big(p) > PP_SMEM_MAX;
+  if (big && !scratch) return;  // callers size the scratch with dense_pp_scratch
+  const size_t sm = big ? 0 : inverse_big(p);
   ensure_smem((const void*)k_inverse, sm);
-  k_inverse<<<K, 256, sm, st>>>(p, A, Ainv, info);
+  k_inverse<<<K, big ? PP_GLOBAL_THREADS : 256, sm, st>>>(p, A, Ainv, info, big ? (unsigned char*)scratch : nullptr,
+                                                           pp_stride(p));
   count_launch();
 }
 
-// Lyapunov by the eigenbasis of S.
+// Lyapunov by the eigenbasis of S; V and the two temporaries in shared memory, or (gscr set,
+// large p) in this k's global scratch.
 __global__ void k_lyap(int p, const double2* __restrict__ Vg, const double* __restrict__ s, const double2* __restrict__ Mg,
-                       double2* __restrict__ X) {
+                       double2* __restrict__ X, unsigned char* gscr, size_t gstride) {
   const int k = blockIdx.x;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* V = reinterpret_cast<double2*>(smem_raw);
+  double2* V = reinterpret_cast<double2*>(gscr ? gscr + (size_t)k * gstride : smem_raw);
   double2* T1 = V + p * p;
   double2* T2 = T1 + p * p;
   const double2* Vk = Vg + (size_t)k * p * p;
@@ -814,10 +856,14 @@ __global__ void k_lyap(int p, const double2* __restrict__ Vg, const double* __re
   }
 }
 
-void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st) {
-  const size_t sm = sizeof(double2) * 3 * p * p;
+void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st,
+                    void* scratch) {
+  const bool big = lyap_big(p) > PP_SMEM_MAX;
+  if (big && !scratch) return;  // callers size the scratch with dense_pp_scratch
+  const size_t sm = big ? 0 : lyap_big(p);
   ensure_smem((const void*)k_lyap, sm);
-  k_lyap<<<K, 256, sm, st>>>(p, V, s, M, X);
+  k_lyap<<<K, big ? PP_GLOBAL_THREADS : 256, sm, st>>>(p, V, s, M, X, big ? (unsigned char*)scratch : nullptr,
+                                                        pp_stride(p));
   count_launch();
 }
 
@@ -1031,6 +1077,14 @@ constexpr int HS_THREADS = 1024;
 __host__ __device__ __forceinline__ size_t poff(int j, int q) {  // start of packed column j
   return (size_t)j * q - (size_t)j * (j - 1) / 2;
 }
+// Offset and size of the large-q region of the shifted solve's work area (tau, d, e, v, w).
+__host__ __device__ __forceinline__ size_t hs_extra_off(int p, int q, size_t es, size_t ts) {
+  const size_t b = poff(q, q) * es + (size_t)q * p * es + (size_t)3 * p * q * ts;
+  return (b + 255) & ~(size_t)255;
+}
+__host__ __device__ __forceinline__ size_t hs_extra_size(int q, size_t es, size_t ts) {
+  return (size_t)q * es + (size_t)(2 * q + 2) * ts + 16 + (size_t)2 * q * es;
+}
 
 template <typename V>
 __device__ __forceinline__ V warp_sum(V v) {
@@ -1066,25 +1120,30 @@ __global__ void __launch_bounds__(HS_THREADS)
     k_hshift(int p, int q, const double2* __restrict__ A, int lda, size_t sA, const double* __restrict__ sh,
              const double2* __restrict__ C, int ldc, size_t sC, double2* __restrict__ Y, unsigned char* work,
              size_t work_stride, const int* __restrict__ kactive, int* __restrict__ info, int pack_in_smem,
-             int z_in_smem) {
+             int z_in_smem, int small_in_smem) {
   using V = cplx<T>;
   const int k = blockIdx.x;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tau = reinterpret_cast<V*>(smem_raw);
-  V* red = tau + q;  // [34]
-  T* dg = reinterpret_cast<T*>(red + 34);
-  T* eg = dg + q;
-  unsigned char* area = reinterpret_cast<unsigned char*>(eg + q + 2);
-  area = reinterpret_cast<unsigned char*>(((uintptr_t)area + 15) & ~(uintptr_t)15);
-  // work area of this k: packed reflectors, then z (q x p), then the bands (3 q per shift)
+  V* red = reinterpret_cast<V*>(smem_raw);  // [34]
+  unsigned char* sbase = reinterpret_cast<unsigned char*>(red + 34);
+  // work area of this k: packed reflectors, then z (q x p), then the bands (3 q per shift), then
+  // (large q) tau, d, e, v and w
   unsigned char* wk = work + (size_t)k * work_stride;
   V* Pg = reinterpret_cast<V*>(wk);
   V* Zg = Pg + poff(q, q);
   T* Bg = reinterpret_cast<T*>(Zg + (size_t)q * p);
+  unsigned char* xg = wk + hs_extra_off(p, q, sizeof(V), sizeof(T));
+  // tau, the tridiagonal (d, e) and v, w in shared memory, or all in the work area for large q
+  V* tau = reinterpret_cast<V*>(small_in_smem ? sbase : xg);
+  T* dg = reinterpret_cast<T*>(tau + q);
+  T* eg = dg + q;
+  unsigned char* after = reinterpret_cast<unsigned char*>(eg + q + 2);
+  after = reinterpret_cast<unsigned char*>(((uintptr_t)after + 15) & ~(uintptr_t)15);
+  unsigned char* area = small_in_smem ? after : sbase;  // the rest of shared memory
   // phase-1 layout of the area: packed matrix (if in shared memory), v, w
   V* P = pack_in_smem ? reinterpret_cast<V*>(area) : Pg;
-  V* vv = pack_in_smem ? P + poff(q, q) : reinterpret_cast<V*>(area);
+  V* vv = pack_in_smem ? P + poff(q, q) : reinterpret_cast<V*>(after);
   V* xv = vv + q;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const double2* Ak = A + k * sA;
@@ -1290,7 +1349,7 @@ __global__ void __launch_bounds__(HS_THREADS)
 
 // Work bytes per k of the shifted solve.
 static size_t hs_work_stride(int p, int q, size_t es, size_t ts) {
-  const size_t b = poff(q, q) * es + (size_t)q * p * es + (size_t)3 * p * q * ts;
+  const size_t b = hs_extra_off(p, q, es, ts) + hs_extra_size(q, es, ts);
   return (b + 255) & ~(size_t)255;
 }
 
@@ -1305,16 +1364,20 @@ static void hshift_launch(int K, int p, int q, const double2* A, int lda, size_t
                           int* info, cudaStream_t st) {
   using V = cplx<T>;
   constexpr size_t LIMIT = 227 * 1024;
-  const size_t persist = (size_t)q * sizeof(V) + 34 * sizeof(V) + (size_t)(2 * q + 2) * sizeof(T) + 16;
+  const size_t red = 34 * sizeof(V);
+  const size_t small = (size_t)q * sizeof(V) + (size_t)(2 * q + 2) * sizeof(T) + 16;  // tau, d, e
   const size_t pack = poff(q, q) * sizeof(V) + 2 * (size_t)q * sizeof(V);
   const size_t vecs = 2 * (size_t)q * sizeof(V);
   const size_t zb = (size_t)q * p * sizeof(V) + (size_t)3 * p * q * sizeof(T);
-  const int pack_in = persist + pack <= LIMIT;
+  const int small_in = red + small + vecs <= LIMIT;
+  const size_t persist = red + (small_in ? small : 0);
+  const int pack_in = small_in && persist + pack <= LIMIT;
   const int z_in = persist + zb <= LIMIT;
-  const size_t sm = persist + std::max(pack_in ? pack : vecs, z_in ? zb : (size_t)0);
+  const size_t sm = persist + std::max(pack_in ? pack : (small_in ? vecs : 0), z_in ? zb : (size_t)0);
   ensure_smem((const void*)k_hshift<T>, sm);
   k_hshift<T><<<K, HS_THREADS, sm, st>>>(p, q, A, lda, sA, s, C, ldc, sC, Y, (unsigned char*)work,
-                                         hs_work_stride(p, q, sizeof(V), sizeof(T)), kactive, info, pack_in, z_in);
+                                         hs_work_stride(p, q, sizeof(V), sizeof(T)), kactive, info, pack_in, z_in,
+                                         small_in);
   count_launch();
 }
 
@@ -1373,11 +1436,13 @@ void fom_pad_diag(int K, int q0, int p, double2* A, int lda, size_t sA, const in
 // 0..p-r-1 and column p-r+c = sum_a e_{piv[a]} (L^{-*})_{ac}, so R M is orthonormal on its
 // last r columns; nzero[k] = p - r.
 __global__ void k_pivchol(int p, const double2* __restrict__ G, const double* __restrict__ ref, double tol,
-                          double2* __restrict__ M, int* __restrict__ nzero, const int* __restrict__ kactive) {
+                          double2* __restrict__ M, int* __restrict__ nzero, const int* __restrict__ kactive,
+                          unsigned char* gscr, size_t gstride) {
   const int k = blockIdx.x;
   if (kactive && !kactive[k]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* S = reinterpret_cast<double2*>(smem_raw);  // Schur complement, S(i, j) = S[j * p + i]
+  // S, L and piv in shared memory, or (gscr set, large p) in this k's global scratch
+  double2* S = reinterpret_cast<double2*>(gscr ? gscr + (size_t)k * gstride : smem_raw);  // S(i, j) = S[j * p + i]
   double2* L = S + p * p;                             // factor, then its inverse
   int* piv = reinterpret_cast<int*>(L + p * p);
   __shared__ int mstep, rsel;
@@ -1399,11 +1464,18 @@ __global__ void k_pivchol(int p, const double2* __restrict__ G, const double* __
     rsel = 0;
   }
   for (int j = 0; j < p; ++j) {
-    if (threadIdx.x == 0) {
-      int m = j;
-      for (int i = j + 1; i < p; ++i)
-        if (S[i * p + i].x > S[m * p + m].x) m = i;
-      mstep = (S[m * p + m].x > thr) ? m : -1;
+    if (threadIdx.x < 32) {  // the first position of the largest remaining diagonal
+      double bv = -INFINITY;
+      int m = p;
+      for (int i = j + (int)threadIdx.x; i < p; i += 32) {
+        const double v = S[i * p + i].x;
+        if (v > bv) {
+          bv = v;
+          m = i;
+        }
+      }
+      warp_argmax(bv, m);
+      if (threadIdx.x == 0) mstep = (m < p && bv > thr) ? m : -1;
     }
     __syncthreads();
     const int m = mstep;
@@ -1470,10 +1542,13 @@ __global__ void k_pivchol(int p, const double2* __restrict__ G, const double* __
   if (threadIdx.x == 0 && nzero) nzero[k] = p - r;
 }
 void small_pivchol(int K, int p, const double2* G, const double* ref, double tol, double2* M, int* nzero,
-                   const int* kactive, cudaStream_t st) {
-  const size_t sm = sizeof(double2) * 2 * p * p + sizeof(int) * p;
+                   const int* kactive, cudaStream_t st, void* scratch) {
+  const bool big = pivchol_big(p) > PP_SMEM_MAX;
+  if (big && !scratch) return;  // callers size the scratch with dense_pp_scratch
+  const size_t sm = big ? 0 : sizeof(double2) * 2 * p * p + sizeof(int) * p;
   ensure_smem((const void*)k_pivchol, sm);
-  k_pivchol<<<K, 128, sm, st>>>(p, G, ref, tol, M, nzero, kactive);
+  k_pivchol<<<K, big ? PP_GLOBAL_THREADS : 128, sm, st>>>(p, G, ref, tol, M, nzero, kactive,
+                                                          big ? (unsigned char*)scratch : nullptr, pp_stride(p));
   count_launch();
 }
 

@@ -40,7 +40,7 @@ struct Status {
 
 namespace eacg {
 void small_pivchol(int K, int p, const double2* G, const double* ref, double tol, double2* M, int* nzero,
-                   const int* kactive, cudaStream_t st);
+                   const int* kactive, cudaStream_t st, void* scratch);
 void small_max_diag(int K, int p, const double2* G, double* out, cudaStream_t st);
 void small_put_herm_block(int K, int p, const double2* src, double2* A, int lda, size_t sA, int q0, cudaStream_t st);
 void small_take_y(int K, int q, int qcap, int p, const double2* Y, double2* Yf, const int* take, cudaStream_t st);
@@ -87,6 +87,7 @@ struct eacg_system {
   double2 *lam = nullptr, *lam_t = nullptr, *sm1 = nullptr, *sm2 = nullptr, *sm3 = nullptr, *evec = nullptr,
           *evec_t = nullptr, *sinv_t = nullptr, *sig = nullptr, *sigv = nullptr, *sigvh = nullptr;
   double *eval = nullptr, *eval_t = nullptr, *alpha = nullptr, *sqd = nullptr, *lref = nullptr;
+  unsigned char* ppscr = nullptr;  // global scratch of the p x p kernels (large p only)
   double2* cn_work = nullptr;
   size_t cn_elems = 0;
   double* d_red = nullptr;    // reduction scratch
@@ -388,6 +389,7 @@ extern "C" size_t eacg_bytes_required(const eacg_model* m, const eacg_params* pr
   const size_t tb = K * p * m->N * ncols * 16;
   const size_t nproj = (size_t)m->natoms * m->nproj_per_atom;
   size_t tot = 17 * blk + tb + N3 * (8 * 6 + 16 + 4) + K * nproj * nmax * 16 + 8 * N3 * 8 + (64 << 20);
+  tot += eacg::dense_pp_scratch((int)K, (int)p);
   if (fom_per_iter) *fom_per_iter = 2 * blk + K * p * p * 16 * 8;
   return tot;
 }
@@ -504,6 +506,7 @@ static eacg_status alloc_work(eacg_system* s) {
   for (auto m : smalls) TRY(dalloc(s, m, sp));
   double** vecs[] = {&s->eval, &s->eval_t, &s->alpha, &s->sqd, &s->lref};
   for (auto v : vecs) TRY(dalloc(s, v, sizeof(double) * (size_t)K * p));
+  if (const size_t ppb = dense_pp_scratch(K, p)) TRY(dalloc(s, &s->ppscr, ppb));
   // tbuf: one FP64 complex value per (band, jx, column)
   TRY(dalloc(s, &s->d_tbuf, sizeof(double2) * (size_t)K * p * N * s->ncols));
   // rho groups: enough CTAs to fill the GPU
@@ -1029,7 +1032,7 @@ static eacg_status polar(eacg_system* s, const double2* psi, double2* out, doubl
   const int K = s->K, p = s->p, nm = s->n_max;
   dense_gemm_cn(K, nm, p, p, psi, (size_t)p * nm, nm, psi, (size_t)p * nm, nm, s->sm1, (size_t)p * p, p, ONE, ZERO,
                 s->cn_work, nullptr, s->st, s->g.df64);
-  dense_heig(K, p, s->sm1, (size_t)p * p, ev, evv, nullptr, s->st);
+  dense_heig(K, p, s->sm1, (size_t)p * p, ev, evv, nullptr, s->st, s->ppscr);
   dense_eig_func(K, p, evv, ev, -0.5, 0.0, sinv, nullptr, s->st);
   dense_gemm_nn(K, nm, p, p, psi, (size_t)p * nm, nm, sinv, (size_t)p * p, p, out, (size_t)p * nm, nm, ONE, ZERO,
                 nullptr, s->st, s->g.df64);
@@ -1256,12 +1259,12 @@ static eacg_status orthonormalise(eacg_system* s, cplx<T>* R, const cplx<T>* V, 
   }
   // first (rank-revealing) pass
   O::cn(K, nm, p, p, R, sb, nm, R, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive, s->st, s->g.df64);
-  small_pivchol(K, p, s->sm1, s->lref, O::drop_tol, s->sm3, s->d_nzero, kactive, s->st);
+  small_pivchol(K, p, s->sm1, s->lref, O::drop_tol, s->sm3, s->d_nzero, kactive, s->st, s->ppscr);
   O::nn(K, nm, p, p, R, sb, nm, s->sm3, (size_t)p * p, p, scratch, sb, nm, ONE, ZERO, kactive, s->st, s->g.df64);
   // second pass on the kept block (reference: its own largest column norm)
   O::cn(K, nm, p, p, scratch, sb, nm, scratch, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, kactive,
         s->st, s->g.df64);
-  small_pivchol(K, p, s->sm1, nullptr, O::drop_tol, s->sm3, s->d_info, kactive, s->st);
+  small_pivchol(K, p, s->sm1, nullptr, O::drop_tol, s->sm3, s->d_info, kactive, s->st, s->ppscr);
   O::nn(K, nm, p, p, scratch, sb, nm, s->sm3, (size_t)p * p, p, out, sb, nm, ONE, ZERO, kactive, s->st, s->g.df64);
   CKL(s);
   return EACG_OK;
@@ -1295,7 +1298,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
   TRY(fom_reserve(s, 2 * p));
   // Sigma = Lambda - mu I, its eigenpairs and Q^H
   dense_shift_diag(K, p, lam, mu, s->sig, s->st);
-  dense_heig(K, p, s->sig, (size_t)p * p, s->eval, s->sigv, nullptr, s->st);
+  dense_heig(K, p, s->sig, (size_t)p * p, s->eval, s->sigv, nullptr, s->st, s->ppscr);
   small_conj_transpose(K, p, s->sigv, s->sigvh, s->st);
   dense_kinetic_alpha(K, p, nm, s->d_kin, phi, s->alpha, s->st);
   // C = Phi - (H X0 - X0 Sigma), X0 = Phi / mu, H X0 = H Phi / mu  (FP64, then in T)
@@ -1401,8 +1404,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
       if (!active[k]) continue;
       iters[k] = j;
       const double rel = std::sqrt(s->h_out[64 + k]) / cnorm[k];
-      // the projected solves keep their pivot bookkeeping for at most 1024 Krylov columns
-      if (!(rel <= s->prm.fom_rtol) && j < s->prm.max_fom && q + p <= 1024) {
+      if (!(rel <= s->prm.fom_rtol) && j < s->prm.max_fom) {
         any = true;
       } else {
         s->h_int[2 * K + k] = 1;  // take Y now
@@ -1469,7 +1471,7 @@ static eacg_status ea_gradient_t(eacg_system* s, const double2* phi, const doubl
     }
     dense_gemm_cn(K, nm, p, p, phi, sb, nm, s->Xb, sb, nm, s->sm1, (size_t)p * p, p, ONE, ZERO, s->cn_work, nullptr,
                   s->st, s->g.df64);
-    dense_inverse(K, p, s->sm1, s->sm2, nullptr, s->st);
+    dense_inverse(K, p, s->sm1, s->sm2, nullptr, s->st, s->ppscr);
     dense_copy(g, phi, s->blk, s->st);
     dense_gemm_nn(K, nm, p, p, s->Xb, sb, nm, s->sm2, (size_t)p * p, p, g, sb, nm, MONE, ONE, nullptr, s->st, s->g.df64);
   });
@@ -1636,7 +1638,7 @@ static eacg_status transport_g(eacg_system* s, double tau) {
                 s->st, s->g.df64);
   small_add_herm(K, p, s->sm1, tau, s->sm2, s->st);  // sm2 = tau (M + M^H)
   small_sqrt_vals(K, p, s->eval_t, s->sqd, s->st);
-  dense_lyapunov(K, p, s->evec_t, s->sqd, s->sm2, s->sm3, s->st);
+  dense_lyapunov(K, p, s->evec_t, s->sqd, s->sm2, s->sm3, s->st, s->ppscr);
   dense_copy(s->tmp1, s->gv, s->blk, s->st);
   dense_gemm_nn(K, nm, p, p, s->phi_t, sb, nm, s->sm3, (size_t)p * p, p, s->tmp1, sb, nm, MONE, ONE, nullptr, s->st, s->g.df64);
   dense_gemm_nn(K, nm, p, p, s->tmp1, sb, nm, s->sinv_t, (size_t)p * p, p, s->tg, sb, nm, ONE, ZERO, nullptr, s->st, s->g.df64);
@@ -1874,11 +1876,11 @@ static eacg_status do_step(eacg_system* s, eacg_step_info* info) {
   } while (0)
 
 // Calls that need the p x p dense kernels (eigen-decompositions, inverses, Lyapunov solves,
-// pivoted Cholesky, projected FOM solves), which hold a p x p block in one CTA's shared memory.
+// pivoted Cholesky, projected FOM solves): one CTA per k, up to 512 bands.
 #define DENSE_CHECK(sys)                                                                         \
   do {                                                                                           \
     if ((sys)->p > EACG_MAX_BANDS_DENSE) {                                                      \
-      (sys)->err = "this call needs the p x p dense kernels, which support at most 64 bands";   \
+      (sys)->err = "this call needs the p x p dense kernels, which support at most 512 bands";   \
       return EACG_EUNSUPPORTED;                                                                  \
     }                                                                                            \
   } while (0)
@@ -2438,7 +2440,7 @@ extern "C" eacg_status eacg_step_many(eacg_system* const* sys, int nsys, eacg_st
   for (int i = 0; i < nsys; ++i) {
     if (!sys[i]) return EACG_EINVAL;
     if (sys[i]->p > EACG_MAX_BANDS_DENSE) {
-      sys[i]->err = "this call needs the p x p dense kernels, which support at most 64 bands";
+      sys[i]->err = "this call needs the p x p dense kernels, which support at most 512 bands";
       return EACG_EUNSUPPORTED;
     }
     for (int j = 0; j < i; ++j)

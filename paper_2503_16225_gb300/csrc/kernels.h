@@ -182,16 +182,22 @@ void dense_axpby32(size_t n, double2 a, const float2* x, double2 b, const float2
 void dense_norms2_32(int K, size_t len, const float2* V, double* out, cudaStream_t st);
 void dense_tpa32(int K, int p, int n_max, const double* kin, const double* alpha, const float2* in, float2* out,
                  cudaStream_t st);
+// The p x p kernels (eigen-decomposition, inverse, Lyapunov, pivoted Cholesky) run one CTA per
+// k with the matrices in shared memory while they fit (up to p = 64 to 80 by kernel), else in a
+// global scratch of dense_pp_scratch(K, p) bytes (0 when none is needed) passed as `scratch`.
+size_t dense_pp_scratch(int K, int p);
 // Hermitian eigen-decomposition of K matrices p x p (ld p): ascending eigenvalues and
-// unit eigenvectors (columns).  p <= 64.
-void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive, cudaStream_t st);
+// unit eigenvectors (columns).
+void dense_heig(int K, int p, const double2* A, size_t sA, double* w, double2* V, const int* kactive, cudaStream_t st,
+                void* scratch = nullptr);
 // out[k] = V diag(f(w)) V^H with f(x) = x^e (e = -0.5, 0.5) restricted to w > cut; else 0.
 void dense_eig_func(int K, int p, const double2* V, const double* w, double expo, double cut_rel, double2* out,
                     const int* kactive, cudaStream_t st);
 // Inverse of K general p x p complex matrices (Gauss-Jordan, partial pivoting).
-void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st);
+void dense_inverse(int K, int p, const double2* A, double2* Ainv, int* info, cudaStream_t st, void* scratch = nullptr);
 // Lyapunov S X + X S = M with S = V diag(s) V^H: X = V [(V^H M V)_ij / (s_i + s_j)] V^H.
-void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st);
+void dense_lyapunov(int K, int p, const double2* V, const double* s, const double2* M, double2* X, cudaStream_t st,
+                    void* scratch = nullptr);
 // Elementwise helpers on blocks of length n per k (K blocks, stride s).
 void dense_axpby(size_t n, double2 a, const double2* x, double2 b, const double2* y, double2* out, cudaStream_t st);
 void dense_herm(int K, int p, double2* A, cudaStream_t st);

@@ -4,6 +4,7 @@ synthetic workload (energy, residual, iteration and Hamiltonian-application coun
 Calls only oracle/ (and the seeded input generators in synth/).  Usage:
     python tests/golden/make_golden.py diamond_k444     # 8-atom diamond, 4x4x4 k, 48^3, 16 bands
     python tests/golden/make_golden.py two_atom
+    python tests/golden/make_golden.py diamond64_ec5    # 64-atom supercell, Ecut 5, 48^3, 128 bands
     python tests/golden/make_golden.py serving          # sampled requests of the serving stream
 
 The serving target writes tests/golden/oracle_serving.json: converged oracle solves of
@@ -28,6 +29,8 @@ WORKLOADS = {
     "diamond_k111": lambda: synth.config_diamond(2, kgrid=(1, 1, 1)),
     "diamond_k222": lambda: synth.config_diamond(2, kgrid=(2, 2, 2)),
     "diamond_k444": lambda: synth.config_diamond(2, kgrid=(4, 4, 4)),
+    # 128 bands (64-atom supercell) at a low cutoff: the many-band dense path at oracle cost
+    "diamond64_ec5": lambda: synth.config_diamond_supercell(2, ecut=5.0, N=48),
 }
 
 

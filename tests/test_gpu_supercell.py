@@ -3,8 +3,9 @@ grid, 128 bands, 256 s/p projectors; Gamma and the unshifted 2x2x2 grid), agains
 CPU oracle.
 
 The transforms, the density, the potential, H application and the energy evaluation take
-more than 64 bands; the calls that decompose p x p matrices report EACG_EUNSUPPORTED.
-Every launch covers all K * 128 bands; the oracle checks a sample of them:
+all 128 bands in one launch per phase, and the p x p kernels work from a global scratch (the
+polar factor of eacg_set_psi is checked on every k-point).  The oracle checks a sample of
+the bands:
   * H psi of all bands on the device, compared on sampled bands per k-point;
   * the density of a block whose other bands are zero (so the oracle sums few bands) and
     the potential built from it;
@@ -47,14 +48,20 @@ def block_from(s, C):
     return t.cuda()
 
 
-def test_sizes_and_limits(supercell):
+def test_sizes_and_polar_factor(supercell):
+    """The p x p kernels take 128 bands from their global scratch: the polar factor of
+    eacg_set_psi against the oracle's Psi (Psi^* Psi)^{-1/2} on every k-point."""
     cfg, model, s = supercell
     assert s.p == 128 and s.N == 96 and model.Dvec.size == 256
     assert s.nk == model.nk
-    # the dense p x p calls are outside this build's band limit
-    with pytest.raises(E.EacgError) as ei:
-        E.eacg_set_psi(s.h, s.block())
-    assert ei.value.code == 9
+    raw = synth.raw_coefficients(cfg["seed"], model.nk, model.p, s.n_max)
+    E.eacg_set_psi(s.h, torch.from_numpy(raw).cuda())
+    phi = s.block()
+    E.eacg_get_psi(s.h, phi)
+    h = phi.cpu().numpy()
+    want = earcg.lowdin([raw[k, :, :model.nk[k]].T.copy() for k in range(model.K)])
+    for k in range(model.K):
+        assert rel(h[k, :, :model.nk[k]].T, want[k]) < 1e-12
 
 
 def test_density_and_potential(supercell):
