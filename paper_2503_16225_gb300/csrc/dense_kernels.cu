@@ -12,6 +12,8 @@
 #include <map>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -1073,6 +1075,7 @@ void dense_scale_rows(int K, int m, int n, double2* P, const double* d, cudaStre
 // reduction when it fits, else in the global work area; the reflectors are kept in the work
 // area for the two transforms.  Every reduction runs in a fixed order (deterministic).
 constexpr int HS_THREADS = 1024;
+constexpr int HG_MAX_CTAS = 1024;  // CTAs per k of the grid-wide variant (partial-sum slots)
 
 __host__ __device__ __forceinline__ size_t poff(int j, int q) {  // start of packed column j
   return (size_t)j * q - (size_t)j * (j - 1) / 2;
@@ -1083,7 +1086,7 @@ __host__ __device__ __forceinline__ size_t hs_extra_off(int p, int q, size_t es,
   return (b + 255) & ~(size_t)255;
 }
 __host__ __device__ __forceinline__ size_t hs_extra_size(int q, size_t es, size_t ts) {
-  return (size_t)q * es + (size_t)(2 * q + 2) * ts + 16 + (size_t)2 * q * es;
+  return (size_t)q * es + (size_t)(2 * q + 2) * ts + 16 + (size_t)2 * q * es + HG_MAX_CTAS * es + 64;
 }
 
 template <typename V>
@@ -1347,6 +1350,230 @@ __global__ void __launch_bounds__(HS_THREADS)
   }
 }
 
+// ---- Grid-wide variant for large q: the same four steps with one cooperative launch of G CTAs
+// per k (grid (G, K), 1024 threads each).  Step 1 keeps the packed matrix in the work area;
+// per column every CTA forms the reflector v from the same values (its own shared copy), warps
+// across all CTAs own rows of x = tau A22 v (each CTA's share of v^* x goes to a slot, summed
+// in slot order after the barrier), then warps across all CTAs own columns of the rank-2 update;
+// the warp owning column j + 1 writes the next tail norm.  Two grid barriers per column.  Steps
+// 2-4 give each shift to one warp of the grid (step 3 on its lane 0), so they need no barrier.
+// Every sum runs in a fixed order (deterministic for a given G).
+template <typename T>
+__global__ void __launch_bounds__(HS_THREADS)
+    k_hshift_grid(int p, int q, const double2* __restrict__ A, int lda, size_t sA, const double* __restrict__ sh,
+                  const double2* __restrict__ C, int ldc, size_t sC, double2* __restrict__ Y, unsigned char* work,
+                  size_t work_stride, const int* __restrict__ kactive, int* __restrict__ info) {
+  using V = cplx<T>;
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int k = blockIdx.y, cta = blockIdx.x, G = gridDim.x;
+  const bool act = !kactive || kactive[k];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* vs = reinterpret_cast<V*>(smem_raw);  // [q] reflector of the current column
+  V* xs = vs + q;                          // [q] x of the current column
+  V* red = xs + q;                         // [34]
+  unsigned char* wk = work + (size_t)k * work_stride;
+  V* Pg = reinterpret_cast<V*>(wk);
+  V* Zg = Pg + poff(q, q);
+  T* Bg = reinterpret_cast<T*>(Zg + (size_t)q * p);
+  unsigned char* xg = wk + hs_extra_off(p, q, sizeof(V), sizeof(T));
+  V* tau = reinterpret_cast<V*>(xg);
+  T* dg = reinterpret_cast<T*>(tau + q);
+  T* eg = dg + q;
+  unsigned char* after = reinterpret_cast<unsigned char*>(eg + q + 2);
+  after = reinterpret_cast<unsigned char*>(((uintptr_t)after + 15) & ~(uintptr_t)15);
+  V* xv = reinterpret_cast<V*>(after) + q;  // x of the current column, shared by the grid
+  V* part = xv + q;                         // [HG_MAX_CTAS] per-CTA shares of v^* x
+  T* ssg = reinterpret_cast<T*>(part + HG_MAX_CTAS);  // squared tail norm of the next column
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int gw = cta * nw + warp, GW = G * nw;  // this warp within the k's grid, and the count
+  V zero;
+  zero.x = 0;
+  zero.y = 0;
+  if (act) {
+    const double2* Ak = A + k * sA;
+    for (int j = cta; j < q; j += G)
+      for (int i = j + tid; i < q; i += blockDim.x) Pg[poff(j, q) + (i - j)] = to_c<T>(Ak[(size_t)j * lda + i]);
+    if (cta == G - 1) {  // tail norm of column 0 (rows 2..), read back after the barrier
+      V prt = zero;
+      for (int i = 2 + tid; i < q; i += blockDim.x) {
+        const double2 a = Ak[i];
+        const V x = to_c<T>(a);
+        prt.x += x.x * x.x + x.y * x.y;
+      }
+      const T s0 = block_sum(prt, red).x;
+      if (tid == 0) *ssg = s0;
+    }
+  }
+  grid.sync();
+  for (int j = 0; j + 1 < q; ++j) {
+    const size_t cj = poff(j, q) - j;  // P(i, j) = Pg[cj + i]
+    V t = zero;
+    if (act) {
+      const T ss = *ssg;
+      const V alpha = Pg[cj + j + 1];
+      V scale = mk<V>((T)1, (T)0);
+      T beta = alpha.x;
+      if (ss > (T)0 || alpha.y != (T)0) {
+        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + ss), alpha.x);
+        t.x = (beta - alpha.x) / beta;
+        t.y = -alpha.y / beta;
+        const V am = mk<V>(alpha.x - beta, alpha.y);
+        const T den = am.x * am.x + am.y * am.y;
+        scale = mk<V>(am.x / den, -am.y / den);
+      }
+      if (cta == 0 && tid == 0) {
+        tau[j] = t;
+        eg[j] = beta;
+        dg[j] = Pg[cj + j].x;
+      }
+      for (int i = j + 1 + tid; i < q; i += blockDim.x) vs[i] = (i == j + 1) ? mk<V>((T)1, (T)0) : cmul(Pg[cj + i], scale);
+      __syncthreads();
+      if (t.x != (T)0 || t.y != (T)0) {
+        V dpart = zero;
+        for (int i = j + 1 + gw; i < q; i += GW) {
+          const size_t ci = poff(i, q) - i;
+          V acc = zero;
+          for (int l = j + 1 + lane; l <= i; l += 32) acc = acc + cmul(Pg[poff(l, q) + (i - l)], vs[l]);
+          for (int l = i + 1 + lane; l < q; l += 32) acc = acc + cmulc(Pg[ci + l], vs[l]);
+          acc = warp_sum(acc);
+          const V xi = cmul(t, acc);
+          if (lane == 0) xv[i] = xi;
+          dpart = dpart + cmulc(vs[i], xi);
+        }
+        const V dsum = block_sum(dpart, red);  // lanes of a warp hold the same dpart: scale below
+        if (tid == 0) part[cta] = cscale(dsum, (T)1 / (T)32);
+      }
+    }
+    grid.sync();  // x and the shares of v^* x are complete; every CTA has read column j
+    if (act) {
+      if (t.x != (T)0 || t.y != (T)0) {
+        if (warp == 0) {
+          V d = zero;
+          for (int c = lane; c < G; c += 32) d = d + part[c];
+          d = warp_sum(d);
+          if (lane == 0) red[32] = d;
+        }
+        for (int i = j + 1 + tid; i < q; i += blockDim.x) xs[i] = xv[i];
+        __syncthreads();
+        const V a2 = cscale(cmul(t, cconj(red[32])), (T)-0.5);
+        for (int l = j + 1 + gw; l < q; l += GW) {
+          const size_t cl = poff(l, q) - l;
+          const V vl = vs[l], wl = xs[l] + cmul(a2, vl);
+          V tail = zero;
+          for (int i = l + lane; i < q; i += 32) {
+            const V vi = vs[i], wi = xs[i] + cmul(a2, vi);
+            const V d = cmul(vi, cconj(wl)) + cmul(wi, cconj(vl));
+            const V nv = Pg[cl + i] - d;
+            Pg[cl + i] = nv;
+            if (l == j + 1 && i >= j + 3) tail.x += nv.x * nv.x + nv.y * nv.y;
+          }
+          if (l == j + 1) {
+            tail = warp_sum(tail);
+            if (lane == 0) *ssg = tail.x;
+          }
+        }
+      } else if (cta == 0) {  // no reflection: the next column's tail norm
+        V prt = zero;
+        const size_t cn = poff(j + 1, q) - (j + 1);
+        for (int i = j + 3 + tid; i < q; i += blockDim.x) {
+          const V x = Pg[cn + i];
+          prt.x += x.x * x.x + x.y * x.y;
+        }
+        const T nss = block_sum(prt, red).x;
+        if (tid == 0) *ssg = nss;
+      }
+      if (cta == 0)  // the reflector replaces column j (all CTAs read it before the barrier)
+        for (int i = j + 1 + tid; i < q; i += blockDim.x) Pg[cj + i] = vs[i];
+    }
+    grid.sync();  // the updated trailing matrix and the next tail norm are complete
+  }
+  if (act && cta == 0 && tid == 0) {
+    dg[q - 1] = Pg[poff(q - 1, q)].x;
+    eg[q - 1] = 0;
+  }
+  grid.sync();
+  if (!act) return;
+  // ---- 2.-4. one warp of the grid per shift: z = Q^* c, (T - s_m I) z = z, y = Q z
+  for (int m = gw; m < p; m += GW) {
+    V* z = Zg + (size_t)m * q;
+    for (int i = lane; i < q; i += 32) z[i] = to_c<T>(C[k * sC + (size_t)m * ldc + i]);
+    __syncwarp();
+    for (int j = 0; j + 1 < q; ++j) {
+      const V tj = tau[j];
+      if (tj.x == (T)0 && tj.y == (T)0) continue;
+      const V* v = Pg + poff(j, q) - j;
+      V acc = zero;
+      for (int i = j + 1 + lane; i < q; i += 32) acc = acc + cmulc(v[i], z[i]);
+      const V f = cmul(cconj(tj), warp_sum(acc));
+      __syncwarp();
+      for (int i = j + 1 + lane; i < q; i += 32) z[i] = z[i] - cmul(v[i], f);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      T* dd = Bg + (size_t)m * 3 * q;
+      T* du = dd + q;
+      T* du2 = du + q;
+      const T smv = (T)sh[(size_t)k * p + m];
+      for (int i = 0; i < q; ++i) {
+        dd[i] = dg[i] - smv;
+        du[i] = eg[i];
+        du2[i] = 0;
+      }
+      int bad = 0;
+      for (int i = 0; i + 1 < q; ++i) {
+        const T sub = eg[i];
+        if (fabs(dd[i]) >= fabs(sub)) {
+          if (dd[i] == (T)0) {
+            bad = 1;
+            continue;
+          }
+          const T f = sub / dd[i];
+          dd[i + 1] -= f * du[i];
+          z[i + 1] = z[i + 1] - cscale(z[i], f);
+          du2[i] = 0;
+        } else {
+          const T f = dd[i] / sub;
+          dd[i] = sub;
+          const T tmp = dd[i + 1];
+          dd[i + 1] = du[i] - f * tmp;
+          if (i + 2 < q) {
+            du2[i] = du[i + 1];
+            du[i + 1] = -f * du2[i];
+          }
+          du[i] = tmp;
+          const V bi = z[i];
+          z[i] = z[i + 1];
+          z[i + 1] = bi - cscale(z[i], f);
+        }
+      }
+      if (dd[q - 1] == (T)0) bad = 1;
+      if (bad) {
+        if (info) info[k * p + m] = 1;
+        for (int i = 0; i < q; ++i) z[i] = zero;
+      } else {
+        z[q - 1] = cscale(z[q - 1], (T)1 / dd[q - 1]);
+        if (q > 1) z[q - 2] = cscale(z[q - 2] - cscale(z[q - 1], du[q - 2]), (T)1 / dd[q - 2]);
+        for (int i = q - 3; i >= 0; --i)
+          z[i] = cscale(z[i] - cscale(z[i + 1], du[i]) - cscale(z[i + 2], du2[i]), (T)1 / dd[i]);
+      }
+    }
+    __syncwarp();
+    for (int j = q - 2; j >= 0; --j) {
+      const V tj = tau[j];
+      if (tj.x == (T)0 && tj.y == (T)0) continue;
+      const V* v = Pg + poff(j, q) - j;
+      V acc = zero;
+      for (int i = j + 1 + lane; i < q; i += 32) acc = acc + cmulc(v[i], z[i]);
+      const V f = cmul(tj, warp_sum(acc));
+      __syncwarp();
+      for (int i = j + 1 + lane; i < q; i += 32) z[i] = z[i] - cmul(v[i], f);
+      __syncwarp();
+    }
+    for (int i = lane; i < q; i += 32) Y[k * sC + (size_t)m * ldc + i] = to_d(z[i]);
+  }
+}
+
 // Work bytes per k of the shifted solve.
 static size_t hs_work_stride(int p, int q, size_t es, size_t ts) {
   const size_t b = hs_extra_off(p, q, es, ts) + hs_extra_size(q, es, ts);
@@ -1364,6 +1591,38 @@ static void hshift_launch(int K, int p, int q, const double2* A, int lda, size_t
                           int* info, cudaStream_t st) {
   using V = cplx<T>;
   constexpr size_t LIMIT = 227 * 1024;
+  constexpr int HG_MIN_Q = 1536;  // below this the one-CTA kernel is faster than grid barriers
+  const size_t gsm = (2 * (size_t)q + 34) * sizeof(V);
+  if (q >= HG_MIN_Q && gsm <= LIMIT) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    int dev = 0, sms = 0, coop = 0, per = 0;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess) {
+      ensure_smem((const void*)k_hshift_grid<T>, gsm);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hshift_grid<T>, HS_THREADS, gsm) != cudaSuccess)
+        per = 0;
+      const int G = std::min(std::min(HG_MAX_CTAS, per * sms / std::max(K, 1)), std::max(1, q / 32));
+      if (cs == cudaStreamCaptureStatusNone && coop && G >= 2) {
+        int p_ = p, q_ = q, lda_ = lda, ldc_ = ldc;
+        size_t sA_ = sA, sC_ = sC, stride = hs_work_stride(p, q, sizeof(V), sizeof(T));
+        const double2* A_ = A;
+        const double* s_ = s;
+        const double2* C_ = C;
+        double2* Y_ = Y;
+        unsigned char* w_ = (unsigned char*)work;
+        const int* ka_ = kactive;
+        int* info_ = info;
+        void* args[] = {&p_, &q_, &A_, &lda_, &sA_, &s_, &C_, &ldc_, &sC_, &Y_, &w_, &stride, &ka_, &info_};
+        if (cudaLaunchCooperativeKernel((const void*)k_hshift_grid<T>, dim3(G, K), dim3(HS_THREADS), args, gsm, st) ==
+            cudaSuccess) {
+          count_launch();
+          return;
+        }
+      }
+    }
+    cudaGetLastError();  // the one-CTA kernel below
+  }
   const size_t red = 34 * sizeof(V);
   const size_t small = (size_t)q * sizeof(V) + (size_t)(2 * q + 2) * sizeof(T) + 16;  // tau, d, e
   const size_t pack = poff(q, q) * sizeof(V) + 2 * (size_t)q * sizeof(V);
