@@ -75,10 +75,11 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="serving_stream",
                     choices=["serving_stream", "diamond_k444", "diamond_k222", "two_atom", "diamond64_gamma",
-                             "diamond64_k222", "diamond216_gamma"],
+                             "diamond64_k222", "diamond64_ec5", "diamond216_gamma"],
                     help="serving_stream: the 256-request stream (headline); the others: concurrent solves "
-                         "of one workload; diamond64_*: the 64-atom supercell (96^3 grid, 128 bands, 256 "
-                         "projectors), --op runs only (its p x p dense steps exceed the 64-band limit)")
+                         "of one workload; diamond64_*: the 64-atom supercell (128 bands, 256 projectors; "
+                         "96^3 grid at Ecut 15, or 48^3 at Ecut 5 for diamond64_ec5, whose oracle solve is "
+                         "stored); diamond216_gamma (N = 128): --op runs with FP32 transforms only")
     ap.add_argument("--resident", type=int, default=16, help="maximum resident requests while serving")
     ap.add_argument("--op", default="solve", choices=["solve", "apply_h", "density", "ea_gradient"],
                     help="apply_h / density / ea_gradient: time a few calls of one operation on the "
@@ -181,6 +182,7 @@ def workload(name):
             "two_atom": lambda: synth.config_two_atom(1),
             "diamond64_gamma": lambda: synth.config_diamond_supercell(2),
             "diamond64_k222": lambda: synth.config_diamond_supercell(2, kgrid=(2, 2, 2)),
+            "diamond64_ec5": lambda: synth.config_diamond_supercell(2, ecut=5.0, N=48),
             "diamond216_gamma": lambda: synth.config_diamond_supercell(3)}[name]()
 
 
@@ -850,6 +852,12 @@ def run_solve(args):
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": C * host.numel() * 16,
                 "d2h_bytes_per_step": C * host.numel() * 16},
     }
+    gpath = os.path.join(ROOT, "tests", "golden", f"oracle_{args.workload}.json")
+    if os.path.exists(gpath):  # the oracle's own converged solve of this workload
+        with open(gpath) as fh:
+            gd = json.load(fh)
+        line["accuracy"] = {"dE_per_atom_Ha": r4(abs(results[-1].E - gd["E"]) / max(1, gd["natoms"])),
+                            "tolerance": 1e-6 if prec else 1e-8, "oracle": os.path.relpath(gpath, ROOT)}
     if rank == 0 and world == 1 and not args.no_extras:
         try:
             if args.workload == "two_atom":
