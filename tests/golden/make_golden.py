@@ -5,6 +5,7 @@ Calls only oracle/ (and the seeded input generators in synth/).  Usage:
     python tests/golden/make_golden.py diamond_k444     # 8-atom diamond, 4x4x4 k, 48^3, 16 bands
     python tests/golden/make_golden.py two_atom
     python tests/golden/make_golden.py diamond64_ec5    # 64-atom supercell, Ecut 5, 48^3, 128 bands
+    python tests/golden/make_golden.py diamond64_gamma  # 64-atom supercell, Ecut 15, 96^3 (hours)
     python tests/golden/make_golden.py serving          # sampled requests of the serving stream
 
 The serving target writes tests/golden/oracle_serving.json: converged oracle solves of
@@ -31,6 +32,8 @@ WORKLOADS = {
     "diamond_k444": lambda: synth.config_diamond(2, kgrid=(4, 4, 4)),
     # 128 bands (64-atom supercell) at a low cutoff: the many-band dense path at oracle cost
     "diamond64_ec5": lambda: synth.config_diamond_supercell(2, ecut=5.0, N=48),
+    # the full-size 64-atom supercell at Gamma (Ecut 15, 96^3, 128 bands): hours of oracle time
+    "diamond64_gamma": lambda: synth.config_diamond_supercell(2),
 }
 
 
