@@ -1600,8 +1600,10 @@ static void hshift_launch(int K, int p, int q, const double2* A, int lda, size_t
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess) {
       ensure_smem((const void*)k_hshift_grid<T>, gsm);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hshift_grid<T>, HS_THREADS, gsm) != cudaSuccess)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hshift_grid<T>, HS_THREADS, gsm) != cudaSuccess) {
+        cudaGetLastError();
         per = 0;
+      }
       const int G = std::min(std::min(HG_MAX_CTAS, per * sms / std::max(K, 1)), std::max(1, q / 32));
       if (cs == cudaStreamCaptureStatusNone && coop && G >= 2) {
         int p_ = p, q_ = q, lda_ = lda, ldc_ = ldc;
@@ -1619,9 +1621,9 @@ static void hshift_launch(int K, int p, int q, const double2* A, int lda, size_t
           count_launch();
           return;
         }
+        cudaGetLastError();  // launch refused (e.g. too few resident CTAs): the one-CTA kernel below
       }
     }
-    cudaGetLastError();  // the one-CTA kernel below
   }
   const size_t red = 34 * sizeof(V);
   const size_t small = (size_t)q * sizeof(V) + (size_t)(2 * q + 2) * sizeof(T) + 16;  // tau, d, e
